@@ -1,0 +1,152 @@
+"""Plain numpy NFFT (type 2 forward, type 1 adjoint, gradient) -- TEST INFRASTRUCTURE.
+
+Only tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline legs
+use this module; the product never imports it.
+
+The paper (Sec. 2.2.1) uses the NFFT only as a black box with cost
+O(N log N + M |log eps|^3) and states no window, oversampling or cutoff.  This
+module restates the standard NFFT approximation of the series (the paper's
+citation [KKP09]) from its derivation, step by step, with no blocking or
+fusion:
+
+  grid nodes   x_l = -1/2 + l/n_d  (l = 0..n_d-1, periodic),  u = n (x + 1/2)
+  window       half-width alpha = m + 1/2 cells (the 2m+1 taps span it),
+               phi(tau) = sinh(b sqrt(alpha^2 - tau^2)) / (pi sqrt(alpha^2 - tau^2))
+               for -alpha < tau <= alpha (value b/pi at tau = alpha), 0 outside;
+               b = pi (2 - 1/sigma), sigma = n/N
+  its transform Phi(nu) = int phi(tau) e^{-2 pi i nu tau} dtau
+                        = I0(alpha sqrt(b^2 - (2 pi nu)^2))     (|2 pi nu| <= b)
+               (one excluded end point does not change the integral)
+  step 1 (deconvolve + zero-pad)  G[k mod n] = c_k (-1)^{k1+k2+k3} / prod_d Phi(k_d/n_d)
+  step 2 (oversampled FFT)        g_l = sum_k G_k e^{+2 pi i k.l/n}      (unnormalised)
+  step 3 (window sum)             f_j = sum_l g_{l mod n} prod_d phi(u_{j,d} - l_d),
+                                  l_d = ceil(u_{j,d} - alpha) + {0, ..., 2m}
+                                  (exactly the nodes with -alpha < u - l <= alpha)
+
+The (-1)^k factor moves the grid origin from 0 to -1/2.  The adjoint applies
+the transposes in reverse order (spread, forward FFT, the same deconvolution),
+and the gradient deconvolves 2 pi i k_d c_k in step 1.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import i0 as _i0
+
+
+def kb_b(n: int, N: int) -> float:
+    """Shape parameter b = pi (2 - 1/sigma), sigma = n/N."""
+    return math.pi * (2.0 - N / n)
+
+
+def kb_phi(tau, m: int, b: float):
+    """Kaiser-Bessel window in grid units, half-width alpha = m + 1/2,
+    support -alpha < tau <= alpha (value b/pi at tau = alpha)."""
+    al = m + 0.5
+    tau = np.asarray(tau, dtype=np.float64)
+    s = np.sqrt(np.maximum((al - tau) * (al + tau), 0.0))
+    safe = np.where(s > 0, s, 1.0)
+    val = np.where(s > 0, np.sinh(b * s) / (math.pi * safe), b / math.pi)
+    return np.where((tau > -al) & (tau <= al), val, 0.0)
+
+
+def kb_Phi(k, n: int, m: int, b: float):
+    """Fourier transform of ``kb_phi`` at nu = k/n: I0(alpha sqrt(b^2 - (2 pi k/n)^2))."""
+    k = np.asarray(k, dtype=np.float64)
+    return _i0((m + 0.5) * np.sqrt(b * b - (2.0 * math.pi * k / n) ** 2))
+
+
+def _setup(N, n, m):
+    N = tuple(int(v) for v in N)
+    n = tuple(int(v) for v in n)
+    if any(nd < Nd for nd, Nd in zip(n, N)):
+        raise ValueError("n_d must be >= N_d")
+    if m < 0:
+        raise ValueError("m must be >= 0")
+    ks = [np.arange(Nd) - Nd // 2 for Nd in N]
+    bs = [kb_b(nd, Nd) for nd, Nd in zip(n, N)]
+    # per-dimension deconvolution factors (-1)^k / Phi(k/n)
+    dec = [((-1.0) ** np.abs(k)) / kb_Phi(k, nd, m, b) for k, nd, b in zip(ks, n, bs)]
+    return N, n, ks, bs, dec
+
+
+def _window_rows(x, n, m, bs):
+    """Per point and dimension: first stencil node l0 = ceil(u - alpha) and the
+    2m+1 window values phi(u - l0 - a), a = 0..2m."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    xw = x - np.floor(x + 0.5)          # wrap onto [-1/2, 1/2)
+    al = m + 0.5
+    l0s, ws = [], []
+    a = np.arange(2 * m + 1)
+    for d in range(3):
+        u = n[d] * (xw[:, d] + 0.5)
+        l0 = np.ceil(u - al)
+        tau = u[:, None] - (l0[:, None] + a[None, :])
+        l0s.append(l0.astype(np.int64))
+        ws.append(kb_phi(tau, m, bs[d]))
+    return l0s, ws
+
+
+def forward(c, x, n, m: int):
+    """NFFT approximation of f_j = sum_k c_k e^{2 pi i k.x_j} (steps 1-3)."""
+    c = np.asarray(c, dtype=np.complex128)
+    N, n, ks, bs, dec = _setup(c.shape, n, m)
+    return _gather(_oversampled_grid(c, N, n, ks, dec), x, n, m, bs)
+
+
+def _oversampled_grid(c, N, n, ks, dec):
+    G = np.zeros(n, dtype=np.complex128)
+    D = dec[0][:, None, None] * dec[1][None, :, None] * dec[2][None, None, :]
+    G[np.ix_(ks[0] % n[0], ks[1] % n[1], ks[2] % n[2])] = c * D
+    return np.fft.ifftn(G) * (n[0] * n[1] * n[2])  # unnormalised e^{+} transform
+
+
+def _gather(g, x, n, m, bs):
+    l0s, ws = _window_rows(x, n, m, bs)
+    M = l0s[0].shape[0]
+    f = np.zeros(M, dtype=np.complex128)
+    a = np.arange(2 * m + 1)
+    i3 = (l0s[2][:, None] + a[None, :]) % n[2]
+    for p in range(2 * m + 1):
+        i1 = (l0s[0] + p) % n[0]
+        for q in range(2 * m + 1):
+            i2 = (l0s[1] + q) % n[1]
+            inner = np.sum(g[i1[:, None], i2[:, None], i3] * ws[2], axis=1)
+            f += ws[0][:, p] * ws[1][:, q] * inner
+    return f
+
+
+def forward_grad(c, x, n, m: int):
+    """NFFT approximation of the series and its gradient (i k-weighted series)."""
+    c = np.asarray(c, dtype=np.complex128)
+    N, n, ks, bs, dec = _setup(c.shape, n, m)
+    f = _gather(_oversampled_grid(c, N, n, ks, dec), x, n, m, bs)
+    grads = []
+    for d in range(3):
+        shape = [1, 1, 1]
+        shape[d] = N[d]
+        kd = ks[d].reshape(shape)
+        cd = 2j * math.pi * kd * c
+        grads.append(_gather(_oversampled_grid(cd, N, n, ks, dec), x, n, m, bs))
+    return f, np.stack(grads, axis=1)
+
+
+def adjoint(f, x, N, n, m: int):
+    """NFFT approximation of h_k = sum_j f_j e^{-2 pi i k.x_j} (transposed steps)."""
+    N, n, ks, bs, dec = _setup(N, n, m)
+    f = np.asarray(f, dtype=np.complex128).reshape(-1)
+    l0s, ws = _window_rows(x, n, m, bs)
+    H = np.zeros(n, dtype=np.complex128)
+    a = np.arange(2 * m + 1)
+    i3 = (l0s[2][:, None] + a[None, :]) % n[2]
+    for p in range(2 * m + 1):
+        i1 = (l0s[0] + p) % n[0]
+        for q in range(2 * m + 1):
+            i2 = (l0s[1] + q) % n[1]
+            vals = (f * ws[0][:, p] * ws[1][:, q])[:, None] * ws[2]
+            np.add.at(H, (np.broadcast_to(i1[:, None], i3.shape),
+                          np.broadcast_to(i2[:, None], i3.shape), i3), vals)
+    Hk = np.fft.fftn(H)  # unnormalised e^{-} transform
+    D = dec[0][:, None, None] * dec[1][None, :, None] * dec[2][None, None, :]
+    return Hk[np.ix_(ks[0] % n[0], ks[1] % n[1], ks[2] % n[2])] * D
