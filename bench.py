@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""NFFT throughput benchmark: Mpoints/s of the 3D type-2 NFFT at N = 256^3.
+
+Workload (the precision sweep): N = 256^3 coefficients c_k = CN(0,1)
+exp(-|k|^2 / (2 * 40^2)); M = 10^7 points, half uniform on the torus, half a
+Gaussian cluster (std 0.02) at the origin; sigma = 2 (n = 512^3).  Two
+families run side by side: FP64 at m = 6 (relative l2 <= 1e-12 against the
+FP64 direct sum) and mixed FP32 at m = 3 (<= 1e-6).  The achieved errors are
+measured on a fixed 2000-point subsample and reported in the JSON line.
+
+A step is one pass of the hot path over one batch: set_points (FP64
+reduction + tile sort) and eval (deconvolve/scatter, cuFFT, window gather).
+Inputs are resident in HBM when the timed region starts; every input (the
+512^3 grid alone is 2.1 GB in FP64) is larger than the 129 MB L2, so no
+explicit flush is done.  `e2e` repeats the step through the host-buffer C-ABI
+call (nfft3d_eval_host), with the H2D copies of x and c and the D2H copy of f
+inside the timed region.
+
+Multi-GPU (torchrun): points shard across ranks with no collective (weak
+scaling: every rank evaluates its own 10^7 points); `value` = all ranks'
+points / max-over-ranks time.
+
+`--impl reference` times the FP64 direct-sum oracle on the host cores on a
+bounded sample of the same workload (the only CPU arm this project has).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_EDGE = 256
+M_POINTS = 10_000_000
+M_FP64 = 6
+M_MIXED = 3
+SUBSAMPLE = 1000  # per population
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--points", type=int, default=M_POINTS)
+    ap.add_argument("--n", type=int, default=N_EDGE)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def gather_flops_per_point(m: int) -> int:
+    """Separable window sum: 2 (2 w^3 + 2 w^2 + 2 w) real flops per point, w = 2m + 1."""
+    w = 2 * m + 1
+    return 2 * (2 * w ** 3 + 2 * w ** 2 + 2 * w)
+
+
+def gather_bytes(M: int, n: int, real_bytes: int) -> int:
+    """Algorithmic bytes of one gather launch: the oversampled grid read once,
+    the reduced point data (3 stencil origins int32 + 3 offsets) and the output."""
+    cplx = 2 * real_bytes
+    return n ** 3 * cplx + M * (3 * 4 + 3 * real_bytes + cplx)
+
+
+def alu_peaks():
+    """FP32 / FP64 CUDA-core peaks from unit counts and clocks: 152 SMs x 128 FP32
+    lanes x 2 flops x 2.07 GHz; FP64 from the GB300's nominal 1.25 TFLOP/s."""
+    return {"fp32_tflops": 152 * 128 * 2 * 2.070e9 / 1e12, "fp64_tflops": 1.25}
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_1605_01244_gb300 import build, workloads as wl
+    from paper_1605_01244_gb300 import _lib
+    from paper_1605_01244_gb300.nfft import Plan
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world > 1:
+        build.build()
+    if dist:
+        dist.barrier()
+
+    N = args.n
+    M = args.points
+    c_np = wl.gaussian_coeffs((N, N, N), 40.0, seed=0)
+    # each rank draws its own batch of points (weak scaling)
+    x_np = wl.mixed_points(M, 0.02, seed=100 + 7919 * rank)
+    dev = torch.device("cuda", local)
+    x = torch.from_numpy(x_np).to(dev)
+    results = {}
+    peaks, peak_src = load_peaks()
+    apk = alu_peaks()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for fam, m, cdt, rb in (("f64", M_FP64, torch.complex128, 8), ("f32", M_MIXED, torch.complex64, 4)):
+        c = torch.from_numpy(c_np).to(cdt).to(dev)
+        plan = Plan((N, N, N), M, m=m, sigma=2.0, precision=fam)
+        f = torch.empty(M, dtype=cdt, device=dev)
+        for _ in range(args.warmup):
+            plan.set_points(x)
+            plan.eval(c, out=f)
+        barrier()
+        _lib.lib().nfft3_timing_enable(plan._h, 1)
+        _lib.lib().nfft3_timing_read(plan._h, None, None, None, 1)
+        sampler = ClockSampler(local)
+        sampler.start()
+        s = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(s)
+        for _ in range(args.steps):
+            plan.set_points(x)
+            plan.eval(c, out=f)
+        e1.record(s)
+        barrier()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1) / args.steps
+        import ctypes
+        st_ms = (ctypes.c_double * 7)()
+        st_n = (ctypes.c_int64 * 7)()
+        launches = ctypes.c_int64()
+        _lib.lib().nfft3_timing_read(plan._h, st_ms, st_n, ctypes.byref(launches), 1)
+        _lib.lib().nfft3_timing_enable(plan._h, 0)
+        stages = {nm: (st_ms[i] / st_n[i] if st_n[i] else 0.0) for i, nm in enumerate(_lib.STAGES[:4])}
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        # eval-only throughput (points already set)
+        barrier()
+        e0.record(s)
+        for _ in range(args.steps):
+            plan.eval(c, out=f)
+        e1.record(s)
+        barrier()
+        ms_eval = e0.elapsed_time(e1) / args.steps
+        # accuracy on the fixed subsample (oracle on rank 0's host; computed later)
+        idx = np.concatenate([wl.rng(99).choice(M // 2, SUBSAMPLE, replace=False),
+                              M // 2 + wl.rng(98).choice(M - M // 2, SUBSAMPLE, replace=False)])
+        f_sub = f[torch.from_numpy(idx).to(dev)].cpu().numpy().astype(np.complex128)
+        # e2e through the host-buffer call (pinned host memory)
+        xh = torch.from_numpy(x_np).pin_memory()
+        ch = torch.from_numpy(c_np).to(cdt).pin_memory()
+        fh = torch.empty(M, dtype=cdt).pin_memory()
+        plan.eval_host(xh, ch, fh)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.eval_host(xh, ch, fh)
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        if dist:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        g_ms = stages["gather"]
+        flops = gather_flops_per_point(m) * M
+        byts = gather_bytes(M, 2 * N, rb)
+        t_alu = flops / (apk["fp64_tflops" if fam == "f64" else "fp32_tflops"] * 1e12)
+        t_hbm = byts / (peaks["hbm_gbs"] * 1e9)
+        if t_alu >= t_hbm:
+            pk = apk["fp64_tflops" if fam == "f64" else "fp32_tflops"]
+            ach = flops / (g_ms * 1e-3) / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                    "traffic": None, "kernel": "gather_kernel", "flops_per_launch": flops,
+                    "peak_source": "derived (unit counts x clock)"}
+        else:
+            pk = peaks["hbm_gbs"]
+            ach = byts / (g_ms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
+                    "traffic": None, "kernel": "gather_kernel", "bytes_per_launch": byts,
+                    "peak_source": peak_src}
+        results[fam] = {
+            "m": m, "ms_per_step": ms, "ms_eval_only": ms_eval, "e2e_ms": e2e_ms,
+            "stages_ms": stages, "launches_per_step": launches.value / args.steps,
+            "clocks": clocks, "roofline": roof, "f_sub": f_sub, "idx": idx,
+            "h2d": M * 3 * 8 + N ** 3 * 2 * rb, "d2h": M * 2 * rb,
+        }
+        plan.close()
+        del c, f
+        torch.cuda.empty_cache()
+
+    if dist:
+        dist.barrier()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    import oracle
+    fd = oracle.forward(c_np, x_np[results["f64"]["idx"]])
+    for fam in results:
+        r = results[fam]
+        r["rel_l2"] = float(np.linalg.norm(r["f_sub"] - fd) / np.linalg.norm(fd))
+    cpu = None
+    if not args.no_cpu_baseline:
+        S = 256
+        sub = x_np[:S]
+        t0 = time.perf_counter()
+        oracle.forward(c_np, sub)
+        dt = time.perf_counter() - t0
+        cpu = {"value": S / dt / 1e6, "unit": "Mpoints/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": "%d uniform points of the workload, FP64 direct sum at N=256^3 (%.1f s)" % (S, dt)}
+
+    def fam_line(fam):
+        r = results[fam]
+        pts = M * world
+        return {
+            "value": pts / (r["ms_per_step"] * 1e-3) / 1e6,
+            "ms_per_step": r["ms_per_step"], "m": r["m"], "rel_l2_vs_oracle": r["rel_l2"],
+            "eval_only_mpoints_s": pts / (r["ms_eval_only"] * 1e-3) / 1e6,
+            "stages_ms": r["stages_ms"], "roofline": r["roofline"],
+            "fft_share": r["stages_ms"]["fft"] / max(sum(r["stages_ms"].values()), 1e-12),
+            "e2e": {"value": pts / (r["e2e_ms"] * 1e-3) / 1e6, "unit": "Mpoints/s",
+                    "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+            "gpu_launches": int(round(r["launches_per_step"] * args.steps)),
+            "clocks": r["clocks"],
+        }
+
+    main = fam_line("f64")
+    mixed = fam_line("f32")
+    line = {
+        "metric": "NFFT Mpoints/s at 256^3 (FP64 1e-12 vs mixed 1e-6); % of roofline",
+        "value": main["value"], "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "precision sweep: N=%d^3 gaussian(40) coefficients, M=%d points (half uniform, "
+                               "half gaussian std 0.02), sigma=2" % (N, M),
+                   "N": N, "M_per_gpu": M, "sigma": 2.0, "m_fp64": M_FP64, "m_mixed": M_MIXED,
+                   "step": "set_points + eval", "l2": "inputs larger than L2 (grid %.2f GB FP64), no flush" % ((2 * N) ** 3 * 16 / 1e9),
+                   "parallelism": "points sharded, no collective" if world > 1 else "single GPU"},
+        "rel_l2_vs_oracle": main["rel_l2_vs_oracle"],
+        "eval_only_mpoints_s": main["eval_only_mpoints_s"],
+        "stages_ms": main["stages_ms"], "fft_share": main["fft_share"],
+        "roofline": main["roofline"],
+        "e2e": main["e2e"],
+        "gpu_launches": main["gpu_launches"],
+        "clocks": main["clocks"],
+        "mixed": mixed,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank, world, local):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1605_01244_gb300 import workloads as wl
+    N = args.n
+    c_np = wl.gaussian_coeffs((N, N, N), 40.0, seed=0)
+    x_np = wl.mixed_points(args.points, 0.02, seed=100)
+    S = 64  # points per step: ~1 s of direct summation at N = 256^3
+    rng = wl.rng(5)
+    times = []
+    for it in range(args.warmup + args.steps):
+        idx = rng.choice(len(x_np), S, replace=False)
+        t0 = time.perf_counter()
+        oracle.forward(c_np, x_np[idx])
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    val = S / (ms * 1e-3) / 1e6
+    cores = oracle.num_threads()
+    print(json.dumps({
+        "impl": "reference", "metric": "NFFT Mpoints/s at 256^3 (FP64 1e-12 vs mixed 1e-6); % of roofline",
+        "value": val, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "precision sweep: N=%d^3 gaussian(40) coefficients, M=%d points (half uniform, "
+                               "half gaussian std 0.02), sigma=2" % (N, args.points), "N": N,
+                   "step": "FP64 direct sum (the oracle) over %d sampled points" % S},
+        "cpu_baseline": {"value": val, "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d random points of the workload per step" % S},
+        "e2e": {"value": val, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world, local)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

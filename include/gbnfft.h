@@ -1,0 +1,175 @@
+/*
+ * gbnfft -- 3D nonequispaced FFT (type-2 NFFT and its adjoint) for one GB300.
+ *
+ * The library evaluates the 3D truncated Fourier series of the INFFTM paper
+ * (Caliari & Zuccher, arXiv:1605.01244, eq. (fs) and the NFFT transform of
+ * Sec. 2.2.1, with the + sign of the physical series)
+ *
+ *     f_j = sum_{k in I_N} c_k exp(+2 pi i k . x_j),     j = 0..M-1,
+ *     I_N = [-N1/2, N1/2) x [-N2/2, N2/2) x [-N3/2, N3/2),
+ *
+ * at M arbitrary torus points x_j (any real coordinates; the series is
+ * 1-periodic, so they are wrapped onto [-1/2, 1/2)^3), its gradient
+ * (eq. (Lambda) in torus units) and its adjoint
+ *
+ *     h_k = sum_j f_j exp(-2 pi i k . x_j).
+ *
+ * The paper uses the NFFT as a black box with cost O(N log N + M |log eps|^3)
+ * (Sec. 1).  This library's approximation: deconvolve by the Fourier
+ * transform of a Kaiser-Bessel window and zero-pad into an oversampled grid
+ * of n_d >= sigma N_d points, one unnormalised inverse 3D FFT, then a
+ * (2m+1)^3-tap window sum per point.
+ *
+ * Data layout (all device pointers unless a name ends in _host):
+ *   c    : N1*N2*N3 complex values, row-major (i3 fastest), entry (i1,i2,i3)
+ *          holding k_d = i_d - N_d/2.  Complex = two interleaved reals
+ *          (re, im): double for the nfft3d_* family, float for nfft3f_*.
+ *   x    : M*3 doubles, row-major (x_j0, x_j1, x_j2), both families.
+ *   f    : M complex values (same real type as c).
+ *   grad : M*3 complex values, grad[3j+d] = d f_j / d x_{j,d}.
+ *
+ * Families: nfft3d_* computes in FP64 throughout.  nfft3f_* ("mixed") keeps
+ * the coordinate reduction and the deconvolution tables in FP64 and runs the
+ * grid, FFT, window sums and spreading in FP32.
+ *
+ * Ownership: the plan owns all device workspaces.  Pointers passed to a call
+ * are borrowed for the duration of the call (the work is enqueued on the
+ * plan's stream; the caller keeps the buffers alive until that stream has
+ * finished the work).  set_points copies what it needs from x.
+ *
+ * Errors: every call returns an int status: 0 OK, > 0 warning, < 0 error
+ * (NFFT3_ERR_*).  No call aborts, throws or prints.  Kernel faults surface
+ * as NFFT3_ERR_CUDA from the next call that synchronises (set_points, the
+ * _host calls, nfft3_sync).  A plan is used from one host thread and one
+ * stream at a time.
+ */
+#ifndef GBNFFT_H
+#define GBNFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nfft3_plan_s *nfft3_plan;
+
+enum {
+    NFFT3_OK = 0,
+    NFFT3_WARN_EPS = 1,        /* the requested eps is below what the plan's m reaches */
+    NFFT3_ERR_ARG = -1,        /* bad argument (size, null pointer, precision family) */
+    NFFT3_ERR_ALLOC = -2,      /* device allocation failed */
+    NFFT3_ERR_CUFFT = -3,      /* cuFFT plan or exec failed */
+    NFFT3_ERR_CUDA = -4,       /* CUDA launch or runtime error */
+    NFFT3_ERR_NO_POINTS = -5,  /* eval/adjoint before a successful set_points */
+    NFFT3_ERR_POINTS = -6,     /* a point coordinate is NaN or infinite */
+    NFFT3_ERR_TOO_LARGE = -7   /* a size exceeds the library's limits */
+};
+
+/*
+ * Create a plan.
+ *   N1,N2,N3 : even, >= 2 (paper Sec. 2: N_d even), each <= 4096.
+ *   M        : number of points, 0 <= M < 2^31.
+ *   m        : window cutoff, 1..8 (2m+1 taps per dimension); if m <= 0 it
+ *              is chosen from eps (smallest m whose relative l2 error
+ *              estimate 8 exp(-2 pi sqrt(1 - 1/sigma) (m + 1/2)) is <= eps;
+ *              the estimate bounds the measured error for flat spectra).
+ *              If m > 0, eps is only checked (warning if the estimate
+ *              exceeds it); eps <= 0 skips the check.
+ *   sigma    : oversampling factor >= 1.25 (<= 0 selects 2); n_d is the
+ *              smallest even integer >= sigma N_d with no prime factor > 7.
+ *   stream   : cudaStream_t to enqueue all work on (NULL = legacy stream).
+ * The plan is created on the device current at the call.
+ */
+int nfft3d_plan(nfft3_plan *out, int N1, int N2, int N3, int64_t M, int m,
+                double sigma, double eps, void *stream);
+int nfft3f_plan(nfft3_plan *out, int N1, int N2, int N3, int64_t M, int m,
+                double sigma, double eps, void *stream);
+
+/*
+ * Set the M points (device pointer x, M*3 doubles).  Each coordinate is
+ * wrapped onto [-1/2, 1/2) (the series is periodic; paper Sec. 2.2.1 uses
+ * mod(.,1)), reduced in FP64 to its first stencil node and a fractional
+ * offset, and the points are bucketed by grid tile.  Synchronises the
+ * plan's stream (it reads back a status word).  NaN/Inf coordinates give
+ * NFFT3_ERR_POINTS and leave the plan without points.
+ */
+int nfft3d_set_points(nfft3_plan p, const double *x);
+int nfft3f_set_points(nfft3_plan p, const double *x);
+
+/* f = A c  (type-2 NFFT).  c: N1*N2*N3 complex, f: M complex (overwritten). */
+int nfft3d_eval(nfft3_plan p, const double *c, double *f);
+int nfft3f_eval(nfft3_plan p, const float *c, float *f);
+
+/*
+ * f = A c and grad_d f = A (2 pi i k_d c), d = 1..3 (eq. (Lambda), torus
+ * units; physical units divide by b_d - a_d).  f may be NULL.
+ * grad: M*3 complex, grad[3j+d].
+ */
+int nfft3d_eval_grad(nfft3_plan p, const double *c, double *f, double *grad);
+int nfft3f_eval_grad(nfft3_plan p, const float *c, float *f, float *grad);
+
+/* c_out = A^H f  (type-1 adjoint): c_out[k] = sum_j f_j exp(-2 pi i k.x_j). */
+int nfft3d_adjoint(nfft3_plan p, const double *f, double *c_out);
+int nfft3f_adjoint(nfft3_plan p, const float *f, float *c_out);
+
+/*
+ * Host-buffer variants: copy x_host (M*3 doubles) and c_host (N^3 complex)
+ * to plan-owned device buffers, set the points, evaluate, copy f back into
+ * f_host (M complex) and synchronise.  Pinned host memory gives full copy
+ * bandwidth; pageable memory works but is slower.
+ */
+int nfft3d_eval_host(nfft3_plan p, const double *x_host, const double *c_host, double *f_host);
+int nfft3f_eval_host(nfft3_plan p, const double *x_host, const float *c_host, float *f_host);
+
+/* Release the plan and every device buffer it owns.  NULL is accepted. */
+int nfft3d_destroy(nfft3_plan p);
+int nfft3f_destroy(nfft3_plan p);
+
+/*
+ * Plan introspection.  Any output pointer may be NULL.
+ *   n[3]: oversampled sizes;  m: cutoff;  M: points;  prec: 64 or 32.
+ */
+int nfft3_plan_info(nfft3_plan p, int *n, int *m, int64_t *M, int *prec);
+
+/* Change the stream later calls enqueue on. */
+int nfft3_set_stream(nfft3_plan p, void *stream);
+
+/* Wait for the plan's stream and report any asynchronous CUDA error. */
+int nfft3_sync(nfft3_plan p);
+
+/* Static description of a status code. */
+const char *nfft3_error_string(int code);
+
+/*
+ * Stage timing.  While enabled, every call records CUDA events on the plan's
+ * stream around its stages; nfft3_timing_read waits for them and returns
+ * the summed milliseconds and call counts per stage (arrays of
+ * NFFT3_NSTAGES, NULL allowed) and the number of kernels this library
+ * enqueued since the last reset (cuFFT's internal kernels not counted).
+ * Timing adds no synchronisation to the calls themselves.
+ */
+enum {
+    NFFT3_STAGE_SET_POINTS = 0,  /* reduction + counting sort          */
+    NFFT3_STAGE_DECONV = 1,      /* deconvolve + zero-pad scatter      */
+    NFFT3_STAGE_FFT = 2,         /* oversampled inverse FFT (cuFFT)    */
+    NFFT3_STAGE_GATHER = 3,      /* window gather (value or gradient)  */
+    NFFT3_STAGE_SPREAD = 4,      /* adjoint: clear + spread            */
+    NFFT3_STAGE_FFT_FWD = 5,     /* adjoint: forward FFT (cuFFT)       */
+    NFFT3_STAGE_DECONV_ADJ = 6,  /* adjoint: deconvolve + gather of c  */
+    NFFT3_NSTAGES = 7
+};
+int nfft3_timing_enable(nfft3_plan p, int on);
+int nfft3_timing_read(nfft3_plan p, double *ms, int64_t *calls, int64_t *launches, int reset);
+
+/*
+ * m chosen for (eps, sigma) by the rule documented at nfft3d_plan
+ * (returns 1..8, or 8 when eps is below what m = 8 reaches).
+ */
+int nfft3_choose_m(double eps, double sigma);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBNFFT_H */

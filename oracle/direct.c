@@ -75,15 +75,23 @@ void oracle_forward_grad(int N1, int N2, int N3, const double *c, int64_t M,
                     double k2 = (double)(i2 - N2 / 2);
                     const double *row = c + 2 * ((int64_t)(i1 * N2 + i2) * N3);
                     double s0r = 0, s0i = 0, s3r = 0, s3i = 0;
-                    for (int i3 = 0; i3 < N3; i3++) {
-                        double k3 = (double)(i3 - N3 / 2);
-                        double cr = row[2 * i3], ci = row[2 * i3 + 1];
-                        double pr = cr * e3r[i3] - ci * e3i[i3];
-                        double pi = cr * e3i[i3] + ci * e3r[i3];
-                        s0r += pr;
-                        s0i += pi;
-                        s3r += k3 * pr;
-                        s3i += k3 * pi;
+                    if (grad) {
+                        for (int i3 = 0; i3 < N3; i3++) {
+                            double k3 = (double)(i3 - N3 / 2);
+                            double cr = row[2 * i3], ci = row[2 * i3 + 1];
+                            double pr = cr * e3r[i3] - ci * e3i[i3];
+                            double pi = cr * e3i[i3] + ci * e3r[i3];
+                            s0r += pr;
+                            s0i += pi;
+                            s3r += k3 * pr;
+                            s3i += k3 * pi;
+                        }
+                    } else { /* value only: the same s0 sums without the k3 weights */
+                        for (int i3 = 0; i3 < N3; i3++) {
+                            double cr = row[2 * i3], ci = row[2 * i3 + 1];
+                            s0r += cr * e3r[i3] - ci * e3i[i3];
+                            s0i += cr * e3i[i3] + ci * e3r[i3];
+                        }
                     }
                     double ar = s0r * e2r[i2] - s0i * e2i[i2];
                     double ai = s0r * e2i[i2] + s0i * e2r[i2];

@@ -1,0 +1,91 @@
+// Internal declarations shared by the gbnfft translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include "gbnfft.h"
+
+namespace gbnfft {
+
+constexpr int kMaxM = 8;       // largest window cutoff compiled in (2m+1 = 17 taps)
+constexpr int kTile = 8;       // grid tile edge (cells) used to bucket points
+
+template <typename R> struct Cplx;
+template <> struct Cplx<double> { using T = double2; };
+template <> struct Cplx<float> { using T = float2; };
+
+// Window constants for one dimension.  The window is the Kaiser-Bessel
+// function in grid units with half-width alpha = m + 1/2,
+//   phi(tau) = sinh(b sqrt(alpha^2 - tau^2)) / (pi sqrt(alpha^2 - tau^2)),
+// evaluated on the support -alpha < tau <= alpha and normalised to
+// phi(0) = 1 (the normalisation is folded into the deconvolution tables).
+template <typename R> struct Win {
+    R b;        // pi (2 - 1/sigma_d)
+    R inv_den;  // alpha / (1 - exp(-2 b alpha))
+    R ebal;     // exp(-b alpha)
+};
+
+// Sorted point data written by set_points.
+//   key[j] = (l0_1, l0_2, l0_3, original index); l0_d in [0, n_d) is the
+//   first stencil node (wrapped), the stencil is l0_d + {0..2m} mod n_d.
+//   s_d[j] in [0,1): tau of tap a is alpha - s_d - a.
+template <typename R> struct PointsView {
+    const int4 *key;
+    const R *s1, *s2, *s3;
+    int64_t M;
+};
+
+struct Grid3 {
+    int n1, n2, n3;
+};
+
+// ---- launchers implemented in kernels.cu (all enqueue on `st`) ------------
+
+template <typename R>
+cudaError_t launch_deconv_scatter(const typename Cplx<R>::T *c, int N1, int N2, int N3,
+                                  const R *D1, const R *D2, const R *D3, typename Cplx<R>::T *G,
+                                  Grid3 g, int with_grad, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_gather(const typename Cplx<R>::T *G, Grid3 g, int m, PointsView<R> pts,
+                          const Win<R> *w, typename Cplx<R>::T *f, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_gather_grad(const typename Cplx<R>::T *G4, Grid3 g, int m, PointsView<R> pts,
+                               const Win<R> *w, typename Cplx<R>::T *f, typename Cplx<R>::T *grad,
+                               cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_spread(const typename Cplx<R>::T *f, Grid3 g, int m, PointsView<R> pts,
+                          const Win<R> *w, typename Cplx<R>::T *H, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_deconv_gather(const typename Cplx<R>::T *H, Grid3 g, const R *D1, const R *D2,
+                                 const R *D3, int N1, int N2, int N3, typename Cplx<R>::T *c,
+                                 cudaStream_t st);
+
+// ---- launchers implemented in points.cu ------------------------------------
+
+struct PointsBuild {
+    int m;
+    Grid3 g;
+    int nt1, nt2, nt3;      // tiles per dimension
+    int64_t ntile;
+    int64_t M;
+    int *tile_count;        // ntile + 1 (last entry stays 0)
+    int *tile_start;        // ntile + 1
+    int *rank;              // M
+    int *scan_tmp;          // scan partials
+    int *status;            // device status word (bit 0: non-finite coordinate)
+};
+
+template <typename R>
+cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R *s2, R *s3,
+                          cudaStream_t st);
+
+size_t scan_tmp_ints(int64_t n);
+int scan_launches(int64_t n);   // kernels exclusive_scan enqueues for n entries
+
+}  // namespace gbnfft

@@ -1,0 +1,636 @@
+// C ABI of gbnfft: plans, tables, cuFFT, and the eval / eval_grad / adjoint
+// sequences.  Kernels live in kernels.cu and points.cu.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+using namespace gbnfft;
+
+constexpr int kTimingRecords = 64;
+constexpr int kTimingMarks = 4;
+
+struct nfft3_plan_s {
+    int prec;                 // 64 or 32
+    int N[3], n[3], m;
+    int64_t M;
+    double b[3];
+    cudaStream_t stream;
+    int sync_check;           // GBNFFT_SYNC_CHECK set: synchronise after every call
+    int fault;                // host-side fault injection (GBNFFT_FAULT)
+    int device;
+    // tables and grid
+    void *D[3];               // deconvolution factors, real type of the family
+    void *grid;               // n1 n2 n3 complex (x4 once eval_grad ran)
+    int grid_count;           // 1 or 4
+    cufftHandle fft1;
+    cufftHandle fft4;
+    int have_fft4;
+    // points
+    int points_ok;
+    int4 *key;
+    void *s[3];
+    PointsBuild pb;
+    // host-buffer staging (allocated on first _host call)
+    double *x_dev;
+    void *c_dev;
+    void *f_dev;
+    // stage timing (CUDA events on the plan's stream), enabled by nfft3_timing_enable
+    int timing;
+    int nrec;
+    cudaEvent_t ev[kTimingRecords][kTimingMarks];
+    int rec_kind[kTimingRecords];
+    int ev_ready[kTimingRecords];
+    double stage_ms[NFFT3_NSTAGES];
+    int64_t stage_calls[NFFT3_NSTAGES];
+    int64_t launches;         // kernels this library enqueued (cuFFT's own not counted)
+};
+
+namespace {
+
+enum { kFaultNone = 0, kFaultAlloc = 1, kFaultFftPlan = 2 };
+
+int read_fault_env() {
+    const char *v = std::getenv("GBNFFT_FAULT");
+    if (!v) return kFaultNone;
+    if (!std::strcmp(v, "alloc")) return kFaultAlloc;
+    if (!std::strcmp(v, "fft_plan")) return kFaultFftPlan;
+    return kFaultNone;
+}
+
+int dev_alloc(nfft3_plan p, void **ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (p->fault == kFaultAlloc) return NFFT3_ERR_ALLOC;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free allocation error
+        *ptr = nullptr;
+        return NFFT3_ERR_ALLOC;
+    }
+    return NFFT3_OK;
+}
+
+void dev_free(void *&ptr) {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? NFFT3_OK : NFFT3_ERR_CUDA; }
+
+// ---- stage timing ----------------------------------------------------------
+// A record holds up to kTimingMarks events of one call; stage i of the call
+// spans marks i..i+1.  Records are folded into stage_ms when the pool fills
+// or when nfft3_timing_read is called.
+enum { kRecSetPoints = 0, kRecEval = 1, kRecGrad = 2, kRecAdjoint = 3 };
+
+void fold_records(nfft3_plan p) {
+    for (int r = 0; r < p->nrec; ++r) {
+        cudaEventSynchronize(p->ev[r][kTimingMarks - 1]);
+        const int kind = p->rec_kind[r];
+        int first = 0, nst = 0;
+        if (kind == kRecSetPoints) first = NFFT3_STAGE_SET_POINTS, nst = 1;
+        if (kind == kRecEval || kind == kRecGrad) first = NFFT3_STAGE_DECONV, nst = 3;
+        if (kind == kRecAdjoint) first = NFFT3_STAGE_SPREAD, nst = 3;
+        for (int i = 0; i < nst; ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p->ev[r][i], p->ev[r][i + 1]) == cudaSuccess) {
+                p->stage_ms[first + i] += ms;
+                p->stage_calls[first + i] += 1;
+            }
+        }
+    }
+    p->nrec = 0;
+    cudaGetLastError();
+}
+
+// start a record; returns its index or -1 when timing is off
+int rec_begin(nfft3_plan p, int kind) {
+    if (!p->timing) return -1;
+    if (p->nrec == kTimingRecords) fold_records(p);
+    const int r = p->nrec++;
+    if (!p->ev_ready[r]) {
+        for (int i = 0; i < kTimingMarks; ++i) cudaEventCreate(&p->ev[r][i]);
+        p->ev_ready[r] = 1;
+    }
+    p->rec_kind[r] = kind;
+    cudaEventRecord(p->ev[r][0], p->stream);
+    return r;
+}
+
+void rec_mark(nfft3_plan p, int r, int i) {
+    if (r >= 0) cudaEventRecord(p->ev[r][i], p->stream);
+}
+
+// fill the marks a call did not use, so that every record ends at mark kTimingMarks-1
+void rec_end(nfft3_plan p, int r, int last_used) {
+    if (r < 0) return;
+    for (int i = last_used + 1; i < kTimingMarks; ++i) cudaEventRecord(p->ev[r][i], p->stream);
+}
+
+// Modified Bessel function I0 by its power series sum_k ((x/2)^{2k} / (k!)^2);
+// all terms are positive, so the sum is accurate to rounding for the
+// arguments used here (x < 60).
+double bessel_i0(double x) {
+    const double t = 0.25 * x * x;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 1000; ++k) {
+        term *= t / ((double)k * (double)k);
+        sum += term;
+        if (term < 1e-17 * sum) break;
+    }
+    return sum;
+}
+
+bool small_primes_only(int v) {
+    for (int p : {2, 3, 5, 7})
+        while (v % p == 0) v /= p;
+    return v == 1;
+}
+
+int oversampled_size(int N, double sigma) {
+    int n = (int)std::ceil(sigma * (double)N - 1e-9);
+    if (n < N) n = N;
+    if (n % 2) ++n;
+    while (!small_primes_only(n)) n += 2;
+    return n;
+}
+
+// relative l2 error estimate of the window at cutoff m and oversampling sigma
+double error_estimate(int m, double sigma) {
+    return 8.0 * std::exp(-2.0 * M_PI * std::sqrt(1.0 - 1.0 / sigma) * (m + 0.5));
+}
+
+template <typename R> Win<R> make_win(double b, int m) {
+    const double al = m + 0.5;
+    Win<R> w;
+    w.b = (R)b;
+    w.inv_den = (R)(al / (1.0 - std::exp(-2.0 * b * al)));
+    w.ebal = (R)std::exp(-b * al);
+    return w;
+}
+
+int finish(nfft3_plan p, int status) {
+    if (status == NFFT3_OK && p && p->sync_check) {
+        if (cudaStreamSynchronize(p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
+        if (cudaGetLastError() != cudaSuccess) return NFFT3_ERR_CUDA;
+    }
+    return status;
+}
+
+void release(nfft3_plan p) {
+    if (!p) return;
+    for (int d = 0; d < 3; ++d) {
+        dev_free(p->D[d]);
+        dev_free(p->s[d]);
+    }
+    dev_free(p->grid);
+    void *k = p->key;
+    dev_free(k);
+    void *v;
+    v = p->pb.tile_count; dev_free(v);
+    v = p->pb.tile_start; dev_free(v);
+    v = p->pb.rank; dev_free(v);
+    v = p->pb.scan_tmp; dev_free(v);
+    v = p->pb.status; dev_free(v);
+    v = p->x_dev; dev_free(v);
+    dev_free(p->c_dev);
+    dev_free(p->f_dev);
+    if (p->fft1) cufftDestroy(p->fft1);
+    if (p->have_fft4) cufftDestroy(p->fft4);
+    for (int r = 0; r < kTimingRecords; ++r)
+        if (p->ev_ready[r])
+            for (int i = 0; i < kTimingMarks; ++i) cudaEventDestroy(p->ev[r][i]);
+    delete p;
+}
+
+int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int m, double sigma,
+              double eps, void *stream) {
+    if (!out) return NFFT3_ERR_ARG;
+    *out = nullptr;
+    const int Ns[3] = {N1, N2, N3};
+    for (int d = 0; d < 3; ++d) {
+        if (Ns[d] < 2 || Ns[d] % 2) return NFFT3_ERR_ARG;
+        if (Ns[d] > 4096) return NFFT3_ERR_TOO_LARGE;
+    }
+    if (M < 0) return NFFT3_ERR_ARG;
+    if (M >= ((int64_t)1 << 31)) return NFFT3_ERR_TOO_LARGE;
+    if (sigma <= 0) sigma = 2.0;
+    if (!(sigma >= 1.25) || !(sigma <= 8.0)) return NFFT3_ERR_ARG;
+    if (m > kMaxM) return NFFT3_ERR_ARG;
+    int warn = NFFT3_OK;
+    if (m <= 0) {
+        if (!(eps > 0)) return NFFT3_ERR_ARG;
+        m = nfft3_choose_m(eps, sigma);
+        if (error_estimate(m, sigma) > eps) warn = NFFT3_WARN_EPS;
+    } else if (eps > 0 && error_estimate(m, sigma) > eps) {
+        warn = NFFT3_WARN_EPS;
+    }
+
+    nfft3_plan p = new (std::nothrow) nfft3_plan_s;
+    if (!p) return NFFT3_ERR_ALLOC;
+    std::memset(p, 0, sizeof(*p));
+    p->prec = prec;
+    p->m = m;
+    p->M = M;
+    p->stream = (cudaStream_t)stream;
+    p->fault = read_fault_env();
+    p->sync_check = std::getenv("GBNFFT_SYNC_CHECK") != nullptr;
+    cudaGetDevice(&p->device);
+    for (int d = 0; d < 3; ++d) {
+        p->N[d] = Ns[d];
+        p->n[d] = oversampled_size(Ns[d], sigma);
+        p->b[d] = M_PI * (2.0 - (double)Ns[d] / (double)p->n[d]);
+    }
+    const size_t rs = prec == 64 ? sizeof(double) : sizeof(float);
+    int st = NFFT3_OK;
+
+    // deconvolution tables: D_d[i] = (-1)^k phi(0) / Phi(k / n_d), k = i - N_d/2,
+    // Phi(nu) = I0(alpha sqrt(b^2 - (2 pi nu)^2)), phi(0) = sinh(b alpha) / (pi alpha).
+    const double al = m + 0.5;
+    for (int d = 0; d < 3 && st == NFFT3_OK; ++d) {
+        const int Nd = p->N[d];
+        double *h = (double *)std::malloc(sizeof(double) * Nd);
+        float *hf = (float *)std::malloc(sizeof(float) * Nd);
+        if (!h || !hf) {
+            std::free(h);
+            std::free(hf);
+            st = NFFT3_ERR_ALLOC;
+            break;
+        }
+        const double b = p->b[d];
+        const double phi0 = std::sinh(b * al) / (M_PI * al);
+        for (int i = 0; i < Nd; ++i) {
+            const int k = i - Nd / 2;
+            const double nu = 2.0 * M_PI * (double)k / (double)p->n[d];
+            const double Phi = bessel_i0(al * std::sqrt(b * b - nu * nu));
+            h[i] = ((k & 1) ? -1.0 : 1.0) * phi0 / Phi;
+            hf[i] = (float)h[i];
+        }
+        st = dev_alloc(p, &p->D[d], rs * Nd);
+        if (st == NFFT3_OK)
+            st = cuda_status(cudaMemcpy(p->D[d], prec == 64 ? (void *)h : (void *)hf, rs * Nd,
+                                        cudaMemcpyHostToDevice));
+        std::free(h);
+        std::free(hf);
+    }
+    const int64_t nn = (int64_t)p->n[0] * p->n[1] * p->n[2];
+    if (st == NFFT3_OK) {
+        p->grid_count = 1;
+        st = dev_alloc(p, &p->grid, 2 * rs * nn);
+    }
+    if (st == NFFT3_OK) {
+        if (p->fault == kFaultFftPlan) {
+            st = NFFT3_ERR_CUFFT;
+        } else if (cufftPlan3d(&p->fft1, p->n[0], p->n[1], p->n[2],
+                               prec == 64 ? CUFFT_Z2Z : CUFFT_C2C) != CUFFT_SUCCESS) {
+            p->fft1 = 0;
+            st = NFFT3_ERR_CUFFT;
+        } else if (cufftSetStream(p->fft1, p->stream) != CUFFT_SUCCESS) {
+            st = NFFT3_ERR_CUFFT;
+        }
+    }
+    // points
+    if (st == NFFT3_OK) {
+        PointsBuild &pb = p->pb;
+        pb.m = m;
+        pb.g = Grid3{p->n[0], p->n[1], p->n[2]};
+        pb.nt1 = (p->n[0] + kTile - 1) / kTile;
+        pb.nt2 = (p->n[1] + kTile - 1) / kTile;
+        pb.nt3 = (p->n[2] + kTile - 1) / kTile;
+        pb.ntile = (int64_t)pb.nt1 * pb.nt2 * pb.nt3;
+        pb.M = M;
+        void *v;
+        st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1));
+        pb.tile_count = (int *)v;
+        if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1)), pb.tile_start = (int *)v;
+        if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (M + 1)), pb.rank = (int *)v;
+        if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * scan_tmp_ints(pb.ntile + 1)), pb.scan_tmp = (int *)v;
+        if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int)), pb.status = (int *)v;
+        if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int4) * (M + 1)), p->key = (int4 *)v;
+        for (int d = 0; d < 3 && st == NFFT3_OK; ++d) st = dev_alloc(p, &p->s[d], rs * (M + 1));
+    }
+    if (st != NFFT3_OK) {
+        release(p);
+        return st;
+    }
+    *out = p;
+    return warn;
+}
+
+template <typename R> PointsView<R> points_view(nfft3_plan p) {
+    PointsView<R> v;
+    v.key = p->key;
+    v.s1 = (const R *)p->s[0];
+    v.s2 = (const R *)p->s[1];
+    v.s3 = (const R *)p->s[2];
+    v.M = p->M;
+    return v;
+}
+
+template <typename R> void wins(nfft3_plan p, Win<R> w[3]) {
+    for (int d = 0; d < 3; ++d) w[d] = make_win<R>(p->b[d], p->m);
+}
+
+int exec_fft(cufftHandle h, void *data, int prec, int direction) {
+    cufftResult r;
+    if (prec == 64)
+        r = cufftExecZ2Z(h, (cufftDoubleComplex *)data, (cufftDoubleComplex *)data, direction);
+    else
+        r = cufftExecC2C(h, (cufftComplex *)data, (cufftComplex *)data, direction);
+    return r == CUFFT_SUCCESS ? NFFT3_OK : NFFT3_ERR_CUFFT;
+}
+
+int set_points_impl(nfft3_plan p, const double *x, int prec) {
+    if (!p || p->prec != prec) return NFFT3_ERR_ARG;
+    if (!x && p->M > 0) return NFFT3_ERR_ARG;
+    p->points_ok = 0;
+    const int rec = rec_begin(p, kRecSetPoints);
+    cudaError_t e;
+    if (prec == 64)
+        e = launch_points<double>(x, p->pb, p->key, (double *)p->s[0], (double *)p->s[1],
+                                  (double *)p->s[2], p->stream);
+    else
+        e = launch_points<float>(x, p->pb, p->key, (float *)p->s[0], (float *)p->s[1],
+                                 (float *)p->s[2], p->stream);
+    if (e != cudaSuccess) return NFFT3_ERR_CUDA;
+    p->launches += p->M > 0 ? 2 + scan_launches(p->pb.ntile + 1) : scan_launches(p->pb.ntile + 1);
+    rec_mark(p, rec, 1);
+    rec_end(p, rec, 1);
+    int status = 0;
+    if (cudaMemcpyAsync(&status, p->pb.status, sizeof(int), cudaMemcpyDeviceToHost, p->stream) !=
+        cudaSuccess)
+        return NFFT3_ERR_CUDA;
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
+    if (status & 1) return NFFT3_ERR_POINTS;
+    p->points_ok = 1;
+    return NFFT3_OK;
+}
+
+template <typename R> int eval_impl(nfft3_plan p, const R *c, R *f) {
+    using C = typename Cplx<R>::T;
+    constexpr int prec = sizeof(R) == 8 ? 64 : 32;
+    if (!p || p->prec != prec) return NFFT3_ERR_ARG;
+    if (!p->points_ok) return NFFT3_ERR_NO_POINTS;
+    if (p->M > 0 && (!c || !f)) return NFFT3_ERR_ARG;
+    if (p->M == 0) return NFFT3_OK;
+    const Grid3 g{p->n[0], p->n[1], p->n[2]};
+    C *G = (C *)p->grid;
+    const int rec = rec_begin(p, kRecEval);
+    cudaError_t e = launch_deconv_scatter<R>((const C *)c, p->N[0], p->N[1], p->N[2],
+                                             (const R *)p->D[0], (const R *)p->D[1],
+                                             (const R *)p->D[2], G, g, 0, p->stream);
+    if (e != cudaSuccess) return NFFT3_ERR_CUDA;
+    rec_mark(p, rec, 1);
+    int st = exec_fft(p->fft1, G, prec, CUFFT_INVERSE);
+    if (st != NFFT3_OK) return st;
+    rec_mark(p, rec, 2);
+    Win<R> w[3];
+    wins<R>(p, w);
+    e = launch_gather<R>(G, g, p->m, points_view<R>(p), w, (C *)f, p->stream);
+    rec_mark(p, rec, 3);
+    p->launches += 2;
+    return finish(p, cuda_status(e));
+}
+
+template <typename R> int ensure_grad_grids(nfft3_plan p) {
+    constexpr int prec = sizeof(R) == 8 ? 64 : 32;
+    if (p->grid_count == 4 && p->have_fft4) return NFFT3_OK;
+    const int64_t nn = (int64_t)p->n[0] * p->n[1] * p->n[2];
+    void *g4 = nullptr;
+    int st = dev_alloc(p, &g4, 2 * sizeof(R) * nn * 4);
+    if (st != NFFT3_OK) return st;
+    int dims[3] = {p->n[0], p->n[1], p->n[2]};
+    cufftHandle h;
+    if (p->fault == kFaultFftPlan ||
+        cufftPlanMany(&h, 3, dims, nullptr, 1, (int)0, nullptr, 1, 0,
+                      prec == 64 ? CUFFT_Z2Z : CUFFT_C2C, 4) != CUFFT_SUCCESS) {
+        cudaFree(g4);
+        return NFFT3_ERR_CUFFT;
+    }
+    cufftSetStream(h, p->stream);
+    // the batched plan uses the default layout: distance n1 n2 n3 between transforms
+    dev_free(p->grid);
+    p->grid = g4;
+    p->grid_count = 4;
+    p->fft4 = h;
+    p->have_fft4 = 1;
+    return NFFT3_OK;
+}
+
+template <typename R> int eval_grad_impl(nfft3_plan p, const R *c, R *f, R *grad) {
+    using C = typename Cplx<R>::T;
+    constexpr int prec = sizeof(R) == 8 ? 64 : 32;
+    if (!p || p->prec != prec) return NFFT3_ERR_ARG;
+    if (!p->points_ok) return NFFT3_ERR_NO_POINTS;
+    if (p->M > 0 && (!c || !grad)) return NFFT3_ERR_ARG;
+    if (p->M == 0) return NFFT3_OK;
+    int st = ensure_grad_grids<R>(p);
+    if (st != NFFT3_OK) return st;
+    const Grid3 g{p->n[0], p->n[1], p->n[2]};
+    C *G = (C *)p->grid;
+    const int rec = rec_begin(p, kRecGrad);
+    cudaError_t e = launch_deconv_scatter<R>((const C *)c, p->N[0], p->N[1], p->N[2],
+                                             (const R *)p->D[0], (const R *)p->D[1],
+                                             (const R *)p->D[2], G, g, 1, p->stream);
+    if (e != cudaSuccess) return NFFT3_ERR_CUDA;
+    rec_mark(p, rec, 1);
+    st = exec_fft(p->fft4, G, prec, CUFFT_INVERSE);
+    if (st != NFFT3_OK) return st;
+    rec_mark(p, rec, 2);
+    Win<R> w[3];
+    wins<R>(p, w);
+    e = launch_gather_grad<R>(G, g, p->m, points_view<R>(p), w, (C *)f, (C *)grad, p->stream);
+    rec_mark(p, rec, 3);
+    p->launches += 2;
+    return finish(p, cuda_status(e));
+}
+
+template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
+    using C = typename Cplx<R>::T;
+    constexpr int prec = sizeof(R) == 8 ? 64 : 32;
+    if (!p || p->prec != prec) return NFFT3_ERR_ARG;
+    if (!p->points_ok) return NFFT3_ERR_NO_POINTS;
+    if (!c_out || (p->M > 0 && !f)) return NFFT3_ERR_ARG;
+    const Grid3 g{p->n[0], p->n[1], p->n[2]};
+    const int64_t nn = (int64_t)g.n1 * g.n2 * g.n3;
+    C *H = (C *)p->grid;
+    const int rec = rec_begin(p, kRecAdjoint);
+    cudaError_t e = cudaMemsetAsync(H, 0, sizeof(C) * nn, p->stream);
+    if (e != cudaSuccess) return NFFT3_ERR_CUDA;
+    Win<R> w[3];
+    wins<R>(p, w);
+    e = launch_spread<R>((const C *)f, g, p->m, points_view<R>(p), w, H, p->stream);
+    if (e != cudaSuccess) return NFFT3_ERR_CUDA;
+    rec_mark(p, rec, 1);
+    int st = exec_fft(p->fft1, H, prec, CUFFT_FORWARD);
+    if (st != NFFT3_OK) return st;
+    rec_mark(p, rec, 2);
+    e = launch_deconv_gather<R>(H, g, (const R *)p->D[0], (const R *)p->D[1], (const R *)p->D[2],
+                                p->N[0], p->N[1], p->N[2], (C *)c_out, p->stream);
+    rec_mark(p, rec, 3);
+    p->launches += p->M > 0 ? 2 : 1;
+    return finish(p, cuda_status(e));
+}
+
+template <typename R> int eval_host_impl(nfft3_plan p, const double *x_host, const R *c_host, R *f_host) {
+    constexpr int prec = sizeof(R) == 8 ? 64 : 32;
+    if (!p || p->prec != prec) return NFFT3_ERR_ARG;
+    if (!c_host || (p->M > 0 && (!x_host || !f_host))) return NFFT3_ERR_ARG;
+    const int64_t NN = (int64_t)p->N[0] * p->N[1] * p->N[2];
+    int st = NFFT3_OK;
+    if (!p->x_dev) {
+        void *v = nullptr;
+        st = dev_alloc(p, &v, sizeof(double) * 3 * (p->M + 1));
+        p->x_dev = (double *)v;
+        if (st == NFFT3_OK) st = dev_alloc(p, &p->c_dev, 2 * sizeof(R) * NN);
+        if (st == NFFT3_OK) st = dev_alloc(p, &p->f_dev, 2 * sizeof(R) * (p->M + 1));
+        if (st != NFFT3_OK) {
+            void *x = p->x_dev;
+            dev_free(x);
+            p->x_dev = nullptr;
+            dev_free(p->c_dev);
+            dev_free(p->f_dev);
+            return st;
+        }
+    }
+    if (p->M > 0 &&
+        cudaMemcpyAsync(p->x_dev, x_host, sizeof(double) * 3 * p->M, cudaMemcpyHostToDevice,
+                        p->stream) != cudaSuccess)
+        return NFFT3_ERR_CUDA;
+    if (cudaMemcpyAsync(p->c_dev, c_host, 2 * sizeof(R) * NN, cudaMemcpyHostToDevice, p->stream) !=
+        cudaSuccess)
+        return NFFT3_ERR_CUDA;
+    st = set_points_impl(p, p->x_dev, prec);
+    if (st != NFFT3_OK) return st;
+    st = eval_impl<R>(p, (const R *)p->c_dev, (R *)p->f_dev);
+    if (st < 0) return st;
+    if (p->M > 0 &&
+        cudaMemcpyAsync(f_host, p->f_dev, 2 * sizeof(R) * p->M, cudaMemcpyDeviceToHost, p->stream) !=
+            cudaSuccess)
+        return NFFT3_ERR_CUDA;
+    return cudaStreamSynchronize(p->stream) == cudaSuccess ? NFFT3_OK : NFFT3_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nfft3_choose_m(double eps, double sigma) {
+    if (sigma <= 0) sigma = 2.0;
+    if (!(sigma > 1.0)) return kMaxM;
+    for (int m = 1; m <= kMaxM; ++m)
+        if (error_estimate(m, sigma) <= eps) return m;
+    return kMaxM;
+}
+
+int nfft3d_plan(nfft3_plan *out, int N1, int N2, int N3, int64_t M, int m, double sigma,
+                double eps, void *stream) {
+    return make_plan(out, 64, N1, N2, N3, M, m, sigma, eps, stream);
+}
+int nfft3f_plan(nfft3_plan *out, int N1, int N2, int N3, int64_t M, int m, double sigma,
+                double eps, void *stream) {
+    return make_plan(out, 32, N1, N2, N3, M, m, sigma, eps, stream);
+}
+
+int nfft3d_set_points(nfft3_plan p, const double *x) { return finish(p, set_points_impl(p, x, 64)); }
+int nfft3f_set_points(nfft3_plan p, const double *x) { return finish(p, set_points_impl(p, x, 32)); }
+
+int nfft3d_eval(nfft3_plan p, const double *c, double *f) { return eval_impl<double>(p, c, f); }
+int nfft3f_eval(nfft3_plan p, const float *c, float *f) { return eval_impl<float>(p, c, f); }
+
+int nfft3d_eval_grad(nfft3_plan p, const double *c, double *f, double *grad) {
+    return eval_grad_impl<double>(p, c, f, grad);
+}
+int nfft3f_eval_grad(nfft3_plan p, const float *c, float *f, float *grad) {
+    return eval_grad_impl<float>(p, c, f, grad);
+}
+
+int nfft3d_adjoint(nfft3_plan p, const double *f, double *c_out) {
+    return adjoint_impl<double>(p, f, c_out);
+}
+int nfft3f_adjoint(nfft3_plan p, const float *f, float *c_out) {
+    return adjoint_impl<float>(p, f, c_out);
+}
+
+int nfft3d_eval_host(nfft3_plan p, const double *x_host, const double *c_host, double *f_host) {
+    return eval_host_impl<double>(p, x_host, c_host, f_host);
+}
+int nfft3f_eval_host(nfft3_plan p, const double *x_host, const float *c_host, float *f_host) {
+    return eval_host_impl<float>(p, x_host, c_host, f_host);
+}
+
+int nfft3d_destroy(nfft3_plan p) {
+    if (p && p->prec != 64) return NFFT3_ERR_ARG;
+    release(p);
+    return NFFT3_OK;
+}
+int nfft3f_destroy(nfft3_plan p) {
+    if (p && p->prec != 32) return NFFT3_ERR_ARG;
+    release(p);
+    return NFFT3_OK;
+}
+
+int nfft3_plan_info(nfft3_plan p, int *n, int *m, int64_t *M, int *prec) {
+    if (!p) return NFFT3_ERR_ARG;
+    if (n)
+        for (int d = 0; d < 3; ++d) n[d] = p->n[d];
+    if (m) *m = p->m;
+    if (M) *M = p->M;
+    if (prec) *prec = p->prec;
+    return NFFT3_OK;
+}
+
+int nfft3_set_stream(nfft3_plan p, void *stream) {
+    if (!p) return NFFT3_ERR_ARG;
+    p->stream = (cudaStream_t)stream;
+    if (p->fft1 && cufftSetStream(p->fft1, p->stream) != CUFFT_SUCCESS) return NFFT3_ERR_CUFFT;
+    if (p->have_fft4 && cufftSetStream(p->fft4, p->stream) != CUFFT_SUCCESS) return NFFT3_ERR_CUFFT;
+    return NFFT3_OK;
+}
+
+int nfft3_sync(nfft3_plan p) {
+    if (!p) return NFFT3_ERR_ARG;
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? NFFT3_OK : NFFT3_ERR_CUDA;
+}
+
+int nfft3_timing_enable(nfft3_plan p, int on) {
+    if (!p) return NFFT3_ERR_ARG;
+    if (!on && p->nrec) fold_records(p);
+    p->timing = on ? 1 : 0;
+    return NFFT3_OK;
+}
+
+int nfft3_timing_read(nfft3_plan p, double *ms, int64_t *calls, int64_t *launches, int reset) {
+    if (!p) return NFFT3_ERR_ARG;
+    fold_records(p);
+    for (int i = 0; i < NFFT3_NSTAGES; ++i) {
+        if (ms) ms[i] = p->stage_ms[i];
+        if (calls) calls[i] = p->stage_calls[i];
+    }
+    if (launches) *launches = p->launches;
+    if (reset) {
+        for (int i = 0; i < NFFT3_NSTAGES; ++i) p->stage_ms[i] = 0.0, p->stage_calls[i] = 0;
+        p->launches = 0;
+    }
+    return NFFT3_OK;
+}
+
+const char *nfft3_error_string(int code) {
+    switch (code) {
+        case NFFT3_OK: return "ok";
+        case NFFT3_WARN_EPS: return "warning: requested eps is below the estimate for this m";
+        case NFFT3_ERR_ARG: return "invalid argument";
+        case NFFT3_ERR_ALLOC: return "device allocation failed";
+        case NFFT3_ERR_CUFFT: return "cuFFT error";
+        case NFFT3_ERR_CUDA: return "CUDA error";
+        case NFFT3_ERR_NO_POINTS: return "no points set";
+        case NFFT3_ERR_POINTS: return "non-finite point coordinate";
+        case NFFT3_ERR_TOO_LARGE: return "size exceeds library limits";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

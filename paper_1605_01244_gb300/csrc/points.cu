@@ -1,0 +1,212 @@
+// set_points: FP64 coordinate reduction and counting sort of the points by
+// grid tile.
+#include "internal.cuh"
+
+namespace gbnfft {
+namespace {
+
+// Reduction of one coordinate (FP64):
+//   xw = x - floor(x + 1/2)                 (wrap onto [-1/2, 1/2); the series is periodic)
+//   u  = n (xw + 1/2)                       (grid units; grid node l sits at x = -1/2 + l/n)
+//   v  = u - alpha, l0 = ceil(v), s = l0 - v in [0, 1)
+// The stencil l0 + {0..2m} holds exactly the nodes l with -alpha < u - l <= alpha.
+// l0 is returned wrapped into [0, n).  Non-finite x is replaced by 0 and flagged.
+struct Reduced {
+    int l0;
+    double s;
+};
+
+__device__ __forceinline__ Reduced reduce_coord(double x, int n, int m, int *status) {
+    if (!isfinite(x)) {
+        atomicOr(status, 1);
+        x = 0.0;
+    }
+    const double xw = x - floor(x + 0.5);
+    const double u = (double)n * (xw + 0.5);
+    const double v = u - ((double)m + 0.5);
+    const double l0 = ceil(v);
+    Reduced r;
+    r.s = l0 - v;
+    if (r.s >= 1.0) r.s = 0.0;  // cannot happen for finite v; keeps s in [0, 1) regardless
+    long long li = (long long)l0 % n;
+    if (li < 0) li += n;
+    r.l0 = (int)li;
+    return r;
+}
+
+// tile of a stencil: the tile holding its centre node l0 + m (mod n)
+__device__ __forceinline__ int tile_coord(int l0, int m, int n) {
+    int c = l0 + m;
+    while (c >= n) c -= n;
+    return c / kTile;
+}
+
+__global__ void points_count_kernel(const double *__restrict__ x, PointsBuild pb) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < pb.M;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const Reduced r1 = reduce_coord(x[3 * j + 0], pb.g.n1, pb.m, pb.status);
+        const Reduced r2 = reduce_coord(x[3 * j + 1], pb.g.n2, pb.m, pb.status);
+        const Reduced r3 = reduce_coord(x[3 * j + 2], pb.g.n3, pb.m, pb.status);
+        const int t1 = tile_coord(r1.l0, pb.m, pb.g.n1);
+        const int t2 = tile_coord(r2.l0, pb.m, pb.g.n2);
+        const int t3 = tile_coord(r3.l0, pb.m, pb.g.n3);
+        const int64_t t = ((int64_t)t1 * pb.nt2 + t2) * pb.nt3 + t3;
+        pb.rank[j] = atomicAdd(&pb.tile_count[t], 1);
+    }
+}
+
+template <typename R>
+__global__ void points_scatter_kernel(const double *__restrict__ x, PointsBuild pb,
+                                      int4 *__restrict__ key, R *__restrict__ s1,
+                                      R *__restrict__ s2, R *__restrict__ s3) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < pb.M;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const Reduced r1 = reduce_coord(x[3 * j + 0], pb.g.n1, pb.m, pb.status);
+        const Reduced r2 = reduce_coord(x[3 * j + 1], pb.g.n2, pb.m, pb.status);
+        const Reduced r3 = reduce_coord(x[3 * j + 2], pb.g.n3, pb.m, pb.status);
+        const int t1 = tile_coord(r1.l0, pb.m, pb.g.n1);
+        const int t2 = tile_coord(r2.l0, pb.m, pb.g.n2);
+        const int t3 = tile_coord(r3.l0, pb.m, pb.g.n3);
+        const int64_t t = ((int64_t)t1 * pb.nt2 + t2) * pb.nt3 + t3;
+        const int64_t pos = (int64_t)pb.tile_start[t] + pb.rank[j];
+        key[pos] = make_int4(r1.l0, r2.l0, r3.l0, (int)j);
+        s1[pos] = (R)r1.s;
+        s2[pos] = (R)r2.s;
+        s3[pos] = (R)r3.s;
+    }
+}
+
+// ---- exclusive scan (three phases, recursive over block sums) -------------
+
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) >= o) v += t;
+    }
+    return v;
+}
+
+// exclusive scan of `in` (n entries) into `out` per chunk of kScanChunk;
+// chunk totals go to bsum (if non-null).
+__global__ void __launch_bounds__(kScanThreads) scan_chunk_kernel(const int *__restrict__ in,
+                                                                  int *__restrict__ out, int64_t n,
+                                                                  int *__restrict__ bsum) {
+    __shared__ int warp_tot[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int local = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t idx = base + i;
+        v[i] = idx < n ? in[idx] : 0;
+        local += v[i];
+    }
+    const int incl = warp_incl_scan(local);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+        t = warp_incl_scan(t);
+        if (lane < kScanThreads / 32) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    int run = incl - local + (wid > 0 ? warp_tot[wid - 1] : 0);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t idx = base + i;
+        if (idx < n) out[idx] = run;
+        run += v[i];
+    }
+    if (bsum && threadIdx.x == kScanThreads - 1) bsum[blockIdx.x] = run;
+}
+
+__global__ void scan_add_kernel(int *__restrict__ out, int64_t n, const int *__restrict__ boff) {
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+    const int add = boff[blockIdx.x];
+    for (int i = threadIdx.x; i < kScanChunk; i += blockDim.x) {
+        const int64_t idx = base + i;
+        if (idx < n) out[idx] += add;
+    }
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Exclusive scan of n ints; tmp must hold scan_tmp_ints(n) ints.
+cudaError_t exclusive_scan(const int *in, int *out, int64_t n, int *tmp, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t nb = ceil_div(n, kScanChunk);
+    if (nb == 1) {
+        scan_chunk_kernel<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
+        return cudaGetLastError();
+    }
+    int *bsum = tmp;
+    int *boff = tmp + nb;
+    scan_chunk_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, bsum);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = exclusive_scan(bsum, boff, nb, tmp + 2 * nb, st);
+    if (e != cudaSuccess) return e;
+    scan_add_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(out, n, boff);
+    return cudaGetLastError();
+}
+
+int point_blocks(int64_t M) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t want = ceil_div(M, 256);
+    int64_t cap = (int64_t)sms * 8;
+    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+}  // namespace
+
+size_t scan_tmp_ints(int64_t n) {
+    size_t tot = 0;
+    while (n > kScanChunk) {
+        const int64_t nb = ceil_div(n, kScanChunk);
+        tot += 2 * nb;
+        n = nb;
+    }
+    return tot + 1;
+}
+
+int scan_launches(int64_t n) {
+    if (n <= 0) return 0;
+    const int64_t nb = ceil_div(n, kScanChunk);
+    return nb == 1 ? 1 : 2 + scan_launches(nb);
+}
+
+template <typename R>
+cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R *s2, R *s3,
+                          cudaStream_t st) {
+    // tile_count has ntile + 1 entries; the extra zero makes tile_start[ntile] = M.
+    cudaError_t e = cudaMemsetAsync(pb.tile_count, 0, sizeof(int) * (pb.ntile + 1), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(pb.status, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    if (pb.M > 0) {
+        points_count_kernel<<<point_blocks(pb.M), 256, 0, st>>>(x, pb);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    e = exclusive_scan(pb.tile_count, pb.tile_start, pb.ntile + 1, pb.scan_tmp, st);
+    if (e != cudaSuccess) return e;
+    if (pb.M > 0) {
+        points_scatter_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(x, pb, key, s1, s2, s3);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template cudaError_t launch_points<double>(const double *, PointsBuild &, int4 *, double *,
+                                           double *, double *, cudaStream_t);
+template cudaError_t launch_points<float>(const double *, PointsBuild &, int4 *, float *, float *,
+                                          float *, cudaStream_t);
+
+}  // namespace gbnfft

@@ -1,0 +1,228 @@
+"""Parity of the CUDA NFFT (through the C ABI) against the CPU oracle.
+
+Two references:
+* ``oracle.forward / forward_grad / adjoint`` -- the FP64 direct sums (the
+  definition, paper eq. (fs)/(Fs), eq. (Lambda)); the gate is relative l2
+  <= 1e-12 (FP64 family) and <= 1e-6 (mixed family);
+* ``oracle.nfft_cpu`` -- the same approximation restated in numpy; the
+  FP64 family must agree with it to rounding (1e-13 of max |f|, element by
+  element), which checks every step of the kernels, not only the end result.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import nfft_cpu
+from paper_1605_01244_gb300 import build, workloads as wl
+from paper_1605_01244_gb300._lib import NFFTError, NFFT3_ERR_NO_POINTS, NFFT3_ERR_POINTS
+from tests._util import rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+CD = {"f64": torch.complex128, "f32": torch.complex64}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def gpu_eval(c, x, m, prec="f64", sigma=2.0):
+    from paper_1605_01244_gb300 import Plan
+    plan = Plan(c.shape, len(x), m=m, sigma=sigma, precision=prec)
+    plan.set_points(to_dev(np.asarray(x, np.float64).reshape(-1, 3)))
+    f = plan.eval(to_dev(c, CD[prec]))
+    return to_np(f).astype(np.complex128), plan
+
+
+def max_rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def test_small_random_fp64_gate():
+    c, x = wl.small_random()
+    f, plan = gpu_eval(c, x, m=6)
+    assert plan.n == (32, 32, 32)
+    assert rel_l2(f, oracle.forward(c, x)) <= 1e-12
+    assert max_rel(f, nfft_cpu.forward(c, x, plan.n, 6)) <= 1e-13
+
+
+def test_small_random_mixed_gate():
+    """m chosen by the plan for eps = 1e-6 (m = 4 at sigma = 2) meets the mixed gate."""
+    from paper_1605_01244_gb300 import Plan, choose_m
+    c, x = wl.small_random()
+    fd = oracle.forward(c, x)
+    m = choose_m(1e-6)
+    assert m == 4
+    f, _ = gpu_eval(c, x, m=m, prec="f32")
+    assert rel_l2(f, fd) <= 1e-6
+    # one m lower the window error alone (6e-7 here) leaves no room for FP32 rounding
+    f3, _ = gpu_eval(c, x, m=3, prec="f32")
+    assert rel_l2(f3, fd) <= 1.5e-6
+
+
+@pytest.mark.parametrize("N,M,m", [((8, 12, 10), 1, 1), ((8, 12, 10), 37, 2), ((16, 6, 20), 515, 3),
+                                   ((4, 4, 4), 100, 5), ((20, 16, 12), 777, 7), ((10, 8, 6), 300, 8)])
+def test_same_algorithm_as_cpu_nfft(N, M, m):
+    c = wl.gaussian_coeffs(N, 1e9, seed=M)
+    x = wl.uniform_points(M, seed=M + 1)
+    f, plan = gpu_eval(c, x, m=m)
+    assert max_rel(f, nfft_cpu.forward(c, x, plan.n, m)) <= 1e-13
+    f32, plan32 = gpu_eval(c, x, m=m, prec="f32")
+    assert rel_l2(f32, nfft_cpu.forward(c, x, plan32.n, m)) <= 2e-6
+
+
+def test_non_power_of_two_oversampling():
+    N = (10, 14, 18)
+    c = wl.gaussian_coeffs(N, 1e9, seed=3)
+    x = wl.uniform_points(400, seed=4)
+    f, plan = gpu_eval(c, x, m=5, sigma=1.5)
+    assert plan.n == (16, 22, 28) or all(v >= 1.5 * w for v, w in zip(plan.n, N))
+    assert max_rel(f, nfft_cpu.forward(c, x, plan.n, 5)) <= 1e-13
+
+
+def test_edge_points():
+    N = (8, 10, 12)
+    c = wl.gaussian_coeffs(N, 3.0, seed=5)
+    n = (16, 20, 24)
+    nodes = np.stack(np.meshgrid(*[np.arange(v) / v - 0.5 for v in n], indexing="ij"), -1).reshape(-1, 3)
+    half = nodes + 0.5 / np.asarray(n)
+    special = np.array([[-0.5, -0.5, -0.5], [0.5, 0.5, 0.5], [np.nextafter(0.5, 0), -0.5, 0.0],
+                        [1e6 + 0.125, -3.25, 7.0], [-1e-300, 1e-300, 0.0], [0.49999999999, -0.49999999999, 0.3]])
+    for pts in (nodes, half, special):
+        f, plan = gpu_eval(c, pts, m=6)
+        assert plan.n == n
+        assert max_rel(f, nfft_cpu.forward(c, pts, n, 6)) <= 1e-13
+        assert rel_l2(f, oracle.forward(c, pts)) <= 1e-11
+
+
+def test_all_points_in_one_cell():
+    c = wl.gaussian_coeffs((16, 16, 16), 4.0, seed=6)
+    x = wl.cluster_points(5000, 1e-4, seed=7)
+    f, plan = gpu_eval(c, x, m=6)
+    assert max_rel(f, nfft_cpu.forward(c, x, plan.n, 6)) <= 1e-13
+
+
+def test_empty_and_errors():
+    from paper_1605_01244_gb300 import Plan
+    c = to_dev(wl.gaussian_coeffs((8, 8, 8), 3.0), torch.complex128)
+    plan = Plan((8, 8, 8), 0, m=4)
+    plan.set_points(torch.zeros((0, 3), dtype=torch.float64, device="cuda"))
+    assert plan.eval(c).shape == (0,)
+    h = plan.adjoint(torch.zeros(0, dtype=torch.complex128, device="cuda"))
+    assert torch.count_nonzero(h).item() == 0
+    plan2 = Plan((8, 8, 8), 4, m=4)
+    with pytest.raises(NFFTError) as e:
+        plan2.eval(c)
+    assert e.value.code == NFFT3_ERR_NO_POINTS
+    bad = torch.tensor([[0.1, 0.2, 0.3], [float("nan"), 0, 0], [0, 0, 0], [0, float("inf"), 0]],
+                       dtype=torch.float64, device="cuda")
+    with pytest.raises(NFFTError) as e:
+        plan2.set_points(bad)
+    assert e.value.code == NFFT3_ERR_POINTS
+    with pytest.raises(NFFTError):
+        plan2.eval(c)          # the failed set_points left no points
+
+
+def test_gradient_against_oracle():
+    from paper_1605_01244_gb300 import Plan
+    N = (12, 16, 10)
+    c = wl.gaussian_coeffs(N, 3.0, seed=8)
+    x = wl.uniform_points(600, seed=9)
+    fd, gd = oracle.forward_grad(c, x)
+    for prec, m, tol_f, tol_g in (("f64", 6, 1e-12, 1e-11), ("f32", 4, 1e-6, 5e-6)):
+        plan = Plan(N, len(x), m=m, precision=prec)
+        plan.set_points(to_dev(x))
+        f, g = plan.eval_grad(to_dev(c, CD[prec]))
+        f = to_np(f).astype(np.complex128)
+        g = to_np(g).astype(np.complex128)
+        assert rel_l2(f, fd) <= tol_f, prec
+        for d in range(3):
+            assert rel_l2(g[:, d], gd[:, d]) <= tol_g, (prec, d)
+        # the value from eval_grad agrees with eval (batched vs single FFT may round differently)
+        fe = to_np(plan.eval(to_dev(c, CD[prec]))).astype(np.complex128)
+        assert max_rel(f, fe) <= (1e-14 if prec == "f64" else 1e-6)
+    # f may be omitted
+    plan = Plan(N, len(x), m=6)
+    plan.set_points(to_dev(x))
+    f, g = plan.eval_grad(to_dev(c, CD["f64"]), want_f=False)
+    assert f is None and rel_l2(to_np(g)[:, 0], gd[:, 0]) <= 1e-11
+
+
+def test_gradient_same_algorithm_as_cpu_nfft():
+    from paper_1605_01244_gb300 import Plan
+    N = (8, 10, 12)
+    c = wl.gaussian_coeffs(N, 1e9, seed=10)
+    x = wl.uniform_points(200, seed=11)
+    plan = Plan(N, len(x), m=5)
+    plan.set_points(to_dev(x))
+    f, g = plan.eval_grad(to_dev(c))
+    fc, gc = nfft_cpu.forward_grad(c, x, plan.n, 5)
+    assert max_rel(to_np(g), gc) <= 1e-13
+    assert max_rel(to_np(f), fc) <= 1e-13
+
+
+@pytest.mark.parametrize("prec,m,tol", [("f64", 6, 5e-12), ("f32", 4, 1e-6)])
+def test_adjoint_against_oracle(prec, m, tol):
+    from paper_1605_01244_gb300 import Plan
+    N = (10, 8, 12)
+    x = np.concatenate([wl.uniform_points(700, seed=12), wl.cluster_points(300, 0.01, seed=13)])
+    g = wl.rng(14)
+    f = g.standard_normal(len(x)) + 1j * g.standard_normal(len(x))
+    plan = Plan(N, len(x), m=m, precision=prec)
+    plan.set_points(to_dev(x))
+    h = to_np(plan.adjoint(to_dev(f, CD[prec]))).astype(np.complex128)
+    assert rel_l2(h, oracle.adjoint(f, x, N)) <= tol
+    if prec == "f64":
+        assert max_rel(h, nfft_cpu.adjoint(f, x, N, plan.n, m)) <= 1e-12
+
+
+def test_fast_adjoint_identity():
+    from paper_1605_01244_gb300 import Plan
+    N = (16, 12, 8)
+    c = wl.gaussian_coeffs(N, 1e9, seed=15)
+    x = wl.mixed_points(2000, 0.05, seed=16)
+    g = wl.rng(17)
+    f = g.standard_normal(len(x)) + 1j * g.standard_normal(len(x))
+    plan = Plan(N, len(x), m=4)
+    plan.set_points(to_dev(x))
+    Ac = to_np(plan.eval(to_dev(c)))
+    Ahf = to_np(plan.adjoint(to_dev(f)))
+    lhs, rhs = np.vdot(f, Ac), np.vdot(Ahf, c)
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_host_path_matches_device_path(prec):
+    from paper_1605_01244_gb300 import Plan
+    c, x = wl.small_random(M=3000)
+    plan = Plan(c.shape, len(x), m=5, precision=prec)
+    xh = torch.from_numpy(x).contiguous()
+    ch = torch.from_numpy(c).to(CD[prec]).contiguous()
+    fh = torch.empty(len(x), dtype=CD[prec])
+    plan.eval_host(xh, ch, fh)
+    plan.set_points(xh.cuda())
+    fdev = plan.eval(ch.cuda()).cpu()
+    assert torch.equal(fh, fdev)
+
+
+@pytest.mark.parametrize("prec,m,tol", [("f64", 6, 1e-12), ("f32", 3, 1e-6)])
+def test_precision_sweep_full_size_sampled(prec, m, tol):
+    """N = 256^3, M = 10^7 (half uniform, half clustered, std 0.02), the
+    benchmark's launch configuration; 2000 sampled outputs (1000 from each
+    population) against the FP64 direct sum."""
+    from paper_1605_01244_gb300 import Plan
+    c, x = wl.precision_sweep()
+    M = len(x)
+    plan = Plan(c.shape, M, m=m, precision=prec)
+    plan.set_points(to_dev(x))
+    f = plan.eval(to_dev(c, CD[prec]))
+    idx = np.concatenate([wl.rng(99).choice(M // 2, 1000, replace=False),
+                          M // 2 + wl.rng(98).choice(M - M // 2, 1000, replace=False)])
+    fs = to_np(f[torch.from_numpy(idx).cuda()]).astype(np.complex128)
+    fd = oracle.forward(c, x[idx])
+    err = rel_l2(fs, fd)
+    print("precision sweep %s m=%d: rel-l2 %.3e" % (prec, m, err))
+    assert err <= tol
+    assert np.all(np.isfinite(to_np(f)))
