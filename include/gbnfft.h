@@ -132,6 +132,13 @@ int nfft3f_destroy(nfft3_plan p);
  */
 int nfft3_plan_info(nfft3_plan p, int *n, int *m, int64_t *M, int *prec);
 
+/*
+ * Largest absolute error of the plan's window weights (each tap's weight is
+ * a polynomial fitted at plan creation; weights are normalised to 1 at the
+ * window centre), measured on the host in the family's precision.
+ */
+int nfft3_window_error(nfft3_plan p, double *max_abs_err);
+
 /* Change the stream later calls enqueue on. */
 int nfft3_set_stream(nfft3_plan p, void *stream);
 
@@ -161,6 +168,14 @@ enum {
 };
 int nfft3_timing_enable(nfft3_plan p, int on);
 int nfft3_timing_read(nfft3_plan p, double *ms, int64_t *calls, int64_t *launches, int reset);
+
+/*
+ * CUDA-core FMA throughput of the current device in TFLOP/s (2 flops per FMA),
+ * measured by a kernel of independent FMA chains on every SM (prec 64 or 32;
+ * iters sets the run length).  Used to state the ALU roofline of the window
+ * sums; not part of the transform.
+ */
+int nfft3_fma_peak(int prec, int iters, void *stream, double *tflops);
 
 /*
  * m chosen for (eps, sigma) by the rule documented at nfft3d_plan

@@ -46,11 +46,13 @@ SIGNATURES = {
     "nfft3_plan_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I64),
                              ctypes.POINTER(_I)]),
     "nfft3_set_stream": (_I, [_P, _P]),
+    "nfft3_window_error": (_I, [_P, ctypes.POINTER(_D)]),
     "nfft3_sync": (_I, [_P]),
     "nfft3_error_string": (ctypes.c_char_p, [_I]),
     "nfft3_choose_m": (_I, [_D, _D]),
     "nfft3_timing_enable": (_I, [_P, _I]),
     "nfft3_timing_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64), ctypes.POINTER(_I64), _I]),
+    "nfft3_fma_peak": (_I, [_I, _I, _P, ctypes.POINTER(_D)]),
 }
 
 STAGES = ("set_points", "deconv", "fft", "gather", "spread", "fft_fwd", "deconv_adj")

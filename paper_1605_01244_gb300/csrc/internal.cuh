@@ -16,16 +16,41 @@ template <typename R> struct Cplx;
 template <> struct Cplx<double> { using T = double2; };
 template <> struct Cplx<float> { using T = float2; };
 
-// Window constants for one dimension.  The window is the Kaiser-Bessel
-// function in grid units with half-width alpha = m + 1/2,
+// Window weights.  The window is the Kaiser-Bessel function in grid units
+// with half-width alpha = m + 1/2,
 //   phi(tau) = sinh(b sqrt(alpha^2 - tau^2)) / (pi sqrt(alpha^2 - tau^2)),
-// evaluated on the support -alpha < tau <= alpha and normalised to
-// phi(0) = 1 (the normalisation is folded into the deconvolution tables).
-template <typename R> struct Win {
-    R b;        // pi (2 - 1/sigma_d)
-    R inv_den;  // alpha / (1 - exp(-2 b alpha))
-    R ebal;     // exp(-b alpha)
+// on the support -alpha < tau <= alpha, normalised to phi(0) = 1 (the
+// normalisation is folded into the deconvolution tables).  A point with
+// offset s in [0,1) has taps tau_a = alpha - s - a, a = 0..2m; each tap's
+// weight w_a(s) is an entire function of s and is evaluated as a polynomial
+// in t = 2s - 1 of degree kPolyDeg<R> (Horner), with coefficients fitted on
+// the host at plan creation (Chebyshev interpolation in long double).
+template <typename R> struct PolyDeg;
+template <> struct PolyDeg<double> { static constexpr int value = 16; };
+template <> struct PolyDeg<float> { static constexpr int value = 10; };
+
+constexpr int kMaxTaps = 2 * kMaxM + 1;
+constexpr int kMaxCoef = 17;   // >= PolyDeg<R>::value + 1
+
+// Host-side coefficient table of a plan: coef[d][a][k], k = power of t.
+template <typename R> struct WinTable {
+    R coef[3][kMaxTaps][kMaxCoef];
 };
+
+// Kernel-parameter copy sized for one m (lives in the constant bank).
+template <typename R, int MM> struct Poly {
+    static constexpr int W = 2 * MM + 1;
+    static constexpr int D = PolyDeg<R>::value;
+    R c[3][W][D + 1];
+};
+
+template <typename R, int MM> Poly<R, MM> make_poly(const WinTable<R> &t) {
+    Poly<R, MM> p;
+    for (int d = 0; d < 3; ++d)
+        for (int a = 0; a < Poly<R, MM>::W; ++a)
+            for (int k = 0; k <= Poly<R, MM>::D; ++k) p.c[d][a][k] = t.coef[d][a][k];
+    return p;
+}
 
 // Sorted point data written by set_points.
 //   key[j] = (l0_1, l0_2, l0_3, original index); l0_d in [0, n_d) is the
@@ -50,16 +75,16 @@ cudaError_t launch_deconv_scatter(const typename Cplx<R>::T *c, int N1, int N2, 
 
 template <typename R>
 cudaError_t launch_gather(const typename Cplx<R>::T *G, Grid3 g, int m, PointsView<R> pts,
-                          const Win<R> *w, typename Cplx<R>::T *f, cudaStream_t st);
+                          const WinTable<R> &w, typename Cplx<R>::T *f, cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_gather_grad(const typename Cplx<R>::T *G4, Grid3 g, int m, PointsView<R> pts,
-                               const Win<R> *w, typename Cplx<R>::T *f, typename Cplx<R>::T *grad,
-                               cudaStream_t st);
+                               const WinTable<R> &w, typename Cplx<R>::T *f,
+                               typename Cplx<R>::T *grad, cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_spread(const typename Cplx<R>::T *f, Grid3 g, int m, PointsView<R> pts,
-                          const Win<R> *w, typename Cplx<R>::T *H, cudaStream_t st);
+                          const WinTable<R> &w, typename Cplx<R>::T *H, cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_deconv_gather(const typename Cplx<R>::T *H, Grid3 g, const R *D1, const R *D2,

@@ -5,35 +5,19 @@
 namespace gbnfft {
 namespace {
 
-template <typename R> __device__ __forceinline__ R dev_exp(R v);
-template <> __device__ __forceinline__ double dev_exp<double>(double v) { return exp(v); }
-template <> __device__ __forceinline__ float dev_exp<float>(float v) { return expf(v); }
-template <typename R> __device__ __forceinline__ R dev_expm1(R v);
-template <> __device__ __forceinline__ double dev_expm1<double>(double v) { return expm1(v); }
-template <> __device__ __forceinline__ float dev_expm1<float>(float v) { return expm1f(v); }
-template <typename R> __device__ __forceinline__ R dev_sqrt(R v);
-template <> __device__ __forceinline__ double dev_sqrt<double>(double v) { return sqrt(v); }
-template <> __device__ __forceinline__ float dev_sqrt<float>(float v) { return sqrtf(v); }
-
-// Normalised window value for tap a of a point with offset s (tau = alpha - s - a):
-//   q^2 = (alpha - tau)(alpha + tau) = (s + a)(2m + 1 - s - a)
-//   w   = (alpha / q) sinh(b q) / sinh(b alpha)
-//       = inv_den * exp(b (q - alpha)) * (-expm1(-2 b q) / q),
-// whose q -> 0 limit (tau = alpha exactly, s = 0, a = 0) is inv_den * ebal * 2b.
+// Weights of the 2m+1 taps of one dimension for offset s in [0, 1):
+// Horner in t = 2s - 1 with the plan's coefficients (kernel parameters,
+// read from the constant bank by every thread at the same index).
 template <typename R, int MM>
-__device__ __forceinline__ void window_row(R s, const Win<R> &w, R out[2 * MM + 1]) {
+__device__ __forceinline__ void window_row(R s, const R (&c)[2 * MM + 1][PolyDeg<R>::value + 1],
+                                           R out[2 * MM + 1]) {
+    constexpr int D = PolyDeg<R>::value;
+    const R t = (R)2 * s - (R)1;
 #pragma unroll
     for (int a = 0; a <= 2 * MM; ++a) {
-        const R lo = s + (R)a;
-        const R hi = (R)(2 * MM + 1) - lo;
-        const R q = dev_sqrt<R>(lo * hi);
-        const R bq = w.b * q;
-        R v;
-        if (q > (R)0) {
-            v = w.inv_den * dev_exp<R>(bq - w.b * (R)(MM + 0.5)) * (-dev_expm1<R>((R)-2 * bq) / q);
-        } else {
-            v = w.inv_den * w.ebal * (R)2 * w.b;
-        }
+        R v = c[a][D];
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) v = fma(v, t, c[a][k]);
         out[a] = v;
     }
 }
@@ -106,8 +90,8 @@ __global__ void deconv_scatter_kernel(const typename Cplx<R>::T *__restrict__ c,
 // ----------------------------------------------------------------------------
 template <typename R, int MM, int NG>
 __global__ void __launch_bounds__(128) gather_kernel(const typename Cplx<R>::T *__restrict__ G,
-                                                     Grid3 g, PointsView<R> pts, Win<R> w1p,
-                                                     Win<R> w2p, Win<R> w3p,
+                                                     Grid3 g, PointsView<R> pts,
+                                                     const __grid_constant__ Poly<R, MM> P,
                                                      typename Cplx<R>::T *__restrict__ f,
                                                      typename Cplx<R>::T *__restrict__ grad) {
     using C = typename Cplx<R>::T;
@@ -116,9 +100,9 @@ __global__ void __launch_bounds__(128) gather_kernel(const typename Cplx<R>::T *
     if (j >= pts.M) return;
     const int4 key = pts.key[j];
     R w1[W], w2[W], w3[W];
-    window_row<R, MM>(pts.s1[j], w1p, w1);
-    window_row<R, MM>(pts.s2[j], w2p, w2);
-    window_row<R, MM>(pts.s3[j], w3p, w3);
+    window_row<R, MM>(pts.s1[j], P.c[0], w1);
+    window_row<R, MM>(pts.s2[j], P.c[1], w2);
+    window_row<R, MM>(pts.s3[j], P.c[2], w3);
     int i3[W];
 #pragma unroll
     for (int c = 0; c < W; ++c) i3[c] = wrap_add(key.z, c, g.n3);
@@ -126,12 +110,15 @@ __global__ void __launch_bounds__(128) gather_kernel(const typename Cplx<R>::T *
     R acc[NG][2];
 #pragma unroll
     for (int q = 0; q < NG; ++q) acc[q][0] = acc[q][1] = 0;
+    // a loop rolled; w1 rotates through registers so that every index is static
     int ia = key.x;
+#pragma unroll 1
     for (int a = 0; a < W; ++a) {
         R mid[NG][2];
 #pragma unroll
         for (int q = 0; q < NG; ++q) mid[q][0] = mid[q][1] = 0;
         int ib = key.y;
+#pragma unroll
         for (int b = 0; b < W; ++b) {
             const int64_t row = ((int64_t)ia * g.n2 + ib) * g.n3;
 #pragma unroll
@@ -150,9 +137,11 @@ __global__ void __launch_bounds__(128) gather_kernel(const typename Cplx<R>::T *
         }
 #pragma unroll
         for (int q = 0; q < NG; ++q) {
-            acc[q][0] += w1[a] * mid[q][0];
-            acc[q][1] += w1[a] * mid[q][1];
+            acc[q][0] += w1[0] * mid[q][0];
+            acc[q][1] += w1[0] * mid[q][1];
         }
+#pragma unroll
+        for (int k = 0; k < W - 1; ++k) w1[k] = w1[k + 1];
         if (++ia == g.n1) ia = 0;
     }
     const int64_t o = key.w;
@@ -184,8 +173,8 @@ __global__ void __launch_bounds__(128) gather_kernel(const typename Cplx<R>::T *
 // ----------------------------------------------------------------------------
 template <typename R, int MM>
 __global__ void __launch_bounds__(128) spread_kernel(const typename Cplx<R>::T *__restrict__ f,
-                                                     Grid3 g, PointsView<R> pts, Win<R> w1p,
-                                                     Win<R> w2p, Win<R> w3p,
+                                                     Grid3 g, PointsView<R> pts,
+                                                     const __grid_constant__ Poly<R, MM> P,
                                                      typename Cplx<R>::T *__restrict__ H) {
     using C = typename Cplx<R>::T;
     constexpr int W = 2 * MM + 1;
@@ -194,17 +183,19 @@ __global__ void __launch_bounds__(128) spread_kernel(const typename Cplx<R>::T *
     const int4 key = pts.key[j];
     const C fv = f[key.w];
     R w1[W], w2[W], w3[W];
-    window_row<R, MM>(pts.s1[j], w1p, w1);
-    window_row<R, MM>(pts.s2[j], w2p, w2);
-    window_row<R, MM>(pts.s3[j], w3p, w3);
+    window_row<R, MM>(pts.s1[j], P.c[0], w1);
+    window_row<R, MM>(pts.s2[j], P.c[1], w2);
+    window_row<R, MM>(pts.s3[j], P.c[2], w3);
     int i3[W];
 #pragma unroll
     for (int c = 0; c < W; ++c) i3[c] = wrap_add(key.z, c, g.n3);
     int ia = key.x;
+#pragma unroll 1
     for (int a = 0; a < W; ++a) {
         int ib = key.y;
+#pragma unroll
         for (int b = 0; b < W; ++b) {
-            const R wab = w1[a] * w2[b];
+            const R wab = w1[0] * w2[b];
             const R fr = fv.x * wab, fi = fv.y * wab;
             R *row = reinterpret_cast<R *>(H + ((int64_t)ia * g.n2 + ib) * g.n3);
 #pragma unroll
@@ -214,6 +205,8 @@ __global__ void __launch_bounds__(128) spread_kernel(const typename Cplx<R>::T *
             }
             if (++ib == g.n2) ib = 0;
         }
+#pragma unroll
+        for (int k = 0; k < W - 1; ++k) w1[k] = w1[k + 1];
         if (++ia == g.n1) ia = 0;
     }
 }
@@ -250,18 +243,18 @@ int grid_blocks(int64_t total, int threads) {
 
 template <typename R, int MM, int NG>
 cudaError_t gather_dispatch(const typename Cplx<R>::T *G, Grid3 g, PointsView<R> pts,
-                            const Win<R> *w, typename Cplx<R>::T *f, typename Cplx<R>::T *grad,
-                            cudaStream_t st) {
+                            const WinTable<R> &w, typename Cplx<R>::T *f,
+                            typename Cplx<R>::T *grad, cudaStream_t st) {
     const int threads = 128;
     const int64_t blocks = (pts.M + threads - 1) / threads;
-    gather_kernel<R, MM, NG><<<(unsigned)blocks, threads, 0, st>>>(G, g, pts, w[0], w[1], w[2], f,
-                                                                   grad);
+    gather_kernel<R, MM, NG><<<(unsigned)blocks, threads, 0, st>>>(G, g, pts, make_poly<R, MM>(w),
+                                                                   f, grad);
     return cudaGetLastError();
 }
 
 template <typename R, int NG>
 cudaError_t gather_select(const typename Cplx<R>::T *G, Grid3 g, int m, PointsView<R> pts,
-                          const Win<R> *w, typename Cplx<R>::T *f, typename Cplx<R>::T *grad,
+                          const WinTable<R> &w, typename Cplx<R>::T *f, typename Cplx<R>::T *grad,
                           cudaStream_t st) {
     if (pts.M == 0) return cudaSuccess;
     switch (m) {
@@ -279,10 +272,10 @@ cudaError_t gather_select(const typename Cplx<R>::T *G, Grid3 g, int m, PointsVi
 
 template <typename R, int MM>
 cudaError_t spread_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsView<R> pts,
-                            const Win<R> *w, typename Cplx<R>::T *H, cudaStream_t st) {
+                            const WinTable<R> &w, typename Cplx<R>::T *H, cudaStream_t st) {
     const int threads = 128;
     const int64_t blocks = (pts.M + threads - 1) / threads;
-    spread_kernel<R, MM><<<(unsigned)blocks, threads, 0, st>>>(f, g, pts, w[0], w[1], w[2], H);
+    spread_kernel<R, MM><<<(unsigned)blocks, threads, 0, st>>>(f, g, pts, make_poly<R, MM>(w), H);
     return cudaGetLastError();
 }
 
@@ -301,20 +294,20 @@ cudaError_t launch_deconv_scatter(const typename Cplx<R>::T *c, int N1, int N2, 
 
 template <typename R>
 cudaError_t launch_gather(const typename Cplx<R>::T *G, Grid3 g, int m, PointsView<R> pts,
-                          const Win<R> *w, typename Cplx<R>::T *f, cudaStream_t st) {
+                          const WinTable<R> &w, typename Cplx<R>::T *f, cudaStream_t st) {
     return gather_select<R, 1>(G, g, m, pts, w, f, nullptr, st);
 }
 
 template <typename R>
 cudaError_t launch_gather_grad(const typename Cplx<R>::T *G4, Grid3 g, int m, PointsView<R> pts,
-                               const Win<R> *w, typename Cplx<R>::T *f, typename Cplx<R>::T *grad,
-                               cudaStream_t st) {
+                               const WinTable<R> &w, typename Cplx<R>::T *f,
+                               typename Cplx<R>::T *grad, cudaStream_t st) {
     return gather_select<R, 4>(G4, g, m, pts, w, f, grad, st);
 }
 
 template <typename R>
 cudaError_t launch_spread(const typename Cplx<R>::T *f, Grid3 g, int m, PointsView<R> pts,
-                          const Win<R> *w, typename Cplx<R>::T *H, cudaStream_t st) {
+                          const WinTable<R> &w, typename Cplx<R>::T *H, cudaStream_t st) {
     if (pts.M == 0) return cudaSuccess;
     switch (m) {
         case 1: return spread_dispatch<R, 1>(f, g, pts, w, H, st);
@@ -345,12 +338,12 @@ cudaError_t launch_deconv_gather(const typename Cplx<R>::T *H, Grid3 g, const R 
                                                   const R *, const R *, Cplx<R>::T *, Grid3, int,  \
                                                   cudaStream_t);                                   \
     template cudaError_t launch_gather<R>(const Cplx<R>::T *, Grid3, int, PointsView<R>,          \
-                                          const Win<R> *, Cplx<R>::T *, cudaStream_t);             \
+                                          const WinTable<R> &, Cplx<R>::T *, cudaStream_t);        \
     template cudaError_t launch_gather_grad<R>(const Cplx<R>::T *, Grid3, int, PointsView<R>,     \
-                                               const Win<R> *, Cplx<R>::T *, Cplx<R>::T *,         \
+                                               const WinTable<R> &, Cplx<R>::T *, Cplx<R>::T *,    \
                                                cudaStream_t);                                      \
     template cudaError_t launch_spread<R>(const Cplx<R>::T *, Grid3, int, PointsView<R>,          \
-                                          const Win<R> *, Cplx<R>::T *, cudaStream_t);             \
+                                          const WinTable<R> &, Cplx<R>::T *, cudaStream_t);        \
     template cudaError_t launch_deconv_gather<R>(const Cplx<R>::T *, Grid3, const R *, const R *, \
                                                  const R *, int, int, int, Cplx<R>::T *,           \
                                                  cudaStream_t);

@@ -21,6 +21,10 @@ struct nfft3_plan_s {
     int sync_check;           // GBNFFT_SYNC_CHECK set: synchronise after every call
     int fault;                // host-side fault injection (GBNFFT_FAULT)
     int device;
+    // window polynomials (both precisions; the family uses one) and their checked error
+    WinTable<double> wt64;
+    WinTable<float> wt32;
+    double window_err;
     // tables and grid
     void *D[3];               // deconvolution factors, real type of the family
     void *grid;               // n1 n2 n3 complex (x4 once eval_grad ran)
@@ -162,14 +166,86 @@ double error_estimate(int m, double sigma) {
     return 8.0 * std::exp(-2.0 * M_PI * std::sqrt(1.0 - 1.0 / sigma) * (m + 0.5));
 }
 
-template <typename R> Win<R> make_win(double b, int m) {
-    const double al = m + 0.5;
-    Win<R> w;
-    w.b = (R)b;
-    w.inv_den = (R)(al / (1.0 - std::exp(-2.0 * b * al)));
-    w.ebal = (R)std::exp(-b * al);
-    return w;
+// ---- window polynomials -----------------------------------------------------
+// Exact normalised window weight of tap a at offset s (long double):
+//   tau = alpha - s - a,  q^2 = alpha^2 - tau^2 = (s + a)(2m + 1 - s - a),
+//   w = (alpha / q) sinh(b q) / sinh(b alpha)
+//     = alpha / (1 - e^{-2 b alpha}) * exp(-b tau^2 / (q + alpha)) * (-expm1(-2 b q) / q),
+// written so that no step cancels (q - alpha = -tau^2 / (q + alpha)); q = 0 gives 2b for the last factor.
+long double exact_weight(long double s, int a, int m, long double b) {
+    const long double al = (long double)m + 0.5L;
+    const long double tau = al - s - (long double)a;
+    const long double q2 = (s + (long double)a) * ((long double)(2 * m + 1) - s - (long double)a);
+    const long double q = q2 > 0 ? sqrtl(q2) : 0.0L;
+    const long double r = q > 0 ? -expm1l(-2.0L * b * q) / q : 2.0L * b;
+    return al / (1.0L - expl(-2.0L * b * al)) * expl(-b * tau * tau / (q + al)) * r;
 }
+
+// Degree-D interpolant of w_a(s) at the Chebyshev nodes of t = 2s - 1,
+// returned as monomial coefficients in t (mono[k] multiplies t^k).
+void fit_tap(int a, int m, long double b, int D, long double *mono) {
+    const long double pi = acosl(-1.0L);
+    long double f[kMaxCoef], cheb[kMaxCoef], Tm[kMaxCoef], T0[kMaxCoef], T1[kMaxCoef];
+    for (int j = 0; j <= D; ++j) {
+        const long double t = cosl(pi * ((long double)j + 0.5L) / (long double)(D + 1));
+        f[j] = exact_weight(0.5L * (t + 1.0L), a, m, b);
+    }
+    for (int k = 0; k <= D; ++k) {
+        long double acc = 0;
+        for (int j = 0; j <= D; ++j)
+            acc += f[j] * cosl(pi * (long double)k * ((long double)j + 0.5L) / (long double)(D + 1));
+        cheb[k] = 2.0L * acc / (long double)(D + 1);
+    }
+    cheb[0] *= 0.5L;
+    for (int k = 0; k < kMaxCoef; ++k) mono[k] = 0, T0[k] = 0, T1[k] = 0;
+    T0[0] = 1;  // T_0
+    T1[1] = 1;  // T_1
+    for (int k = 0; k <= D; ++k) mono[k] += cheb[0] * T0[k];
+    if (D >= 1)
+        for (int k = 0; k <= D; ++k) mono[k] += cheb[1] * T1[k];
+    for (int n = 2; n <= D; ++n) {
+        // T_n = 2 t T_{n-1} - T_{n-2}
+        for (int k = 0; k <= D; ++k) Tm[k] = (k > 0 ? 2.0L * T1[k - 1] : 0.0L) - T0[k];
+        for (int k = 0; k <= D; ++k) {
+            mono[k] += cheb[n] * Tm[k];
+            T0[k] = T1[k];
+            T1[k] = Tm[k];
+        }
+    }
+}
+
+template <typename R> R host_fma(R a, R b, R c);
+template <> double host_fma<double>(double a, double b, double c) { return std::fma(a, b, c); }
+template <> float host_fma<float>(float a, float b, float c) { return std::fmaf(a, b, c); }
+
+// Fill a plan's table for precision R; returns the largest absolute error of
+// the polynomial (evaluated by Horner in R, as the kernels do) on a fine grid of s.
+template <typename R> double build_window_table(WinTable<R> &wt, const double *b, int m) {
+    constexpr int D = PolyDeg<R>::value;
+    double worst = 0;
+    std::memset(&wt, 0, sizeof(wt));
+    for (int d = 0; d < 3; ++d) {
+        for (int a = 0; a <= 2 * m; ++a) {
+            long double mono[kMaxCoef];
+            fit_tap(a, m, (long double)b[d], D, mono);
+            for (int k = 0; k <= D; ++k) wt.coef[d][a][k] = (R)mono[k];
+            for (int i = 0; i <= 2000; ++i) {
+                const R s = (R)(i / 2000.0);
+                const R t = (R)2 * s - (R)1;
+                R v = wt.coef[d][a][D];
+                for (int k = D - 1; k >= 0; --k) v = host_fma<R>(v, t, wt.coef[d][a][k]);
+                const long double ex = exact_weight((long double)s, a, m, (long double)b[d]);
+                const double e = (double)fabsl((long double)v - ex);
+                if (e > worst) worst = e;
+            }
+        }
+    }
+    return worst;
+}
+
+template <typename R> const WinTable<R> &win_table(nfft3_plan p);
+template <> const WinTable<double> &win_table<double>(nfft3_plan p) { return p->wt64; }
+template <> const WinTable<float> &win_table<float>(nfft3_plan p) { return p->wt32; }
 
 int finish(nfft3_plan p, int status) {
     if (status == NFFT3_OK && p && p->sync_check) {
@@ -243,6 +319,8 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         p->n[d] = oversampled_size(Ns[d], sigma);
         p->b[d] = M_PI * (2.0 - (double)Ns[d] / (double)p->n[d]);
     }
+    p->window_err = prec == 64 ? build_window_table<double>(p->wt64, p->b, m)
+                               : build_window_table<float>(p->wt32, p->b, m);
     const size_t rs = prec == 64 ? sizeof(double) : sizeof(float);
     int st = NFFT3_OK;
 
@@ -329,10 +407,6 @@ template <typename R> PointsView<R> points_view(nfft3_plan p) {
     return v;
 }
 
-template <typename R> void wins(nfft3_plan p, Win<R> w[3]) {
-    for (int d = 0; d < 3; ++d) w[d] = make_win<R>(p->b[d], p->m);
-}
-
 int exec_fft(cufftHandle h, void *data, int prec, int direction) {
     cufftResult r;
     if (prec == 64)
@@ -386,9 +460,7 @@ template <typename R> int eval_impl(nfft3_plan p, const R *c, R *f) {
     int st = exec_fft(p->fft1, G, prec, CUFFT_INVERSE);
     if (st != NFFT3_OK) return st;
     rec_mark(p, rec, 2);
-    Win<R> w[3];
-    wins<R>(p, w);
-    e = launch_gather<R>(G, g, p->m, points_view<R>(p), w, (C *)f, p->stream);
+    e = launch_gather<R>(G, g, p->m, points_view<R>(p), win_table<R>(p), (C *)f, p->stream);
     rec_mark(p, rec, 3);
     p->launches += 2;
     return finish(p, cuda_status(e));
@@ -439,9 +511,8 @@ template <typename R> int eval_grad_impl(nfft3_plan p, const R *c, R *f, R *grad
     st = exec_fft(p->fft4, G, prec, CUFFT_INVERSE);
     if (st != NFFT3_OK) return st;
     rec_mark(p, rec, 2);
-    Win<R> w[3];
-    wins<R>(p, w);
-    e = launch_gather_grad<R>(G, g, p->m, points_view<R>(p), w, (C *)f, (C *)grad, p->stream);
+    e = launch_gather_grad<R>(G, g, p->m, points_view<R>(p), win_table<R>(p), (C *)f, (C *)grad,
+                              p->stream);
     rec_mark(p, rec, 3);
     p->launches += 2;
     return finish(p, cuda_status(e));
@@ -459,9 +530,7 @@ template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
     const int rec = rec_begin(p, kRecAdjoint);
     cudaError_t e = cudaMemsetAsync(H, 0, sizeof(C) * nn, p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
-    Win<R> w[3];
-    wins<R>(p, w);
-    e = launch_spread<R>((const C *)f, g, p->m, points_view<R>(p), w, H, p->stream);
+    e = launch_spread<R>((const C *)f, g, p->m, points_view<R>(p), win_table<R>(p), H, p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     rec_mark(p, rec, 1);
     int st = exec_fft(p->fft1, H, prec, CUFFT_FORWARD);
@@ -579,6 +648,12 @@ int nfft3_plan_info(nfft3_plan p, int *n, int *m, int64_t *M, int *prec) {
     if (m) *m = p->m;
     if (M) *M = p->M;
     if (prec) *prec = p->prec;
+    return NFFT3_OK;
+}
+
+int nfft3_window_error(nfft3_plan p, double *max_abs_err) {
+    if (!p || !max_abs_err) return NFFT3_ERR_ARG;
+    *max_abs_err = p->window_err;
     return NFFT3_OK;
 }
 

@@ -21,12 +21,14 @@ __device__ __forceinline__ Reduced reduce_coord(double x, int n, int m, int *sta
         atomicOr(status, 1);
         x = 0.0;
     }
-    const double xw = x - floor(x + 0.5);
-    const double u = (double)n * (xw + 0.5);
-    const double v = u - ((double)m + 0.5);
+    // explicit round-to-nearest steps: no contraction into FMAs, so that the
+    // stencil choice at exact half-integer u is reproducible
+    const double xw = __dsub_rn(x, floor(__dadd_rn(x, 0.5)));
+    const double u = __dmul_rn((double)n, __dadd_rn(xw, 0.5));
+    const double v = __dsub_rn(u, (double)m + 0.5);
     const double l0 = ceil(v);
     Reduced r;
-    r.s = l0 - v;
+    r.s = __dsub_rn(l0, v);
     if (r.s >= 1.0) r.s = 0.0;  // cannot happen for finite v; keeps s in [0, 1) regardless
     long long li = (long long)l0 % n;
     if (li < 0) li += n;

@@ -226,3 +226,17 @@ def test_precision_sweep_full_size_sampled(prec, m, tol):
     print("precision sweep %s m=%d: rel-l2 %.3e" % (prec, m, err))
     assert err <= tol
     assert np.all(np.isfinite(to_np(f)))
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 2e-14), ("f32", 3e-7)])
+def test_window_polynomials_accuracy(prec, tol):
+    """Each tap's weight polynomial (fitted at plan creation, evaluated by
+    Horner in the family's precision) against the exact long-double window."""
+    import ctypes
+    from paper_1605_01244_gb300 import Plan, _lib
+    for sigma in (1.25, 2.0, 8.0):
+        for m in range(1, 9):
+            plan = Plan((16, 12, 10), 1, m=m, sigma=sigma, precision=prec)
+            err = ctypes.c_double()
+            _lib.call("nfft3_window_error", plan._h, ctypes.byref(err))
+            assert err.value <= tol, (sigma, m, err.value)
