@@ -109,6 +109,27 @@ int nfft3f_eval(nfft3_plan p, const float *c, float *f);
 int nfft3d_eval_grad(nfft3_plan p, const double *c, double *f, double *grad);
 int nfft3f_eval_grad(nfft3_plan p, const float *c, float *f, float *grad);
 
+/*
+ * nfft3d_eval_grad without allocation.  The paper has no counterpart: this
+ * is a service for callers that cannot call cudaMalloc when they evaluate --
+ * a process whose device memory is already reserved by another allocator (a
+ * framework's caching pool, where cudaMalloc may fail), or a latency-bound
+ * loop that cannot take cudaMalloc's implicit device synchronisation.
+ * nfft3d_eval_grad allocates its four gradient grids on first use; this
+ * variant computes the same f and grad (same layout and meaning) with those
+ * grids in a fixed 16 MiB device array compiled into the library (every GPU
+ * that loads the library holds it until the process exits).  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   Limit: 4 * n1*n2*n3 complex doubles must fit, i.e. n1*n2*n3 <= 262144
+ *   (64^3); larger plans get NFFT3_ERR_TOO_LARGE.  FP64 plans only.
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   All calls share the array: calls whose work overlaps on the GPU (other
+ *   streams or host threads) race and give wrong results.  Each call rewrites
+ *   every grid element before reading it, so leftover contents are harmless.
+ */
+int nfft3d_eval_grad_noalloc(nfft3_plan p, const double *c, double *f, double *grad);
+
 /* c_out = A^H f  (type-1 adjoint): c_out[k] = sum_j f_j exp(-2 pi i k.x_j). */
 int nfft3d_adjoint(nfft3_plan p, const double *f, double *c_out);
 int nfft3f_adjoint(nfft3_plan p, const float *f, float *c_out);

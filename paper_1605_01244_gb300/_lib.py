@@ -37,6 +37,7 @@ SIGNATURES = {
     "nfft3f_eval": (_I, [_P, _P, _P]),
     "nfft3d_eval_grad": (_I, [_P, _P, _P, _P]),
     "nfft3f_eval_grad": (_I, [_P, _P, _P, _P]),
+    "nfft3d_eval_grad_noalloc": (_I, [_P, _P, _P, _P]),
     "nfft3d_adjoint": (_I, [_P, _P, _P]),
     "nfft3f_adjoint": (_I, [_P, _P, _P]),
     "nfft3d_eval_host": (_I, [_P, _P, _P, _P]),

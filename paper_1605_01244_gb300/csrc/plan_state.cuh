@@ -1,0 +1,48 @@
+// Definition of the plan object shared by the translation units that need
+// its fields (plan.cu and noalloc.cu).  Not part of the public ABI.
+#pragma once
+
+#include "internal.cuh"
+
+constexpr int kTimingRecords = 64;
+constexpr int kTimingMarks = 4;
+
+struct nfft3_plan_s {
+    int prec;                 // 64 or 32
+    int N[3], n[3], m;
+    int64_t M;
+    double b[3];
+    cudaStream_t stream;
+    int sync_check;           // GBNFFT_SYNC_CHECK set: synchronise after every call
+    int fault;                // host-side fault injection (GBNFFT_FAULT)
+    int device;
+    // window polynomials (both precisions; the family uses one) and their checked error
+    gbnfft::WinTable<double> wt64;
+    gbnfft::WinTable<float> wt32;
+    double window_err;
+    // tables and grid
+    void *D[3];               // deconvolution factors, real type of the family
+    void *grid;               // n1 n2 n3 complex (x4 once eval_grad ran)
+    int grid_count;           // 1 or 4
+    cufftHandle fft1;
+    cufftHandle fft4;
+    int have_fft4;
+    // points
+    int points_ok;
+    int4 *key;
+    void *s[3];
+    gbnfft::PointsBuild pb;
+    // host-buffer staging (allocated on first _host call)
+    double *x_dev;
+    void *c_dev;
+    void *f_dev;
+    // stage timing (CUDA events on the plan's stream), enabled by nfft3_timing_enable
+    int timing;
+    int nrec;
+    cudaEvent_t ev[kTimingRecords][kTimingMarks];
+    int rec_kind[kTimingRecords];
+    int ev_ready[kTimingRecords];
+    double stage_ms[NFFT3_NSTAGES];
+    int64_t stage_calls[NFFT3_NSTAGES];
+    int64_t launches;         // kernels this library enqueued (cuFFT's own not counted)
+};
