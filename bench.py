@@ -203,12 +203,13 @@ def run_ours(args, rank, world, local):
         clocks = sampler.stop()
         ms = e0.elapsed_time(e1) / args.steps
         import ctypes
-        st_ms = (ctypes.c_double * 7)()
-        st_n = (ctypes.c_int64 * 7)()
+        st_ms = (ctypes.c_double * len(_lib.STAGES))()
+        st_n = (ctypes.c_int64 * len(_lib.STAGES))()
         launches = ctypes.c_int64()
         _lib.lib().nfft3_timing_read(plan._h, st_ms, st_n, ctypes.byref(launches), 1)
         _lib.lib().nfft3_timing_enable(plan._h, 0)
-        stages = {nm: (st_ms[i] / st_n[i] if st_n[i] else 0.0) for i, nm in enumerate(_lib.STAGES[:4])}
+        stages = {nm: (st_ms[i] / st_n[i] if st_n[i] else 0.0) for i, nm in enumerate(_lib.STAGES)
+                  if nm in ("set_points", "deconv", "fft", "split", "gather")}
         if dist:
             t = torch.tensor([ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)

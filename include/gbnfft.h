@@ -185,10 +185,34 @@ enum {
     NFFT3_STAGE_SPREAD = 4,      /* adjoint: clear + spread            */
     NFFT3_STAGE_FFT_FWD = 5,     /* adjoint: forward FFT (cuFFT)       */
     NFFT3_STAGE_DECONV_ADJ = 6,  /* adjoint: deconvolve + gather of c  */
-    NFFT3_NSTAGES = 7
+    NFFT3_STAGE_SPLIT = 7,       /* FP64 family: split the grid into hi/lo floats */
+    NFFT3_NSTAGES = 8
 };
 int nfft3_timing_enable(nfft3_plan p, int on);
 int nfft3_timing_read(nfft3_plan p, double *ms, int64_t *calls, int64_t *launches, int reset);
+
+/*
+ * One Newton step towards the zero set of psi (vortex cores), for M points
+ * (device arrays).  F = (Re psi, Im psi) and J = [Re grad psi; Im grad psi]
+ * (2 x 3) come from nfft3*_eval_grad at x (f: M complex, grad: M*3 complex,
+ * double2 for prec 64, float2 for prec 32); the minimum-norm step
+ * dx = -J^T (J J^T)^{-1} F is added to x (M*3 doubles) for active points.
+ * status[j] (int, caller-initialised to 0): 0 active, 1 converged
+ * (|psi| < tol at the x it was evaluated at; x not moved), 2 singular
+ * J J^T (det <= 1e-30 (|Re grad|^2 + |Im grad|^2)^2), 3 step longer than
+ * max_step (torus units).  resid[j] receives |psi| at the evaluated x.
+ * The paper finds cores by thresholding rho = |psi|^2 on refined point sets
+ * (Sec. 4, sftubeeval3); this step refines candidates onto the zero set.
+ */
+int nfft3_newton_step(int prec, int64_t M, double *x, const void *f, const void *grad,
+                      int *status, double *resid, double tol, double max_step, void *stream);
+
+/*
+ * keep[i] = 1 when status[i] == 1 and no converged point of lower index lies
+ * within radius of x_i (periodic distance on the unit torus); else 0.
+ */
+int nfft3_dedupe(int64_t M, const double *x, const int *status, double radius, int *keep,
+                 void *stream);
 
 /*
  * CUDA-core FMA throughput of the current device in TFLOP/s (2 flops per FMA),

@@ -54,7 +54,9 @@ def build(force: bool = False, extra_flags: tuple[str, ...] = (), verbose: bool 
     home = cuda_home()
     nvcc = os.path.join(home, "bin", "nvcc")
     os.makedirs(BUILD, exist_ok=True)
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    # host code: no FMA contraction, so the host-side window checks round the
+    # same way on x86 and Arm
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
                      "-I", os.path.join(ROOT, "include"), "-I", CSRC, *extra_flags]
 
     def compile_one(src):

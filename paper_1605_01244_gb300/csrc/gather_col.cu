@@ -1,0 +1,413 @@
+// Column-parallel window gather: one point per group of GS = 2^ceil(log2(2m+1))
+// lanes, lane c of the group owning column c of the stencil's contiguous
+// dimension.  For every stencil row (a, b) the group reads 2m+1 consecutive
+// grid values, so a warp's load touches a few contiguous segments instead of
+// 32 scattered sectors.  Each lane accumulates
+//     T_c = sum_a w1[a] sum_b w2[b] g[l1+a, l2+b, l3+c]
+// and the group finishes f = sum_c w3[c] T_c with a shuffle reduction.
+// Window weights: lane c evaluates the polynomials of tap c for the three
+// dimensions (coefficients staged in shared memory), then w1 and w2 are
+// broadcast to the group's registers by shuffles, once per point.
+//
+// The kernels read a ghost-padded copy of the grid, P[p] = g[p mod n] for
+// p in [0, n + 2m) per dimension (written by pad_grid_*), so a stencil never
+// wraps and a row's address is a pointer increment.
+//
+// Two arithmetic variants: FP32 (mixed family) and double-float on the FP32
+// pipe (FP64 family; see gather_df.cu for the arithmetic).
+#include "internal.cuh"
+
+namespace gbnfft {
+namespace {
+
+template <int W> struct GroupSize {
+    static constexpr int value = W <= 2 ? 2 : W <= 4 ? 4 : W <= 8 ? 8 : W <= 16 ? 16 : 32;
+};
+
+// ---- double-float helpers (same arithmetic as gather_df.cu) ------------------
+__device__ __forceinline__ void df_mac(float &ah, float &al, float xh, float xl, float yh,
+                                       float yl) {
+    const float p = __fmul_rn(xh, yh);
+    float e = __fmaf_rn(xh, yh, -p);
+    e = __fmaf_rn(xh, yl, e);
+    e = __fmaf_rn(xl, yh, e);
+    const float s = __fadd_rn(ah, p);
+    const float bb = __fsub_rn(s, ah);
+    const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    al = __fadd_rn(al, __fadd_rn(err, e));
+    ah = s;
+}
+__device__ __forceinline__ void df_norm(float &ah, float &al) {
+    const float s = __fadd_rn(ah, al);
+    al = __fsub_rn(al, __fsub_rn(s, ah));
+    ah = s;
+}
+__device__ __forceinline__ void df_add(float &ah, float &al, float bh, float bl) {
+    const float s = __fadd_rn(ah, bh);
+    const float bb = __fsub_rn(s, ah);
+    const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    al = __fadd_rn(al, __fadd_rn(err, bl));
+    ah = s;
+}
+__device__ __forceinline__ void df_horner_step(float &vh, float &vl, float th, float tl, float ch,
+                                               float cl) {
+    const float p = __fmul_rn(vh, th);
+    float e = __fmaf_rn(vh, th, -p);
+    e = __fmaf_rn(vh, tl, e);
+    e = __fmaf_rn(vl, th, e);
+    const float s = __fadd_rn(p, ch);
+    const float bb = __fsub_rn(s, p);
+    float err = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(ch, bb));
+    err = __fadd_rn(err, __fadd_rn(e, cl));
+    vh = __fadd_rn(s, err);
+    vl = __fsub_rn(err, __fsub_rn(vh, s));
+}
+
+// ---- FP32 (mixed family) -----------------------------------------------------
+template <int MM, int NG>
+__global__ void __launch_bounds__(256) gather_col_f32_kernel(const float2 *__restrict__ G, Grid3 pg,
+                                                             PointsView<float> pts,
+                                                             const __grid_constant__ Poly<float, MM> P,
+                                                             float2 *__restrict__ f,
+                                                             float2 *__restrict__ grad) {
+    constexpr int W = 2 * MM + 1;
+    constexpr int GS = GroupSize<W>::value;
+    constexpr int D = PolyDeg<float>::value;
+    __shared__ float coef[3][W][D + 1];
+    for (int i = threadIdx.x; i < 3 * W * (D + 1); i += blockDim.x)
+        (&coef[0][0][0])[i] = (&P.c[0][0][0])[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (GS - 1);
+    const int gbase = lane & ~(GS - 1);
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / GS;
+    const bool valid = j < pts.M;
+    const int64_t jj = valid ? j : 0;
+    const int4 key = pts.M > 0 ? pts.key[jj] : make_int4(0, 0, 0, 0);
+    const int tap = sub < W ? sub : 0;
+    float myw[3];
+    {
+        const float s[3] = {pts.s1[jj], pts.s2[jj], pts.s3[jj]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float t = 2.f * s[d] - 1.f;
+            float v = coef[d][tap][D];
+#pragma unroll
+            for (int k = D - 1; k >= 0; --k) v = fmaf(v, t, coef[d][tap][k]);
+            myw[d] = sub < W ? v : 0.f;
+        }
+    }
+    float w1[W], w2[W];
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+        w1[a] = __shfl_sync(0xffffffffu, myw[0], gbase + a);
+        w2[a] = __shfl_sync(0xffffffffu, myw[1], gbase + a);
+    }
+    // pg: padded dims; the stencil origin key.{x,y,z} is a padded index too
+    const int64_t s1 = (int64_t)pg.n2 * pg.n3, gsz = (int64_t)pg.n1 * s1;
+    const float2 *base = G + (int64_t)key.x * s1 + (int64_t)key.y * pg.n3 + key.z + tap;
+    float T[NG][2];
+#pragma unroll
+    for (int q = 0; q < NG; ++q) T[q][0] = T[q][1] = 0.f;
+#pragma unroll 1
+    for (int a = 0; a < W; ++a) {
+        float S[NG][2];
+#pragma unroll
+        for (int q = 0; q < NG; ++q) S[q][0] = S[q][1] = 0.f;
+        const float2 *row = base;
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+#pragma unroll
+            for (int q = 0; q < NG; ++q) {
+                const float2 v = __ldg(row + q * gsz);
+                S[q][0] = fmaf(w2[b], v.x, S[q][0]);
+                S[q][1] = fmaf(w2[b], v.y, S[q][1]);
+            }
+            row += pg.n3;
+        }
+#pragma unroll
+        for (int q = 0; q < NG; ++q) {
+            T[q][0] = fmaf(w1[0], S[q][0], T[q][0]);
+            T[q][1] = fmaf(w1[0], S[q][1], T[q][1]);
+        }
+#pragma unroll
+        for (int k = 0; k < W - 1; ++k) w1[k] = w1[k + 1];
+        base += s1;
+    }
+    // f = sum_c w3[c] T_c over the group (lanes >= W contribute 0)
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
+        float re = myw[2] * T[q][0], im = myw[2] * T[q][1];
+#pragma unroll
+        for (int off = GS / 2; off > 0; off >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, off, GS);
+            im += __shfl_xor_sync(0xffffffffu, im, off, GS);
+        }
+        T[q][0] = re;
+        T[q][1] = im;
+    }
+    if (valid && sub == 0) {
+        if (NG == 1) {
+            f[key.w] = make_float2(T[0][0], T[0][1]);
+        } else {
+            if (f) f[key.w] = make_float2(T[0][0], T[0][1]);
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                grad[3 * (int64_t)key.w + d] = make_float2(T[(d + 1) % NG][0], T[(d + 1) % NG][1]);
+        }
+    }
+}
+
+// ---- double-float (FP64 family) ----------------------------------------------
+template <int MM, int NG>
+__global__ void __launch_bounds__(256) gather_col_df_kernel(const float4 *__restrict__ G, Grid3 pg,
+                                                            PointsView<double> pts,
+                                                            const __grid_constant__ PolyDF<MM> P,
+                                                            double2 *__restrict__ f,
+                                                            double2 *__restrict__ grad) {
+    constexpr int W = 2 * MM + 1;
+    constexpr int GS = GroupSize<W>::value;
+    constexpr int D = kPolyDegDF;
+    __shared__ float ch[3][W][D + 1];
+    __shared__ float cl[3][W][D + 1];
+    for (int i = threadIdx.x; i < 3 * W * (D + 1); i += blockDim.x) {
+        (&ch[0][0][0])[i] = (&P.ch[0][0][0])[i];
+        (&cl[0][0][0])[i] = (&P.cl[0][0][0])[i];
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (GS - 1);
+    const int gbase = lane & ~(GS - 1);
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / GS;
+    const bool valid = j < pts.M;
+    const int64_t jj = valid ? j : 0;
+    const int4 key = pts.M > 0 ? pts.key[jj] : make_int4(0, 0, 0, 0);
+    const int tap = sub < W ? sub : 0;
+    float mwh[3], mwl[3];
+    {
+        const double s[3] = {pts.s1[jj], pts.s2[jj], pts.s3[jj]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double t = 2.0 * s[d] - 1.0;
+            const float th = __double2float_rn(t);
+            const float tl = __double2float_rn(t - (double)th);
+            float vh = ch[d][tap][D], vl = cl[d][tap][D];
+#pragma unroll
+            for (int k = D - 1; k >= 0; --k) df_horner_step(vh, vl, th, tl, ch[d][tap][k], cl[d][tap][k]);
+            mwh[d] = sub < W ? vh : 0.f;
+            mwl[d] = sub < W ? vl : 0.f;
+        }
+    }
+    float w1h[W], w1l[W], w2h[W], w2l[W];
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+        w1h[a] = __shfl_sync(0xffffffffu, mwh[0], gbase + a);
+        w1l[a] = __shfl_sync(0xffffffffu, mwl[0], gbase + a);
+        w2h[a] = __shfl_sync(0xffffffffu, mwh[1], gbase + a);
+        w2l[a] = __shfl_sync(0xffffffffu, mwl[1], gbase + a);
+    }
+    const int64_t s1 = (int64_t)pg.n2 * pg.n3, gsz = (int64_t)pg.n1 * s1;
+    const float4 *base = G + (int64_t)key.x * s1 + (int64_t)key.y * pg.n3 + key.z + tap;
+    float T[NG][4];
+#pragma unroll
+    for (int q = 0; q < NG; ++q) T[q][0] = T[q][1] = T[q][2] = T[q][3] = 0.f;
+#pragma unroll 1
+    for (int a = 0; a < W; ++a) {
+        float S[NG][4];
+#pragma unroll
+        for (int q = 0; q < NG; ++q) S[q][0] = S[q][1] = S[q][2] = S[q][3] = 0.f;
+        const float4 *row = base;
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+#pragma unroll
+            for (int q = 0; q < NG; ++q) {
+                const float4 v = __ldg(row + q * gsz);
+                df_mac(S[q][0], S[q][1], v.x, v.y, w2h[b], w2l[b]);
+                df_mac(S[q][2], S[q][3], v.z, v.w, w2h[b], w2l[b]);
+            }
+            row += pg.n3;
+        }
+#pragma unroll
+        for (int q = 0; q < NG; ++q) {
+            df_norm(S[q][0], S[q][1]);
+            df_norm(S[q][2], S[q][3]);
+            df_mac(T[q][0], T[q][1], S[q][0], S[q][1], w1h[0], w1l[0]);
+            df_mac(T[q][2], T[q][3], S[q][2], S[q][3], w1h[0], w1l[0]);
+        }
+#pragma unroll
+        for (int k = 0; k < W - 1; ++k) {
+            w1h[k] = w1h[k + 1];
+            w1l[k] = w1l[k + 1];
+        }
+        base += s1;
+    }
+    double2 out[NG];
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
+        df_norm(T[q][0], T[q][1]);
+        df_norm(T[q][2], T[q][3]);
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        df_mac(rh, rl, T[q][0], T[q][1], mwh[2], mwl[2]);
+        df_mac(ih, il, T[q][2], T[q][3], mwh[2], mwl[2]);
+#pragma unroll
+        for (int off = GS / 2; off > 0; off >>= 1) {
+            const float orh = __shfl_xor_sync(0xffffffffu, rh, off, GS);
+            const float orl = __shfl_xor_sync(0xffffffffu, rl, off, GS);
+            const float oih = __shfl_xor_sync(0xffffffffu, ih, off, GS);
+            const float oil = __shfl_xor_sync(0xffffffffu, il, off, GS);
+            df_add(rh, rl, orh, orl);
+            df_add(ih, il, oih, oil);
+        }
+        out[q].x = (double)rh + (double)rl;
+        out[q].y = (double)ih + (double)il;
+    }
+    if (valid && sub == 0) {
+        if (NG == 1) {
+            f[key.w] = out[0];
+        } else {
+            if (f) f[key.w] = out[0];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) grad[3 * (int64_t)key.w + d] = out[(d + 1) % NG];
+        }
+    }
+}
+
+// P[p1, p2, p3] = g[p1 mod n1, p2 mod n2, p3 mod n3] for ng grids; FP32 copy.
+__global__ void pad_grid_f32_kernel(const float2 *__restrict__ G, Grid3 g, float2 *__restrict__ P,
+                                    Grid3 pg, int ng) {
+    const int64_t psz = (int64_t)pg.n1 * pg.n2 * pg.n3, gsz = (int64_t)g.n1 * g.n2 * g.n3;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ng * psz;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(e / psz);
+        const int64_t r = e - q * psz;
+        int p3 = (int)(r % pg.n3);
+        const int64_t r2 = r / pg.n3;
+        int p2 = (int)(r2 % pg.n2);
+        int p1 = (int)(r2 / pg.n2);
+        while (p1 >= g.n1) p1 -= g.n1;
+        while (p2 >= g.n2) p2 -= g.n2;
+        while (p3 >= g.n3) p3 -= g.n3;
+        P[e] = G[q * gsz + ((int64_t)p1 * g.n2 + p2) * g.n3 + p3];
+    }
+}
+
+// FP64 grids to padded double-float: P[p] = split(g[p mod n]) as (re_hi, re_lo, im_hi, im_lo).
+__global__ void pad_grid_df_kernel(const double2 *__restrict__ G, Grid3 g, float4 *__restrict__ P,
+                                   Grid3 pg, int ng) {
+    const int64_t psz = (int64_t)pg.n1 * pg.n2 * pg.n3, gsz = (int64_t)g.n1 * g.n2 * g.n3;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ng * psz;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(e / psz);
+        const int64_t r = e - q * psz;
+        int p3 = (int)(r % pg.n3);
+        const int64_t r2 = r / pg.n3;
+        int p2 = (int)(r2 % pg.n2);
+        int p1 = (int)(r2 / pg.n2);
+        while (p1 >= g.n1) p1 -= g.n1;
+        while (p2 >= g.n2) p2 -= g.n2;
+        while (p3 >= g.n3) p3 -= g.n3;
+        const double2 v = G[q * gsz + ((int64_t)p1 * g.n2 + p2) * g.n3 + p3];
+        const float rh = __double2float_rn(v.x);
+        const float ih = __double2float_rn(v.y);
+        P[e] = make_float4(rh, __double2float_rn(v.x - (double)rh), ih,
+                           __double2float_rn(v.y - (double)ih));
+    }
+}
+
+int pad_blocks(int64_t total) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (total + 255) / 256, cap = (int64_t)sms * 16;
+    return (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+}
+
+template <int MM, int NG>
+cudaError_t col_f32_dispatch(const float2 *G, Grid3 g, PointsView<float> pts,
+                             const WinTable<float> &w, float2 *f, float2 *grad, cudaStream_t st) {
+    constexpr int GS = GroupSize<2 * MM + 1>::value;
+    const int threads = 256;
+    const int64_t blocks = (pts.M * GS + threads - 1) / threads;
+    gather_col_f32_kernel<MM, NG><<<(unsigned)blocks, threads, 0, st>>>(
+        G, g, pts, make_poly<float, MM>(w), f, grad);
+    return cudaGetLastError();
+}
+
+template <int MM, int NG>
+cudaError_t col_df_dispatch(const float4 *G, Grid3 g, PointsView<double> pts, const WinTableDF &w,
+                            double2 *f, double2 *grad, cudaStream_t st) {
+    constexpr int GS = GroupSize<2 * MM + 1>::value;
+    const int threads = 256;
+    const int64_t blocks = (pts.M * GS + threads - 1) / threads;
+    gather_col_df_kernel<MM, NG><<<(unsigned)blocks, threads, 0, st>>>(
+        G, g, pts, make_poly_df<MM>(w), f, grad);
+    return cudaGetLastError();
+}
+
+template <int NG>
+cudaError_t col_f32_select(const float2 *G, Grid3 g, int m, PointsView<float> pts,
+                           const WinTable<float> &w, float2 *f, float2 *grad, cudaStream_t st) {
+    if (pts.M == 0) return cudaSuccess;
+    switch (m) {
+        case 1: return col_f32_dispatch<1, NG>(G, g, pts, w, f, grad, st);
+        case 2: return col_f32_dispatch<2, NG>(G, g, pts, w, f, grad, st);
+        case 3: return col_f32_dispatch<3, NG>(G, g, pts, w, f, grad, st);
+        case 4: return col_f32_dispatch<4, NG>(G, g, pts, w, f, grad, st);
+        case 5: return col_f32_dispatch<5, NG>(G, g, pts, w, f, grad, st);
+        case 6: return col_f32_dispatch<6, NG>(G, g, pts, w, f, grad, st);
+        case 7: return col_f32_dispatch<7, NG>(G, g, pts, w, f, grad, st);
+        case 8: return col_f32_dispatch<8, NG>(G, g, pts, w, f, grad, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NG>
+cudaError_t col_df_select(const float4 *G, Grid3 g, int m, PointsView<double> pts,
+                          const WinTableDF &w, double2 *f, double2 *grad, cudaStream_t st) {
+    if (pts.M == 0) return cudaSuccess;
+    switch (m) {
+        case 1: return col_df_dispatch<1, NG>(G, g, pts, w, f, grad, st);
+        case 2: return col_df_dispatch<2, NG>(G, g, pts, w, f, grad, st);
+        case 3: return col_df_dispatch<3, NG>(G, g, pts, w, f, grad, st);
+        case 4: return col_df_dispatch<4, NG>(G, g, pts, w, f, grad, st);
+        case 5: return col_df_dispatch<5, NG>(G, g, pts, w, f, grad, st);
+        case 6: return col_df_dispatch<6, NG>(G, g, pts, w, f, grad, st);
+        case 7: return col_df_dispatch<7, NG>(G, g, pts, w, f, grad, st);
+        case 8: return col_df_dispatch<8, NG>(G, g, pts, w, f, grad, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pad_grid_f32(const float2 *G, Grid3 g, float2 *P, Grid3 pg, int ng,
+                                cudaStream_t st) {
+    const int64_t total = (int64_t)ng * pg.n1 * pg.n2 * pg.n3;
+    pad_grid_f32_kernel<<<pad_blocks(total), 256, 0, st>>>(G, g, P, pg, ng);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad_grid_df(const double2 *G, Grid3 g, float4 *P, Grid3 pg, int ng,
+                               cudaStream_t st) {
+    const int64_t total = (int64_t)ng * pg.n1 * pg.n2 * pg.n3;
+    pad_grid_df_kernel<<<pad_blocks(total), 256, 0, st>>>(G, g, P, pg, ng);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_col_f32(const float2 *G, Grid3 g, int m, PointsView<float> pts,
+                                  const WinTable<float> &w, float2 *f, float2 *grad, int ng,
+                                  cudaStream_t st) {
+    return ng == 4 ? col_f32_select<4>(G, g, m, pts, w, f, grad, st)
+                   : col_f32_select<1>(G, g, m, pts, w, f, nullptr, st);
+}
+
+cudaError_t launch_gather_col_df(const float4 *G, Grid3 g, int m, PointsView<double> pts,
+                                 const WinTableDF &w, double2 *f, double2 *grad, int ng,
+                                 cudaStream_t st) {
+    return ng == 4 ? col_df_select<4>(G, g, m, pts, w, f, grad, st)
+                   : col_df_select<1>(G, g, m, pts, w, f, nullptr, st);
+}
+
+}  // namespace gbnfft

@@ -66,6 +66,51 @@ struct Grid3 {
     int n1, n2, n3;
 };
 
+// Double-float window polynomials for the FP64 family's FP32-pipe gather:
+// each coefficient is hi + lo (two floats), degree kPolyDegDF in t.
+constexpr int kPolyDegDF = 16;
+struct WinTableDF {
+    float ch[3][kMaxTaps][kMaxCoef];
+    float cl[3][kMaxTaps][kMaxCoef];
+};
+template <int MM> struct PolyDF {
+    static constexpr int W = 2 * MM + 1;
+    float ch[3][W][kPolyDegDF + 1];
+    float cl[3][W][kPolyDegDF + 1];
+};
+template <int MM> PolyDF<MM> make_poly_df(const WinTableDF &t) {
+    PolyDF<MM> p;
+    for (int d = 0; d < 3; ++d)
+        for (int a = 0; a < PolyDF<MM>::W; ++a)
+            for (int k = 0; k <= kPolyDegDF; ++k) {
+                p.ch[d][a][k] = t.ch[d][a][k];
+                p.cl[d][a][k] = t.cl[d][a][k];
+            }
+    return p;
+}
+
+// ---- launchers implemented in gather_df.cu ---------------------------------
+cudaError_t launch_grid_to_df(double2 *G, int64_t total, cudaStream_t st);
+cudaError_t launch_gather_df(const float4 *G, Grid3 g, int m, PointsView<double> pts,
+                             const WinTableDF &w, double2 *f, cudaStream_t st);
+cudaError_t launch_gather_grad_df(const float4 *G4, Grid3 g, int m, PointsView<double> pts,
+                                  const WinTableDF &w, double2 *f, double2 *grad, cudaStream_t st);
+
+// ---- launchers implemented in gather_col.cu (ng = 1: value, 4: value+gradient)
+// Padded copy P (dims pg = n + 2m) of ng grids: P[p] = g[p mod n]; the _df
+// variant also splits FP64 values into double-float (re_hi, re_lo, im_hi, im_lo).
+cudaError_t launch_pad_grid_f32(const float2 *G, Grid3 g, float2 *P, Grid3 pg, int ng,
+                                cudaStream_t st);
+cudaError_t launch_pad_grid_df(const double2 *G, Grid3 g, float4 *P, Grid3 pg, int ng,
+                               cudaStream_t st);
+// Column-parallel gathers over the padded grid (G = P, g = pg).
+cudaError_t launch_gather_col_f32(const float2 *G, Grid3 g, int m, PointsView<float> pts,
+                                  const WinTable<float> &w, float2 *f, float2 *grad, int ng,
+                                  cudaStream_t st);
+cudaError_t launch_gather_col_df(const float4 *G, Grid3 g, int m, PointsView<double> pts,
+                                 const WinTableDF &w, double2 *f, double2 *grad, int ng,
+                                 cudaStream_t st);
+
 // ---- launchers implemented in kernels.cu (all enqueue on `st`) ------------
 
 template <typename R>

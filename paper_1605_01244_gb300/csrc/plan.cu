@@ -12,6 +12,8 @@ using namespace gbnfft;
 
 namespace {
 
+int ensure_pgrid(nfft3_plan p, int ng);
+
 enum { kFaultNone = 0, kFaultAlloc = 1, kFaultFftPlan = 2 };
 
 int read_fault_env() {
@@ -48,18 +50,22 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? NFFT3_OK : NFFT3_ERR_
 enum { kRecSetPoints = 0, kRecEval = 1, kRecGrad = 2, kRecAdjoint = 3 };
 
 void fold_records(nfft3_plan p) {
+    // stages spanned by consecutive marks, per record kind (-1: unused span)
+    static const int kSpans[4][kTimingMarks - 1] = {
+        {NFFT3_STAGE_SET_POINTS, -1, -1, -1},
+        {NFFT3_STAGE_DECONV, NFFT3_STAGE_FFT, NFFT3_STAGE_SPLIT, NFFT3_STAGE_GATHER},
+        {NFFT3_STAGE_DECONV, NFFT3_STAGE_FFT, NFFT3_STAGE_SPLIT, NFFT3_STAGE_GATHER},
+        {NFFT3_STAGE_SPREAD, NFFT3_STAGE_FFT_FWD, NFFT3_STAGE_DECONV_ADJ, -1}};
     for (int r = 0; r < p->nrec; ++r) {
         cudaEventSynchronize(p->ev[r][kTimingMarks - 1]);
         const int kind = p->rec_kind[r];
-        int first = 0, nst = 0;
-        if (kind == kRecSetPoints) first = NFFT3_STAGE_SET_POINTS, nst = 1;
-        if (kind == kRecEval || kind == kRecGrad) first = NFFT3_STAGE_DECONV, nst = 3;
-        if (kind == kRecAdjoint) first = NFFT3_STAGE_SPREAD, nst = 3;
-        for (int i = 0; i < nst; ++i) {
+        for (int i = 0; i < kTimingMarks - 1; ++i) {
+            const int st = kSpans[kind][i];
+            if (st < 0) continue;
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, p->ev[r][i], p->ev[r][i + 1]) == cudaSuccess) {
-                p->stage_ms[first + i] += ms;
-                p->stage_calls[first + i] += 1;
+                p->stage_ms[st] += ms;
+                p->stage_calls[st] += 1;
             }
         }
     }
@@ -176,29 +182,77 @@ template <typename R> R host_fma(R a, R b, R c);
 template <> double host_fma<double>(double a, double b, double c) { return std::fma(a, b, c); }
 template <> float host_fma<float>(float a, float b, float c) { return std::fmaf(a, b, c); }
 
-// Fill a plan's table for precision R; returns the largest absolute error of
-// the polynomial (evaluated by Horner in R, as the kernels do) on a fine grid of s.
-template <typename R> double build_window_table(WinTable<R> &wt, const double *b, int m) {
-    constexpr int D = PolyDeg<R>::value;
-    double worst = 0;
-    std::memset(&wt, 0, sizeof(wt));
+constexpr int kWindowSamples = 400;  // points of s per tap at which the fits are checked
+
+template <typename R> R horner(const R *c, int D, R t) {
+    R v = c[D];
+    for (int k = D - 1; k >= 0; --k) v = host_fma<R>(v, t, c[k]);
+    return v;
+}
+
+// the double-float Horner of the FP64 family's FP32-pipe gather, step for step
+long double horner_df(const float *ch, const float *cl, int D, double s) {
+    const double t = 2.0 * s - 1.0;
+    const float th = (float)t, tl = (float)(t - (double)th);
+    float vh = ch[D], vl = cl[D];
+    for (int k = D - 1; k >= 0; --k) {
+        const float pp = vh * th;
+        float e = std::fmaf(vh, th, -pp);
+        e = std::fmaf(vh, tl, e);
+        e = std::fmaf(vl, th, e);
+        const float sm = pp + ch[k];
+        const float bb = sm - pp;
+        float err = (pp - (sm - bb)) + (ch[k] - bb);
+        err = err + (e + cl[k]);
+        vh = sm + err;
+        vl = err - (vh - sm);
+    }
+    return (long double)vh + (long double)vl;
+}
+
+// Fit the window polynomials of a plan (FP64 family: FP64 and double-float
+// tables; mixed family: FP32 table) and record the largest absolute error of
+// each evaluation, as the kernels perform it, against the exact weight.
+void build_window_tables(nfft3_plan p) {
+    const int m = p->m;
+    p->window_err = 0;
+    p->window_err_df = 0;
+    std::memset(&p->wt64, 0, sizeof(p->wt64));
+    std::memset(&p->wt32, 0, sizeof(p->wt32));
+    std::memset(&p->wtdf, 0, sizeof(p->wtdf));
     for (int d = 0; d < 3; ++d) {
+        const long double b = (long double)p->b[d];
         for (int a = 0; a <= 2 * m; ++a) {
             long double mono[kMaxCoef];
-            fit_tap(a, m, (long double)b[d], D, mono);
-            for (int k = 0; k <= D; ++k) wt.coef[d][a][k] = (R)mono[k];
-            for (int i = 0; i <= 2000; ++i) {
-                const R s = (R)(i / 2000.0);
-                const R t = (R)2 * s - (R)1;
-                R v = wt.coef[d][a][D];
-                for (int k = D - 1; k >= 0; --k) v = host_fma<R>(v, t, wt.coef[d][a][k]);
-                const long double ex = exact_weight((long double)s, a, m, (long double)b[d]);
-                const double e = (double)fabsl((long double)v - ex);
-                if (e > worst) worst = e;
+            if (p->prec == 64) {
+                fit_tap(a, m, b, PolyDeg<double>::value, mono);
+                for (int k = 0; k <= PolyDeg<double>::value; ++k) p->wt64.coef[d][a][k] = (double)mono[k];
+                fit_tap(a, m, b, kPolyDegDF, mono);
+                for (int k = 0; k <= kPolyDegDF; ++k) {
+                    p->wtdf.ch[d][a][k] = (float)mono[k];
+                    p->wtdf.cl[d][a][k] = (float)(mono[k] - (long double)p->wtdf.ch[d][a][k]);
+                }
+            } else {
+                fit_tap(a, m, b, PolyDeg<float>::value, mono);
+                for (int k = 0; k <= PolyDeg<float>::value; ++k) p->wt32.coef[d][a][k] = (float)mono[k];
+            }
+            for (int i = 0; i <= kWindowSamples; ++i) {
+                const double s = (double)i / kWindowSamples;
+                const long double ex = exact_weight((long double)s, a, m, b);
+                if (p->prec == 64) {
+                    const double v = horner<double>(p->wt64.coef[d][a], PolyDeg<double>::value, 2.0 * s - 1.0);
+                    const double e1 = (double)fabsl((long double)v - ex);
+                    const double e2 = (double)fabsl(horner_df(p->wtdf.ch[d][a], p->wtdf.cl[d][a], kPolyDegDF, s) - ex);
+                    if (e1 > p->window_err) p->window_err = e1;
+                    if (e2 > p->window_err_df) p->window_err_df = e2;
+                } else {
+                    const float v = horner<float>(p->wt32.coef[d][a], PolyDeg<float>::value, (float)(2.0 * s - 1.0));
+                    const double e1 = (double)fabsl((long double)v - ex);
+                    if (e1 > p->window_err) p->window_err = e1;
+                }
             }
         }
     }
-    return worst;
 }
 
 template <typename R> const WinTable<R> &win_table(nfft3_plan p);
@@ -220,6 +274,7 @@ void release(nfft3_plan p) {
         dev_free(p->s[d]);
     }
     dev_free(p->grid);
+    dev_free(p->pgrid);
     void *k = p->key;
     dev_free(k);
     void *v;
@@ -277,8 +332,15 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         p->n[d] = oversampled_size(Ns[d], sigma);
         p->b[d] = M_PI * (2.0 - (double)Ns[d] / (double)p->n[d]);
     }
-    p->window_err = prec == 64 ? build_window_table<double>(p->wt64, p->b, m)
-                               : build_window_table<float>(p->wt32, p->b, m);
+    build_window_tables(p);
+    {
+        // gather variant: col (default) = column-parallel groups (FP32, or
+        // double-float for the FP64 family); thread = one thread per point
+        // (FP32 / double-float); native = one thread per point in the
+        // family's own precision (FP64 on the FP64 pipe)
+        const char *g = std::getenv("GBNFFT_GATHER");
+        p->gather_mode = !g ? 0 : !std::strcmp(g, "thread") ? 1 : !std::strcmp(g, "native") ? 2 : 0;
+    }
     const size_t rs = prec == 64 ? sizeof(double) : sizeof(float);
     int st = NFFT3_OK;
 
@@ -316,6 +378,7 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         p->grid_count = 1;
         st = dev_alloc(p, &p->grid, 2 * rs * nn);
     }
+    if (st == NFFT3_OK && p->gather_mode == 0) st = ensure_pgrid(p, 1);
     if (st == NFFT3_OK) {
         if (p->fault == kFaultFftPlan) {
             st = NFFT3_ERR_CUFFT;
@@ -400,6 +463,67 @@ int set_points_impl(nfft3_plan p, const double *x, int prec) {
     return NFFT3_OK;
 }
 
+// Padded grid storage for ng grids (allocated on first use, kept by the plan).
+int ensure_pgrid(nfft3_plan p, int ng) {
+    if (p->pgrid && p->pgrid_count >= ng) return NFFT3_OK;
+    const int64_t pn = (int64_t)(p->n[0] + 2 * p->m) * (p->n[1] + 2 * p->m) * (p->n[2] + 2 * p->m);
+    const size_t elem = p->prec == 64 ? 16 : 8;   // double-float float4 or float2
+    void *v = nullptr;
+    const int st = dev_alloc(p, &v, elem * pn * ng);
+    if (st != NFFT3_OK) return st;
+    dev_free(p->pgrid);
+    p->pgrid = v;
+    p->pgrid_count = ng;
+    return NFFT3_OK;
+}
+
+// Window gather of ng grids (1: value, 4: value + gradient) after the FFT:
+// the FP64 family splits the grid into double-float (timed as the split
+// stage, mark 3) unless the native FP64 kernel is selected.
+template <typename R>
+cudaError_t gather_stage(nfft3_plan p, typename Cplx<R>::T *G, int ng, typename Cplx<R>::T *f,
+                         typename Cplx<R>::T *grad, int rec) {
+    constexpr int prec = sizeof(R) == 8 ? 64 : 32;
+    const Grid3 g{p->n[0], p->n[1], p->n[2]};
+    const int64_t nn = (int64_t)g.n1 * g.n2 * g.n3;
+    cudaError_t e;
+    if (p->gather_mode == 0) {
+        // padded copy (FP64: split into double-float), then the column gather
+        const int st = ensure_pgrid(p, ng);
+        if (st != NFFT3_OK) return cudaErrorMemoryAllocation;
+        const Grid3 pg{g.n1 + 2 * p->m, g.n2 + 2 * p->m, g.n3 + 2 * p->m};
+        if (prec == 64)
+            e = launch_pad_grid_df((const double2 *)G, g, (float4 *)p->pgrid, pg, ng, p->stream);
+        else
+            e = launch_pad_grid_f32((const float2 *)G, g, (float2 *)p->pgrid, pg, ng, p->stream);
+        if (e != cudaSuccess) return e;
+        rec_mark(p, rec, 3);
+        p->launches += 2;
+        if (prec == 64)
+            return launch_gather_col_df((const float4 *)p->pgrid, pg, p->m, points_view<double>(p),
+                                        p->wtdf, (double2 *)f, (double2 *)grad, ng, p->stream);
+        return launch_gather_col_f32((const float2 *)p->pgrid, pg, p->m, points_view<float>(p),
+                                     p->wt32, (float2 *)f, (float2 *)grad, ng, p->stream);
+    }
+    if (prec == 64 && p->gather_mode == 1) {
+        e = launch_grid_to_df((double2 *)G, ng * nn, p->stream);
+        if (e != cudaSuccess) return e;
+        rec_mark(p, rec, 3);
+        PointsView<double> v = points_view<double>(p);
+        if (ng == 1)
+            e = launch_gather_df((const float4 *)G, g, p->m, v, p->wtdf, (double2 *)f, p->stream);
+        else
+            e = launch_gather_grad_df((const float4 *)G, g, p->m, v, p->wtdf, (double2 *)f,
+                                      (double2 *)grad, p->stream);
+        p->launches += 2;
+        return e;
+    }
+    rec_mark(p, rec, 3);
+    p->launches += 1;
+    if (ng == 1) return launch_gather<R>(G, g, p->m, points_view<R>(p), win_table<R>(p), f, p->stream);
+    return launch_gather_grad<R>(G, g, p->m, points_view<R>(p), win_table<R>(p), f, grad, p->stream);
+}
+
 template <typename R> int eval_impl(nfft3_plan p, const R *c, R *f) {
     using C = typename Cplx<R>::T;
     constexpr int prec = sizeof(R) == 8 ? 64 : 32;
@@ -417,10 +541,10 @@ template <typename R> int eval_impl(nfft3_plan p, const R *c, R *f) {
     rec_mark(p, rec, 1);
     int st = exec_fft(p->fft1, G, prec, CUFFT_INVERSE);
     if (st != NFFT3_OK) return st;
+    p->launches += 1;  // deconv
     rec_mark(p, rec, 2);
-    e = launch_gather<R>(G, g, p->m, points_view<R>(p), win_table<R>(p), (C *)f, p->stream);
-    rec_mark(p, rec, 3);
-    p->launches += 2;
+    e = gather_stage<R>(p, G, 1, (C *)f, nullptr, rec);
+    rec_mark(p, rec, 4);
     return finish(p, cuda_status(e));
 }
 
@@ -468,11 +592,10 @@ template <typename R> int eval_grad_impl(nfft3_plan p, const R *c, R *f, R *grad
     rec_mark(p, rec, 1);
     st = exec_fft(p->fft4, G, prec, CUFFT_INVERSE);
     if (st != NFFT3_OK) return st;
+    p->launches += 1;  // deconv
     rec_mark(p, rec, 2);
-    e = launch_gather_grad<R>(G, g, p->m, points_view<R>(p), win_table<R>(p), (C *)f, (C *)grad,
-                              p->stream);
-    rec_mark(p, rec, 3);
-    p->launches += 2;
+    e = gather_stage<R>(p, G, 4, (C *)f, (C *)grad, rec);
+    rec_mark(p, rec, 4);
     return finish(p, cuda_status(e));
 }
 
@@ -497,6 +620,7 @@ template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
     e = launch_deconv_gather<R>(H, g, (const R *)p->D[0], (const R *)p->D[1], (const R *)p->D[2],
                                 p->N[0], p->N[1], p->N[2], (C *)c_out, p->stream);
     rec_mark(p, rec, 3);
+    rec_end(p, rec, 3);
     p->launches += p->M > 0 ? 2 : 1;
     return finish(p, cuda_status(e));
 }
@@ -611,7 +735,7 @@ int nfft3_plan_info(nfft3_plan p, int *n, int *m, int64_t *M, int *prec) {
 
 int nfft3_window_error(nfft3_plan p, double *max_abs_err) {
     if (!p || !max_abs_err) return NFFT3_ERR_ARG;
-    *max_abs_err = p->window_err;
+    *max_abs_err = p->window_err > p->window_err_df ? p->window_err : p->window_err_df;
     return NFFT3_OK;
 }
 

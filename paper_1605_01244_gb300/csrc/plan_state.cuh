@@ -5,7 +5,7 @@
 #include "internal.cuh"
 
 constexpr int kTimingRecords = 64;
-constexpr int kTimingMarks = 4;
+constexpr int kTimingMarks = 5;
 
 struct nfft3_plan_s {
     int prec;                 // 64 or 32
@@ -19,11 +19,16 @@ struct nfft3_plan_s {
     // window polynomials (both precisions; the family uses one) and their checked error
     gbnfft::WinTable<double> wt64;
     gbnfft::WinTable<float> wt32;
+    gbnfft::WinTableDF wtdf;   // FP64 family: double-float copy for the FP32-pipe gather
     double window_err;
+    double window_err_df;
+    int gather_mode;           // GBNFFT_GATHER: 0 col (default), 1 thread, 2 native (see plan.cu)
     // tables and grid
     void *D[3];               // deconvolution factors, real type of the family
     void *grid;               // n1 n2 n3 complex (x4 once eval_grad ran)
     int grid_count;           // 1 or 4
+    void *pgrid;              // ghost-padded copy for the column gathers, (n+2m)^3 x pgrid_count
+    int pgrid_count;
     cufftHandle fft1;
     cufftHandle fft4;
     int have_fft4;

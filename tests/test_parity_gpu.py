@@ -240,3 +240,37 @@ def test_window_polynomials_accuracy(prec, tol):
             err = ctypes.c_double()
             _lib.call("nfft3_window_error", plan._h, ctypes.byref(err))
             assert err.value <= tol, (sigma, m, err.value)
+
+
+@pytest.mark.parametrize("m", [2, 3, 6, 8])
+def test_gather_variants_agree(m, monkeypatch):
+    """Gather variants selected by GBNFFT_GATHER: col (default: column-parallel
+    groups; FP32 for the mixed family, double-float on the FP32 pipe for the
+    FP64 family), thread (one thread per point) and native (FP64 family on
+    the FP64 pipe).  Every variant must match the CPU NFFT, for eval and
+    eval_grad: to rounding in FP64, to FP32 accuracy in the mixed family."""
+    from paper_1605_01244_gb300 import Plan
+    N = (12, 16, 10)
+    c = wl.gaussian_coeffs(N, 1e9, seed=30 + m)
+    x = wl.mixed_points(900, 0.03, seed=31)
+    ref = None
+    for prec, modes in (("f64", ("col", "thread", "native")), ("f32", ("col", "thread"))):
+        for mode in modes:
+            monkeypatch.setenv("GBNFFT_GATHER", mode)
+            plan = Plan(N, len(x), m=m, precision=prec)
+            plan.set_points(to_dev(x))
+            f = to_np(plan.eval(to_dev(c, CD[prec]))).astype(np.complex128)
+            fg, g = plan.eval_grad(to_dev(c, CD[prec]))
+            fg = to_np(fg).astype(np.complex128)
+            g = to_np(g).astype(np.complex128)
+            if ref is None:
+                ref = nfft_cpu.forward_grad(c, x, plan.n, m)
+            fc, gc = ref
+            if prec == "f64":
+                assert max_rel(f, fc) <= 1e-13, mode
+                assert max_rel(fg, fc) <= 1e-13, mode
+                assert max_rel(g, gc) <= 1e-13, mode
+            else:
+                assert rel_l2(f, fc) <= 2e-6, mode
+                assert rel_l2(fg, fc) <= 2e-6, mode
+                assert rel_l2(g, gc) <= 5e-6, mode
