@@ -63,7 +63,8 @@ enum {
     NFFT3_ERR_CUDA = -4,       /* CUDA launch or runtime error */
     NFFT3_ERR_NO_POINTS = -5,  /* eval/adjoint before a successful set_points */
     NFFT3_ERR_POINTS = -6,     /* a point coordinate is NaN or infinite */
-    NFFT3_ERR_TOO_LARGE = -7   /* a size exceeds the library's limits */
+    NFFT3_ERR_TOO_LARGE = -7,  /* a size exceeds the library's limits */
+    NFFT3_ERR_NO_COEFFS = -8   /* *_stored call without a valid *_precompute */
 };
 
 /*
@@ -129,6 +130,30 @@ int nfft3f_eval_grad(nfft3_plan p, const float *c, float *f, float *grad);
  *   every grid element before reading it, so leftover contents are harmless.
  */
 int nfft3d_eval_grad_noalloc(nfft3_plan p, const double *c, double *f, double *grad);
+
+/*
+ * Evaluate one series at many point sets: nfft3*_precompute runs the
+ * deconvolution, oversampled FFT(s) and padding for c once and keeps the
+ * result in the plan (with_grad != 0: also the three gradient grids);
+ * nfft3*_eval_stored / nfft3*_eval_grad_stored then gather at the points
+ * currently set (f and grad as in eval / eval_grad; grad requires a
+ * with_grad precompute).  set_points keeps the stored grids; eval,
+ * eval_grad and adjoint overwrite them (a later *_stored call returns
+ * NFFT3_ERR_NO_COEFFS).  Default gather mode only.
+ */
+int nfft3d_precompute(nfft3_plan p, const double *c, int with_grad);
+int nfft3f_precompute(nfft3_plan p, const float *c, int with_grad);
+int nfft3d_eval_stored(nfft3_plan p, double *f);
+int nfft3f_eval_stored(nfft3_plan p, float *f);
+int nfft3d_eval_grad_stored(nfft3_plan p, double *f, double *grad);
+int nfft3f_eval_grad_stored(nfft3_plan p, float *f, float *grad);
+
+/*
+ * Use the first M points of the plan's capacity (0 <= M <= the M given at
+ * plan creation): later set_points reads M points and eval writes M values.
+ * Clears the points (set_points must follow).
+ */
+int nfft3_set_num_points(nfft3_plan p, int64_t M);
 
 /* c_out = A^H f  (type-1 adjoint): c_out[k] = sum_j f_j exp(-2 pi i k.x_j). */
 int nfft3d_adjoint(nfft3_plan p, const double *f, double *c_out);
@@ -213,6 +238,56 @@ int nfft3_newton_step(int prec, int64_t M, double *x, const void *f, const void 
  */
 int nfft3_dedupe(int64_t M, const double *x, const int *status, double radius, int *keep,
                  void *stream);
+
+/*
+ * Dense local-grid core detection.
+ * nfft3_lattice_points: x[(i1 R2 + i2) R3 + i3] = lo + i * h (device x, R1 R2 R3 x 3
+ * doubles; lo, h: host arrays of 3), the points at which psi is evaluated.
+ * nfft3_plaquette_crossings: for psi sampled on that lattice (device, R1 R2 R3
+ * complex; double2 for prec 64, float2 for prec 32), finds every lattice face
+ * around which the phase of psi winds by +-2 pi (sum of the four phase
+ * differences, each wrapped into (-pi, pi]) -- a vortex core crosses that
+ * face.  Writes the face centres (out: cap x 3 doubles, torus coordinates)
+ * and out_dir = +-(normal direction 1..3) signed by the winding; *count
+ * (device unsigned long long, zeroed by the call) receives the total number
+ * found, which may exceed cap (then only cap are written).  The paper marks
+ * low-density lattice nodes instead (Sec. 4: rho = |psi|^2 <= 0.0012).
+ */
+int nfft3_lattice_points(double *x, int R1, int R2, int R3, const double *lo, const double *h,
+                         void *stream);
+int nfft3_plaquette_crossings(int prec, const void *psi, int R1, int R2, int R3, const double *lo,
+                              const double *h, double *out, int *out_dir, int64_t cap,
+                              unsigned long long *count, void *stream);
+
+/*
+ * Kernels of the core-proposal CNN (no counterpart in the paper: a learned
+ * proposal stage in front of the NFFT + Newton refinement).  All pointers
+ * are device pointers; activations and weights are BF16 (bit pattern
+ * __nv_bfloat16, passed as void*), accumulations FP32.  Activations are
+ * [B][C][D][D][D] row-major, weights [Cout][Cin][k][k][k] with k = 1 or 3 and
+ * zero padding k/2 (output size = input size), bias [Cout].
+ *   cnn_conv3d_fwd:   y = conv(x, w) + bias, optional ReLU; y_bf16 and/or y_f32.
+ *   cnn_conv3d_dgrad: dx = conv^T(dy, w), times the ReLU mask (relu_mask[i] > 0)
+ *                     of the layer input when relu_mask != NULL.
+ *   cnn_conv3d_wgrad: dw (FP32, same layout as w) and db (FP32, may be NULL).
+ *   cnn_core_loss:    4-channel head y (FP32: logit, 3 offsets) vs target
+ *                     (B D^3 in {0,1}) and off_target (B D^3 x 3): mean BCE,
+ *                     positives weighted by pos_weight, + lam * L1 over the
+ *                     positive voxels (npos of them);
+ *                     writes dy, adds the loss to *loss (caller zeroes it).
+ *   cnn_adam:         Adam step `step` (1-based) on FP32 master weights, also
+ *                     writing the BF16 copy when w_bf16 != NULL.
+ */
+int cnn_conv3d_fwd(const void *x, const void *w, const float *bias, int B, int Cin, int Cout, int D,
+                   int k, int relu, void *y_bf16, float *y_f32, void *stream);
+int cnn_conv3d_dgrad(const float *dy, const void *w, int B, int Cin, int Cout, int D, int k,
+                     const void *relu_mask, float *dx, void *stream);
+int cnn_conv3d_wgrad(const float *dy, const void *x, int B, int Cin, int Cout, int D, int k, float *dw,
+                     float *db, void *stream);
+int cnn_core_loss(const float *y, const float *target, const float *off_target, int B, int D, float lam,
+                  float pos_weight, float npos, float *dy, float *loss, void *stream);
+int cnn_adam(float *w_master, void *w_bf16, const float *g, float *m1, float *m2, int64_t n, float lr,
+             float b1, float b2, float eps, int step, void *stream);
 
 /*
  * CUDA-core FMA throughput of the current device in TFLOP/s (2 flops per FMA),

@@ -22,6 +22,7 @@ NFFT3_ERR_CUDA = -4
 NFFT3_ERR_NO_POINTS = -5
 NFFT3_ERR_POINTS = -6
 NFFT3_ERR_TOO_LARGE = -7
+NFFT3_ERR_NO_COEFFS = -8
 
 # name -> (restype, argtypes)
 _P = ctypes.c_void_p
@@ -40,6 +41,13 @@ SIGNATURES = {
     "nfft3d_eval_grad_noalloc": (_I, [_P, _P, _P, _P]),
     "nfft3d_adjoint": (_I, [_P, _P, _P]),
     "nfft3f_adjoint": (_I, [_P, _P, _P]),
+    "nfft3d_precompute": (_I, [_P, _P, _I]),
+    "nfft3f_precompute": (_I, [_P, _P, _I]),
+    "nfft3d_eval_stored": (_I, [_P, _P]),
+    "nfft3f_eval_stored": (_I, [_P, _P]),
+    "nfft3d_eval_grad_stored": (_I, [_P, _P, _P]),
+    "nfft3f_eval_grad_stored": (_I, [_P, _P, _P]),
+    "nfft3_set_num_points": (_I, [_P, _I64]),
     "nfft3d_eval_host": (_I, [_P, _P, _P, _P]),
     "nfft3f_eval_host": (_I, [_P, _P, _P, _P]),
     "nfft3d_destroy": (_I, [_P]),
@@ -56,6 +64,15 @@ SIGNATURES = {
     "nfft3_fma_peak": (_I, [_I, _I, _P, ctypes.POINTER(_D)]),
     "nfft3_newton_step": (_I, [_I, _I64, _P, _P, _P, _P, _P, _D, _D, _P]),
     "nfft3_dedupe": (_I, [_I64, _P, _P, _D, _P, _P]),
+    "cnn_conv3d_fwd": (_I, [_P, _P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P]),
+    "cnn_conv3d_dgrad": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
+    "cnn_conv3d_wgrad": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
+    "cnn_core_loss": (_I, [_P, _P, _P, _I, _I, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P, _P, _P]),
+    "cnn_adam": (_I, [_P, _P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                      ctypes.c_float, _I, _P]),
+    "nfft3_lattice_points": (_I, [_P, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
+    "nfft3_plaquette_crossings": (_I, [_I, _P, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), _P,
+                                       _P, _I64, _P, _P]),
 }
 
 STAGES = ("set_points", "deconv", "fft", "gather", "spread", "fft_fwd", "deconv_adj", "split")

@@ -1,0 +1,255 @@
+"""Learned vortex-core proposals.
+
+A small fully convolutional 3D network reads psi on the coarse native
+lattice of a local box -- channels (Re psi, Im psi, |psi|^2), scaled by the
+RMS of |psi| -- and predicts for every coarse cell a logit ("a core crosses
+this cell") and a sub-cell offset.  Layers: conv 3^3 (3 -> 16), ReLU,
+conv 3^3 (16 -> 16), ReLU, conv 1^3 (16 -> 4).  Weights and activations are
+BF16 with FP32 accumulation; the optimiser (Adam) keeps FP32 master weights.
+Every forward, backward, loss and optimiser step runs in this project's
+CUDA kernels (``cnn_*`` in the C ABI); torch provides memory only.
+
+Training labels come from the dense judge (``judge``): a coarse cell is
+positive when a fine-lattice core crossing lies in it; the offset target is
+the mean position of the refined core points in the cell.  At inference the
+proposed cells (sigmoid(logit) > tau) are refined at fine resolution only
+inside themselves (``refine_cells``): the plaquette test on their fine
+sub-lattices, aligned with the judge's lattice, followed by Newton.  This
+mirrors the paper's idea of refining only inside vortex tubes (Sec. 3.3,
+sftubeeval3), with the tube chosen by the network instead of by rho <= rhobar.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib, judge, newton
+from .nfft import Plan
+
+LAYERS = ((3, 16, 3, True), (16, 16, 3, True), (16, 4, 1, False))
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class CoreCNN:
+    """The proposal network (parameters on the current CUDA device)."""
+
+    def __init__(self, seed: int = 0):
+        g = np.random.Generator(np.random.PCG64(seed))
+        self.w, self.b, self.wbf = [], [], []
+        for cin, cout, k, _ in LAYERS:
+            fan_in = cin * k ** 3
+            w = g.standard_normal((cout, cin, k, k, k)) * math.sqrt(2.0 / fan_in)
+            wt = torch.from_numpy(w.astype(np.float32)).cuda()
+            self.w.append(wt)
+            self.b.append(torch.zeros(cout, dtype=torch.float32, device="cuda"))
+            self.wbf.append(wt.to(torch.bfloat16))
+        self.m1 = [torch.zeros_like(t) for t in self.w + self.b]
+        self.m2 = [torch.zeros_like(t) for t in self.w + self.b]
+        self.step = 0
+
+    # -- forward -------------------------------------------------------------
+    def forward(self, x: torch.Tensor):
+        """x: (B, 3, D, D, D) bfloat16.  Returns (head FP32 (B, 4, D, D, D), activations)."""
+        B, _, D = x.shape[0], x.shape[1], x.shape[2]
+        acts = [x.contiguous()]
+        head = None
+        for li, (cin, cout, k, relu) in enumerate(LAYERS):
+            if relu:
+                y = torch.empty((B, cout, D, D, D), dtype=torch.bfloat16, device=x.device)
+                _lib.call("cnn_conv3d_fwd", _p(acts[-1]), _p(self.wbf[li]), _p(self.b[li]), B, cin, cout, D,
+                          k, 1, _p(y), None, _stream())
+                acts.append(y)
+            else:
+                head = torch.empty((B, cout, D, D, D), dtype=torch.float32, device=x.device)
+                _lib.call("cnn_conv3d_fwd", _p(acts[-1]), _p(self.wbf[li]), _p(self.b[li]), B, cin, cout, D,
+                          k, 0, None, _p(head), _stream())
+        return head, acts
+
+    def predict(self, x: torch.Tensor):
+        """(probability (B, D, D, D), offsets (B, 3, D, D, D)) in FP32."""
+        head, _ = self.forward(x)
+        return torch.sigmoid(head[:, 0]), head[:, 1:]
+
+    # -- training ------------------------------------------------------------
+    def gradients(self, x, target, off_target, lam: float = 1.0, pos_weight: float = 1.0):
+        """Loss and parameter gradients (FP32) for one batch; returns (loss, [dW..., db...])."""
+        B, D = x.shape[0], x.shape[2]
+        head, acts = self.forward(x)
+        dy = torch.empty_like(head)
+        loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+        npos = float(target.sum().item())
+        _lib.call("cnn_core_loss", _p(head), _p(target.contiguous()), _p(off_target.contiguous()), B, D,
+                  ctypes.c_float(lam), ctypes.c_float(pos_weight), ctypes.c_float(npos), _p(dy), _p(loss),
+                  _stream())
+        dws = [None] * len(LAYERS)
+        dbs = [None] * len(LAYERS)
+        grad = dy
+        for li in range(len(LAYERS) - 1, -1, -1):
+            cin, cout, k, _ = LAYERS[li]
+            dw = torch.empty_like(self.w[li])
+            db = torch.empty_like(self.b[li])
+            _lib.call("cnn_conv3d_wgrad", _p(grad), _p(acts[li]), B, cin, cout, D, k, _p(dw), _p(db), _stream())
+            dws[li], dbs[li] = dw, db
+            if li > 0:
+                dx = torch.empty((B, cin, D, D, D), dtype=torch.float32, device=x.device)
+                # the input of layer li is the ReLU output of layer li-1: mask by it
+                _lib.call("cnn_conv3d_dgrad", _p(grad), _p(self.wbf[li]), B, cin, cout, D, k,
+                          _p(acts[li]), _p(dx), _stream())
+                grad = dx
+        return float(loss.item()), dws + dbs
+
+    def train_step(self, x, target, off_target, lr: float = 2e-3, lam: float = 1.0,
+                   pos_weight: float = 1.0) -> float:
+        loss, grads = self.gradients(x, target, off_target, lam, pos_weight)
+        self.step += 1
+        params = self.w + self.b
+        for i, (p, g) in enumerate(zip(params, grads)):
+            wbf = self.wbf[i] if i < len(self.w) else None
+            _lib.call("cnn_adam", _p(p), _p(wbf), _p(g), _p(self.m1[i]), _p(self.m2[i]), p.numel(),
+                      ctypes.c_float(lr), ctypes.c_float(0.9), ctypes.c_float(0.999), ctypes.c_float(1e-8),
+                      self.step, _stream())
+        return loss
+
+
+# ---- data --------------------------------------------------------------------
+
+@dataclass
+class Box:
+    """Local box on the torus: Dn coarse nodes per dimension, r fine cells per coarse cell."""
+    lo: tuple
+    h_coarse: float
+    Dn: int
+    r: int
+
+    @property
+    def h_fine(self):
+        return self.h_coarse / self.r
+
+    @property
+    def R_fine(self):
+        return (self.Dn - 1) * self.r + 1
+
+    @property
+    def hi(self):
+        return tuple(a + (self.Dn - 1) * self.h_coarse for a in self.lo)
+
+
+def coarse_features(c: torch.Tensor, box: Box, precision: str = "f64", plan: Plan | None = None,
+                    precomputed: bool = False) -> torch.Tensor:
+    """(3, Dn, Dn, Dn) bfloat16 channels of psi on the coarse lattice (NFFT eval)."""
+    R = (box.Dn,) * 3
+    x = judge.lattice(R, box.lo, box.hi, c.device)
+    if plan is None:
+        plan = judge.make_plan(c, x.shape[0], precision)
+    plan.set_num_points(x.shape[0])
+    if not precomputed:
+        plan.precompute(c, with_grad=False)
+    plan.set_points(x)
+    psi = plan.eval_stored().reshape(R)
+    s = torch.sqrt(torch.mean(psi.abs() ** 2)).clamp_min(1e-30)
+    ch = torch.stack([psi.real / s, psi.imag / s, psi.abs() ** 2 / s ** 2]).to(torch.float32)
+    return ch.to(torch.bfloat16).contiguous()
+
+
+def cell_labels(crossings: torch.Tensor, cores: torch.Tensor, box: Box):
+    """target (Dn^3 float32: 1 where a crossing face centre lies in the cell
+    with that lower-corner node) and offset targets (Dn^3 x 3: mean core
+    position in cell units relative to the cell centre)."""
+    Dn = box.Dn
+    lo = torch.tensor(box.lo, dtype=torch.float64, device=crossings.device)
+    target = torch.zeros(Dn ** 3, dtype=torch.float32, device=crossings.device)
+    off = torch.zeros((Dn ** 3, 3), dtype=torch.float32, device=crossings.device)
+    cnt = torch.zeros(Dn ** 3, dtype=torch.float32, device=crossings.device)
+
+    def cell_of(p):
+        idx = torch.floor((p - lo) / box.h_coarse).long()
+        ok = ((idx >= 0) & (idx < Dn - 1)).all(dim=1)
+        return idx, ok
+
+    if crossings.shape[0]:
+        idx, ok = cell_of(crossings)
+        lin = (idx[:, 0] * Dn + idx[:, 1]) * Dn + idx[:, 2]
+        target[lin[ok]] = 1.0
+    if cores.shape[0]:
+        idx, ok = cell_of(cores)
+        lin = (idx[:, 0] * Dn + idx[:, 1]) * Dn + idx[:, 2]
+        rel = ((cores - lo) / box.h_coarse - idx.double() - 0.5).float()
+        off.index_add_(0, lin[ok], rel[ok])
+        cnt.index_add_(0, lin[ok], torch.ones_like(lin[ok], dtype=torch.float32))
+        off = off / cnt.clamp_min(1.0)[:, None]
+    return target, off
+
+
+def proposals(prob: torch.Tensor, tau: float) -> torch.Tensor:
+    """Lower-corner node indices (K, 3) of cells with probability > tau (last node layer excluded)."""
+    Dn = prob.shape[-1]
+    p = prob.reshape(Dn, Dn, Dn)[: Dn - 1, : Dn - 1, : Dn - 1]
+    return torch.nonzero(p > tau)
+
+
+def rho_proposals(feat: torch.Tensor, rho_bar: float) -> torch.Tensor:
+    """Baseline without the network: cells whose minimum scaled rho over their 8
+    corner nodes is below rho_bar (the paper's rho <= rhobar tube test on the
+    coarse lattice)."""
+    rho = feat[2].float()
+    m = rho[:-1, :-1, :-1]
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                m = torch.minimum(m, rho[dz:rho.shape[0] - 1 + dz, dy:rho.shape[1] - 1 + dy,
+                                         dx:rho.shape[2] - 1 + dx])
+    return torch.nonzero(m < rho_bar)
+
+
+def refine_cells(c: torch.Tensor, cells: torch.Tensor, box: Box, precision: str = "f64",
+                 plan: Plan | None = None, precomputed: bool = False):
+    """Core points found inside the given coarse cells: psi on each cell's
+    (r+1)^3 fine sub-lattice (aligned with the judge's lattice), the plaquette
+    test, Newton.  Returns converged points (K, 3).  With a plan whose
+    gradient grids were precomputed for c, no FFT runs here."""
+    K = cells.shape[0]
+    if K == 0:
+        return torch.zeros((0, 3), dtype=torch.float64, device=c.device)
+    r = box.r
+    n1 = r + 1
+    loc = torch.arange(n1, device=c.device, dtype=torch.float64) * box.h_fine
+    g1, g2, g3 = torch.meshgrid(loc, loc, loc, indexing="ij")
+    sub = torch.stack([g1, g2, g3], -1).reshape(1, -1, 3)
+    lo = torch.tensor(box.lo, dtype=torch.float64, device=c.device)
+    origin = lo + cells.double() * box.h_coarse
+    x = (origin[:, None, :] + sub).reshape(-1, 3).contiguous()
+    if plan is None:
+        plan = judge.make_plan(c, x.shape[0], precision)
+    if plan.capacity < x.shape[0]:
+        raise ValueError("plan capacity %d < %d sub-lattice points" % (plan.capacity, x.shape[0]))
+    if not precomputed:
+        plan.precompute(c, with_grad=True)
+    plan.set_num_points(x.shape[0])
+    plan.set_points(x)
+    psi = plan.eval_stored()
+    # stacked along dimension 1 as a (K (r+1), r+1, r+1) lattice with unit spacing;
+    # faces that straddle two blocks along dimension 1 are discarded
+    cr = judge.crossings_from_samples(psi, (K * n1, n1, n1), (0.0, 0.0, 0.0),
+                                      (K * n1 - 1.0, n1 - 1.0, n1 - 1.0))
+    if cr.points.shape[0] == 0:
+        return torch.zeros((0, 3), dtype=torch.float64, device=c.device)
+    i1 = cr.points[:, 0]
+    blk = torch.floor(i1 / n1)
+    li1 = i1 - blk * n1
+    straddle = (li1 > r - 1e-9) & (cr.direction.abs() != 1)
+    keep = ~straddle
+    local = torch.stack([li1, cr.points[:, 1], cr.points[:, 2]], 1)[keep]
+    pts = origin[blk[keep].long()] + local * box.h_fine
+    res = newton.locate(plan, c, pts.contiguous(), precomputed=True)
+    return res.x[res.status == newton.CONVERGED]

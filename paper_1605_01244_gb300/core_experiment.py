@@ -1,0 +1,174 @@
+"""Learned proposals vs the dense judge on swept two-vortex snapshots.
+
+Snapshots: the two-vortex ansatz on [-L, L)^3 with vortex offset a swept from
+0.8 to 0.05 (the reconnection regime as a -> 0), coefficients on the native
+N^3 grid.  A local box around the origin is covered by Dn coarse nodes (the
+native lattice spacing) and by the judge's fine lattice with r fine cells per
+coarse cell.
+
+For each held-out snapshot, three ways to find the cores are compared:
+* dense: the judge on the whole fine lattice (ground truth);
+* learned: CoreCNN proposals, refined only in the proposed cells;
+* rho: the no-network baseline, cells whose corner |psi|^2 is below a level
+  fixed on the training snapshots (the paper's rho <= rhobar tube test).
+The report gives recall against the dense cores (a dense core point is
+recovered when a found point lies within 2 fine spacings), the number of
+refined cells, and CUDA-timed wall time of each path.
+
+``python -m paper_1605_01244_gb300.core_experiment --N 256 --fine 512`` runs
+the full-size configuration (16 snapshots at N = 256^3, 512^3 dense box).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import cnn, judge, workloads
+
+
+def make_box(N: int, L: float, half_width_phys: float, r: int) -> cnn.Box:
+    """Coarse nodes at the native lattice spacing covering [-w, w]^3 (physical)."""
+    h = 1.0 / N                               # native spacing on the torus (2L/N physical)
+    k = int(np.ceil(half_width_phys / (2 * L) / h))
+    return cnn.Box(lo=(-k * h,) * 3, h_coarse=h, Dn=2 * k + 1, r=r)
+
+
+def timed(fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def make_snapshot(N: int, L: float, a: float, box: cnn.Box, plan, precision: str = "f64"):
+    """Coefficients, coarse features and the dense judge's cores of one snapshot.
+    ``plan`` (capacity >= R_fine^3) is reused; its creation is not timed."""
+    c = torch.from_numpy(workloads.gpe_coeffs((N, N, N), L, a)).cuda()
+    if precision == "f32":
+        c = c.to(torch.complex64)
+    feat = cnn.coarse_features(c, box, precision, plan=plan)
+    (cores, cr), t_dense = timed(lambda: judge.dense_cores(c, (box.R_fine,) * 3, box.lo, box.hi, precision,
+                                                          plan=plan))
+    target, off = cell_labels_for(cr, cores, box)
+    return {"a": a, "c": c, "feat": feat, "target": target, "off": off, "cores": cores,
+            "crossings": cr.points, "t_dense": t_dense}
+
+
+def cell_labels_for(cr, cores, box):
+    return cnn.cell_labels(cr.points, cores, box)
+
+
+def train(model: cnn.CoreCNN, snaps, steps: int, lr: float = 3e-3, lam: float = 0.5,
+          pos_weight: float | None = None):
+    """Adam with a decaying rate; positives weighted by a tenth of the class
+    imbalance (at least 1) unless pos_weight is given."""
+    x = torch.stack([s["feat"] for s in snaps]).contiguous()
+    t = torch.stack([s["target"] for s in snaps]).contiguous()
+    o = torch.stack([s["off"] for s in snaps]).contiguous()
+    if pos_weight is None:
+        npos = float(t.sum().item())
+        pos_weight = max(1.0, 0.1 * (t.numel() - npos) / max(npos, 1.0))
+    losses = []
+    for i in range(steps):
+        lr_i = lr * (0.1 ** (i / max(steps - 1, 1)))
+        losses.append(model.train_step(x, t, o, lr=lr_i, lam=lam, pos_weight=pos_weight))
+    return losses
+
+
+def cell_recall(cells: torch.Tensor, snap, box: cnn.Box) -> float:
+    """Fraction of the snapshot's crossing points that lie in the given cells."""
+    pts = snap["crossings"]
+    if pts.shape[0] == 0:
+        return 1.0
+    Dn = box.Dn
+    lo = torch.tensor(box.lo, dtype=torch.float64, device=pts.device)
+    idx = torch.floor((pts - lo) / box.h_coarse).long().clamp(0, Dn - 2)
+    mark = torch.zeros((Dn, Dn, Dn), dtype=torch.bool, device=pts.device)
+    if cells.shape[0]:
+        mark[cells[:, 0], cells[:, 1], cells[:, 2]] = True
+    return float(mark[idx[:, 0], idx[:, 1], idx[:, 2]].float().mean().item())
+
+
+def choose_tau(model, snaps, box, target_recall=0.995):
+    """Largest threshold reaching the target cell recall on every given snapshot."""
+    probs = [model.predict(s["feat"][None])[0][0] for s in snaps]
+    for tau in np.linspace(0.9, 0.01, 90):
+        if all(cell_recall(cnn.proposals(p, float(tau)), s, box) >= target_recall for p, s in zip(probs, snaps)):
+            return float(tau)
+    return 0.01
+
+
+def choose_rho(snaps, box, target_recall=0.995):
+    """Smallest rho level reaching the target cell recall on every given snapshot."""
+    for rho in np.geomspace(1e-4, 2.0, 200):
+        if all(cell_recall(cnn.rho_proposals(s["feat"], float(rho)), s, box) >= target_recall for s in snaps):
+            return float(rho)
+    return 2.0
+
+
+def evaluate(model, snap, box, tau, rho_bar, plan, precision="f64"):
+    """Both proposal paths from the coefficients: coarse features, proposals,
+    one series transform (value + gradient grids), refinement in the proposed
+    cells.  The plan is created beforehand (like the dense judge's)."""
+    radius = 2 * box.h_fine
+    c = snap["c"]
+
+    def learned():
+        plan.precompute(c, with_grad=True)
+        feat = cnn.coarse_features(c, box, precision, plan=plan, precomputed=True)
+        prob, _ = model.predict(feat[None])
+        cells = cnn.proposals(prob[0], tau)
+        return cells, cnn.refine_cells(c, cells, box, precision, plan=plan, precomputed=True)
+
+    def rho_path():
+        plan.precompute(c, with_grad=True)
+        feat = cnn.coarse_features(c, box, precision, plan=plan, precomputed=True)
+        cells = cnn.rho_proposals(feat, rho_bar)
+        return cells, cnn.refine_cells(c, cells, box, precision, plan=plan, precomputed=True)
+
+    (cells_l, found_l), t_l = timed(learned)
+    (cells_r, found_r), t_r = timed(rho_path)
+    truth = snap["cores"]
+    return {
+        "a": snap["a"], "dense_points": int(truth.shape[0]), "t_dense_s": snap["t_dense"],
+        "learned": {"cells": int(cells_l.shape[0]), "recall": judge.recall(found_l, truth, radius), "t_s": t_l},
+        "rho": {"cells": int(cells_r.shape[0]), "recall": judge.recall(found_r, truth, radius), "t_s": t_r},
+        "total_cells": (box.Dn - 1) ** 3,
+    }
+
+
+def run(N=64, L=8.0, half_width=1.5, r=6, steps=1200, precision="f64", seed=0, heldout=(1, 5, 9, 13)):
+    a_values = np.linspace(0.8, 0.05, 16)
+    box = make_box(N, L, half_width, r)
+    probe = torch.zeros((N, N, N), dtype=torch.complex128 if precision == "f64" else torch.complex64,
+                        device="cuda")
+    plan = judge.make_plan(probe, box.R_fine ** 3, precision)
+    snaps = [make_snapshot(N, L, float(a), box, plan, precision) for a in a_values]
+    train_s = [s for i, s in enumerate(snaps) if i not in heldout]
+    test_s = [s for i, s in enumerate(snaps) if i in heldout]
+    model = cnn.CoreCNN(seed)
+    losses, t_train = timed(lambda: train(model, train_s, steps))
+    tau = choose_tau(model, train_s, box)
+    rho_bar = choose_rho(train_s, box)
+    results = [evaluate(model, s, box, tau, rho_bar, plan, precision) for s in test_s]
+    return {"N": N, "fine": box.R_fine, "box_nodes": box.Dn, "tau": tau, "rho_bar": rho_bar,
+            "loss_first": losses[0], "loss_last": losses[-1], "train_s": t_train, "steps": steps,
+            "heldout": results}
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--N", type=int, default=64)
+    ap.add_argument("--fine", type=int, default=0, help="fine lattice nodes per dimension (sets r)")
+    ap.add_argument("--steps", type=int, default=1200)
+    ap.add_argument("--precision", default="f64")
+    args = ap.parse_args()
+    box = make_box(args.N, 8.0, 1.5, 6)
+    r = max(1, round((args.fine - 1) / (box.Dn - 1))) if args.fine else 6
+    out = run(N=args.N, r=r, steps=args.steps, precision=args.precision)
+    print(json.dumps(out))

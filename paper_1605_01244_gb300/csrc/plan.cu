@@ -323,6 +323,7 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
     p->prec = prec;
     p->m = m;
     p->M = M;
+    p->M_cap = M;
     p->stream = (cudaStream_t)stream;
     p->fault = read_fault_env();
     p->sync_check = std::getenv("GBNFFT_SYNC_CHECK") != nullptr;
@@ -533,6 +534,7 @@ template <typename R> int eval_impl(nfft3_plan p, const R *c, R *f) {
     if (p->M == 0) return NFFT3_OK;
     const Grid3 g{p->n[0], p->n[1], p->n[2]};
     C *G = (C *)p->grid;
+    p->stored_ng = 0;
     const int rec = rec_begin(p, kRecEval);
     cudaError_t e = launch_deconv_scatter<R>((const C *)c, p->N[0], p->N[1], p->N[2],
                                              (const R *)p->D[0], (const R *)p->D[1],
@@ -584,6 +586,7 @@ template <typename R> int eval_grad_impl(nfft3_plan p, const R *c, R *f, R *grad
     if (st != NFFT3_OK) return st;
     const Grid3 g{p->n[0], p->n[1], p->n[2]};
     C *G = (C *)p->grid;
+    p->stored_ng = 0;
     const int rec = rec_begin(p, kRecGrad);
     cudaError_t e = launch_deconv_scatter<R>((const C *)c, p->N[0], p->N[1], p->N[2],
                                              (const R *)p->D[0], (const R *)p->D[1],
@@ -599,6 +602,62 @@ template <typename R> int eval_grad_impl(nfft3_plan p, const R *c, R *f, R *grad
     return finish(p, cuda_status(e));
 }
 
+// Deconvolve + FFT + pad the series c into the plan's padded grid(s) and keep
+// them: afterwards eval_stored / eval_grad_stored gather at whatever points
+// are set, without repeating the FFT (column gather mode only).
+template <typename R> int precompute_impl(nfft3_plan p, const R *c, int with_grad) {
+    using C = typename Cplx<R>::T;
+    constexpr int prec = sizeof(R) == 8 ? 64 : 32;
+    if (!p || p->prec != prec || !c || p->gather_mode != 0) return NFFT3_ERR_ARG;
+    const int ng = with_grad ? 4 : 1;
+    int st = ng == 4 ? ensure_grad_grids<R>(p) : NFFT3_OK;
+    if (st == NFFT3_OK) st = ensure_pgrid(p, ng);
+    if (st != NFFT3_OK) return st;
+    p->stored_ng = 0;
+    const Grid3 g{p->n[0], p->n[1], p->n[2]};
+    const Grid3 pg{g.n1 + 2 * p->m, g.n2 + 2 * p->m, g.n3 + 2 * p->m};
+    C *G = (C *)p->grid;
+    cudaError_t e = launch_deconv_scatter<R>((const C *)c, p->N[0], p->N[1], p->N[2],
+                                             (const R *)p->D[0], (const R *)p->D[1],
+                                             (const R *)p->D[2], G, g, ng == 4, p->stream);
+    if (e != cudaSuccess) return NFFT3_ERR_CUDA;
+    st = exec_fft(ng == 4 ? p->fft4 : p->fft1, G, prec, CUFFT_INVERSE);
+    if (st != NFFT3_OK) return st;
+    if (prec == 64)
+        e = launch_pad_grid_df((const double2 *)G, g, (float4 *)p->pgrid, pg, ng, p->stream);
+    else
+        e = launch_pad_grid_f32((const float2 *)G, g, (float2 *)p->pgrid, pg, ng, p->stream);
+    if (e != cudaSuccess) return NFFT3_ERR_CUDA;
+    p->launches += 2;
+    p->stored_ng = ng;
+    return finish(p, NFFT3_OK);
+}
+
+template <typename R> int eval_stored_impl(nfft3_plan p, R *f, R *grad, int ng) {
+    constexpr int prec = sizeof(R) == 8 ? 64 : 32;
+    if (!p || p->prec != prec) return NFFT3_ERR_ARG;
+    if (p->stored_ng < ng) return NFFT3_ERR_NO_COEFFS;
+    if (!p->points_ok) return NFFT3_ERR_NO_POINTS;
+    if (p->M == 0) return NFFT3_OK;
+    if ((ng == 1 && !f) || (ng == 4 && !grad)) return NFFT3_ERR_ARG;
+    const Grid3 g{p->n[0], p->n[1], p->n[2]};
+    const Grid3 pg{g.n1 + 2 * p->m, g.n2 + 2 * p->m, g.n3 + 2 * p->m};
+    const int rec = rec_begin(p, ng == 4 ? kRecGrad : kRecEval);
+    rec_mark(p, rec, 1);
+    rec_mark(p, rec, 2);
+    rec_mark(p, rec, 3);
+    cudaError_t e;
+    if (prec == 64)
+        e = launch_gather_col_df((const float4 *)p->pgrid, pg, p->m, points_view<double>(p), p->wtdf,
+                                 (double2 *)f, (double2 *)grad, ng, p->stream);
+    else
+        e = launch_gather_col_f32((const float2 *)p->pgrid, pg, p->m, points_view<float>(p), p->wt32,
+                                  (float2 *)f, (float2 *)grad, ng, p->stream);
+    rec_mark(p, rec, 4);
+    p->launches += 1;
+    return finish(p, cuda_status(e));
+}
+
 template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
     using C = typename Cplx<R>::T;
     constexpr int prec = sizeof(R) == 8 ? 64 : 32;
@@ -608,6 +667,7 @@ template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
     const Grid3 g{p->n[0], p->n[1], p->n[2]};
     const int64_t nn = (int64_t)g.n1 * g.n2 * g.n3;
     C *H = (C *)p->grid;
+    p->stored_ng = 0;
     const int rec = rec_begin(p, kRecAdjoint);
     cudaError_t e = cudaMemsetAsync(H, 0, sizeof(C) * nn, p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
@@ -698,6 +758,30 @@ int nfft3f_eval_grad(nfft3_plan p, const float *c, float *f, float *grad) {
     return eval_grad_impl<float>(p, c, f, grad);
 }
 
+int nfft3d_precompute(nfft3_plan p, const double *c, int with_grad) {
+    return precompute_impl<double>(p, c, with_grad);
+}
+int nfft3f_precompute(nfft3_plan p, const float *c, int with_grad) {
+    return precompute_impl<float>(p, c, with_grad);
+}
+int nfft3d_eval_stored(nfft3_plan p, double *f) { return eval_stored_impl<double>(p, f, nullptr, 1); }
+int nfft3f_eval_stored(nfft3_plan p, float *f) { return eval_stored_impl<float>(p, f, nullptr, 1); }
+int nfft3d_eval_grad_stored(nfft3_plan p, double *f, double *grad) {
+    return eval_stored_impl<double>(p, f, grad, 4);
+}
+int nfft3f_eval_grad_stored(nfft3_plan p, float *f, float *grad) {
+    return eval_stored_impl<float>(p, f, grad, 4);
+}
+
+int nfft3_set_num_points(nfft3_plan p, int64_t M) {
+    if (!p || M < 0) return NFFT3_ERR_ARG;
+    if (M > p->M_cap) return NFFT3_ERR_TOO_LARGE;
+    p->M = M;
+    p->pb.M = M;
+    p->points_ok = 0;
+    return NFFT3_OK;
+}
+
 int nfft3d_adjoint(nfft3_plan p, const double *f, double *c_out) {
     return adjoint_impl<double>(p, f, c_out);
 }
@@ -786,6 +870,7 @@ const char *nfft3_error_string(int code) {
         case NFFT3_ERR_NO_POINTS: return "no points set";
         case NFFT3_ERR_POINTS: return "non-finite point coordinate";
         case NFFT3_ERR_TOO_LARGE: return "size exceeds library limits";
+        case NFFT3_ERR_NO_COEFFS: return "no precomputed coefficients (call nfft3*_precompute)";
         default: return "unknown status";
     }
 }

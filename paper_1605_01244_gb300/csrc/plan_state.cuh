@@ -10,7 +10,8 @@ constexpr int kTimingMarks = 5;
 struct nfft3_plan_s {
     int prec;                 // 64 or 32
     int N[3], n[3], m;
-    int64_t M;
+    int64_t M;                // points in use (set_points reads M points)
+    int64_t M_cap;            // capacity the point buffers were allocated for
     double b[3];
     cudaStream_t stream;
     int sync_check;           // GBNFFT_SYNC_CHECK set: synchronise after every call
@@ -29,6 +30,7 @@ struct nfft3_plan_s {
     int grid_count;           // 1 or 4
     void *pgrid;              // ghost-padded copy for the column gathers, (n+2m)^3 x pgrid_count
     int pgrid_count;
+    int stored_ng;            // grids precomputed by nfft3*_precompute (0: none valid)
     cufftHandle fft1;
     cufftHandle fft4;
     int have_fft4;

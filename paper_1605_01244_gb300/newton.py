@@ -36,9 +36,12 @@ def _p(t):
 
 
 def locate(plan: Plan, c: torch.Tensor, seeds: torch.Tensor, tol: float | None = None,
-           max_iter: int = 30, max_step: float | None = None) -> NewtonResult:
-    """Newton from ``seeds`` (M x 3 float64 CUDA tensor, M = plan.M).
+           max_iter: int = 30, max_step: float | None = None, precomputed: bool = False) -> NewtonResult:
+    """Newton from ``seeds`` (M x 3 float64 CUDA tensor; the plan's capacity must be >= M).
 
+    The series is deconvolved and transformed once (``precompute`` with the
+    gradient grids; skipped when ``precomputed``), then every iteration is a
+    set_points + stored gather of psi and grad psi + the step kernel.
     tol: |psi| below which a point is converged (default 1e-10 for FP64 plans,
     1e-5 for mixed).  max_step: largest accepted step (default two coarse
     cells, 2 / max N_d).
@@ -47,7 +50,11 @@ def locate(plan: Plan, c: torch.Tensor, seeds: torch.Tensor, tol: float | None =
         tol = 1e-10 if plan.precision == "f64" else 1e-5
     if max_step is None:
         max_step = 2.0 / max(plan.N)
-    M = plan.M
+    M = seeds.shape[0]
+    if plan.M != M:
+        plan.set_num_points(M)
+    if not precomputed:
+        plan.precompute(c, with_grad=True)
     x = seeds.detach().to(torch.float64).clone().contiguous()
     status = torch.zeros(M, dtype=torch.int32, device=x.device)
     resid = torch.full((M,), float("inf"), dtype=torch.float64, device=x.device)
@@ -55,7 +62,7 @@ def locate(plan: Plan, c: torch.Tensor, seeds: torch.Tensor, tol: float | None =
     it = 0
     for it in range(1, max_iter + 1):
         plan.set_points(x)
-        f, g = plan.eval_grad(c)
+        f, g = plan.eval_grad_stored()
         _lib.call("nfft3_newton_step", prec, M, _p(x), _p(f), _p(g), _p(status), _p(resid),
                   float(tol), float(max_step), ctypes.c_void_p(plan.stream.cuda_stream))
         if not bool((status == ACTIVE).any()):

@@ -40,6 +40,7 @@ class Plan:
         self.precision = precision
         self.N = tuple(int(v) for v in N)
         self.M = int(M)
+        self.capacity = int(M)
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = ctypes.c_void_p()
@@ -124,6 +125,32 @@ class Plan:
         self._cuda(out, self.cdtype, self.N, "out")
         _lib.check(self.prefix + "_adjoint", self._fn("_adjoint")(self._h, _ptr(f), _ptr(out)))
         return out
+
+    # -- one series at many point sets -----------------------------------------
+    def precompute(self, c: torch.Tensor, with_grad: bool = False):
+        """Deconvolve, FFT and pad c once; eval_stored / eval_grad_stored reuse it."""
+        self._cuda(c, self.cdtype, self.N, "c")
+        _lib.check(self.prefix + "_precompute", self._fn("_precompute")(self._h, _ptr(c), int(with_grad)))
+
+    def eval_stored(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.M, dtype=self.cdtype, device=self.device)
+        self._cuda(out, self.cdtype, (self.M,), "out")
+        _lib.check(self.prefix + "_eval_stored", self._fn("_eval_stored")(self._h, _ptr(out)))
+        return out
+
+    def eval_grad_stored(self, want_f: bool = True):
+        f = torch.empty(self.M, dtype=self.cdtype, device=self.device) if want_f else None
+        g = torch.empty((self.M, 3), dtype=self.cdtype, device=self.device)
+        _lib.check(self.prefix + "_eval_grad_stored", self._fn("_eval_grad_stored")(self._h, _ptr(f), _ptr(g)))
+        return f, g
+
+    def set_num_points(self, M: int):
+        """Use M points (at most the capacity given at creation); set_points must follow."""
+        if M > self.capacity:
+            raise ValueError("M exceeds the plan's capacity %d" % self.capacity)
+        _lib.call("nfft3_set_num_points", self._h, int(M))
+        self.M = int(M)
 
     def eval_host(self, x_host: torch.Tensor, c_host: torch.Tensor, f_host: torch.Tensor):
         """Host-buffer path: copy x and c in, set points, evaluate, copy f out, synchronise."""

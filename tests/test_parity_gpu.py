@@ -274,3 +274,40 @@ def test_gather_variants_agree(m, monkeypatch):
                 assert rel_l2(f, fc) <= 2e-6, mode
                 assert rel_l2(fg, fc) <= 2e-6, mode
                 assert rel_l2(g, gc) <= 5e-6, mode
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_precompute_then_stored_evaluations(prec):
+    """One transform of c, then value and gradient at several point sets
+    (smaller than the plan's capacity) match eval / eval_grad."""
+    from paper_1605_01244_gb300 import Plan
+    from paper_1605_01244_gb300._lib import NFFT3_ERR_NO_COEFFS
+    N = (16, 12, 20)
+    c = to_dev(wl.gaussian_coeffs(N, 1e9, seed=24), CD[prec])
+    plan = Plan(N, 1000, m=5, precision=prec)
+    ref = Plan(N, 1000, m=5, precision=prec)
+    tol = 1e-13 if prec == "f64" else 2e-6
+    with pytest.raises(NFFTError) as e:
+        plan.set_points(to_dev(wl.uniform_points(1000, seed=25)))
+        plan.eval_stored()
+    assert e.value.code == NFFT3_ERR_NO_COEFFS
+    plan.precompute(c, with_grad=True)
+    for M, seed in ((1000, 26), (333, 27), (1, 28)):
+        x = to_dev(wl.mixed_points(M, 0.04, seed=seed))
+        plan.set_num_points(M)
+        plan.set_points(x)
+        f = to_np(plan.eval_stored()).astype(np.complex128)
+        fg, g = plan.eval_grad_stored()
+        ref.set_num_points(M)
+        ref.set_points(x)
+        fr, gr = ref.eval_grad(c)
+        fr = to_np(fr).astype(np.complex128)
+        gr = to_np(gr).astype(np.complex128)
+        assert max_rel(f, fr) <= tol and max_rel(to_np(fg).astype(np.complex128), fr) <= tol
+        assert max_rel(to_np(g).astype(np.complex128), gr) <= tol
+    # eval overwrites the stored grids
+    plan.eval(c)
+    with pytest.raises(NFFTError):
+        plan.eval_stored()
+    with pytest.raises(ValueError):
+        plan.set_num_points(1001)
