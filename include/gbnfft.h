@@ -188,7 +188,8 @@ int nfft3_window_error(nfft3_plan p, double *max_abs_err);
 /* Change the stream later calls enqueue on. */
 int nfft3_set_stream(nfft3_plan p, void *stream);
 
-/* Wait for the plan's stream and report any asynchronous CUDA error. */
+/* Wait for the plan's stream and report any asynchronous CUDA error (including
+ * a tile-staged gather that gave up waiting for its shared-memory copy). */
 int nfft3_sync(nfft3_plan p);
 
 /* Static description of a status code. */

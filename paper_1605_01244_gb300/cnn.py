@@ -191,11 +191,30 @@ def cell_labels(crossings: torch.Tensor, cores: torch.Tensor, box: Box):
     return target, off
 
 
-def proposals(prob: torch.Tensor, tau: float) -> torch.Tensor:
-    """Lower-corner node indices (K, 3) of cells with probability > tau (last node layer excluded)."""
+def proposals(prob: torch.Tensor, tau: float, hysteresis: float = 1.0) -> torch.Tensor:
+    """Lower-corner node indices (K, 3) of proposed cells (last node layer excluded):
+    cells with probability > tau, plus their face neighbours with probability
+    > tau / hysteresis (cores near a cell face are often split between two
+    cells of moderate probability)."""
     Dn = prob.shape[-1]
     p = prob.reshape(Dn, Dn, Dn)[: Dn - 1, : Dn - 1, : Dn - 1]
-    return torch.nonzero(p > tau)
+    strong = p > tau
+    grown = strong.clone()
+    if hysteresis > 1.0:
+        weak = p > tau / hysteresis
+        for d in range(3):
+            for sh in (1, -1):
+                grown |= weak & torch.roll(strong, sh, dims=d) & _not_wrapped(strong.shape, d, sh, p.device)
+    return torch.nonzero(grown)
+
+
+def _not_wrapped(shape, d, sh, device):
+    """Mask excluding the layer that torch.roll wraps around."""
+    m = torch.ones(shape, dtype=torch.bool, device=device)
+    idx = [slice(None)] * 3
+    idx[d] = 0 if sh > 0 else shape[d] - 1
+    m[tuple(idx)] = False
+    return m
 
 
 def rho_proposals(feat: torch.Tensor, rho_bar: float) -> torch.Tensor:
@@ -223,33 +242,39 @@ def refine_cells(c: torch.Tensor, cells: torch.Tensor, box: Box, precision: str 
         return torch.zeros((0, 3), dtype=torch.float64, device=c.device)
     r = box.r
     n1 = r + 1
+    if plan is None:
+        plan = judge.make_plan(c, K * n1 ** 3, precision)
+    if not precomputed:
+        plan.precompute(c, with_grad=True)
+    per = max(1, plan.capacity // n1 ** 3)    # cells per batch that fit the plan
     loc = torch.arange(n1, device=c.device, dtype=torch.float64) * box.h_fine
     g1, g2, g3 = torch.meshgrid(loc, loc, loc, indexing="ij")
     sub = torch.stack([g1, g2, g3], -1).reshape(1, -1, 3)
     lo = torch.tensor(box.lo, dtype=torch.float64, device=c.device)
-    origin = lo + cells.double() * box.h_coarse
-    x = (origin[:, None, :] + sub).reshape(-1, 3).contiguous()
-    if plan is None:
-        plan = judge.make_plan(c, x.shape[0], precision)
-    if plan.capacity < x.shape[0]:
-        raise ValueError("plan capacity %d < %d sub-lattice points" % (plan.capacity, x.shape[0]))
-    if not precomputed:
-        plan.precompute(c, with_grad=True)
-    plan.set_num_points(x.shape[0])
-    plan.set_points(x)
-    psi = plan.eval_stored()
-    # stacked along dimension 1 as a (K (r+1), r+1, r+1) lattice with unit spacing;
-    # faces that straddle two blocks along dimension 1 are discarded
-    cr = judge.crossings_from_samples(psi, (K * n1, n1, n1), (0.0, 0.0, 0.0),
-                                      (K * n1 - 1.0, n1 - 1.0, n1 - 1.0))
-    if cr.points.shape[0] == 0:
+    found = []
+    for s0 in range(0, K, per):
+        origin = lo + cells[s0:s0 + per].double() * box.h_coarse
+        Kb = origin.shape[0]
+        x = (origin[:, None, :] + sub).reshape(-1, 3).contiguous()
+        plan.set_num_points(x.shape[0])
+        plan.set_points(x)
+        psi = plan.eval_stored()
+        # stacked along dimension 1 as a (Kb (r+1), r+1, r+1) lattice with unit
+        # spacing; faces that straddle two blocks along dimension 1 are discarded
+        cr = judge.crossings_from_samples(psi, (Kb * n1, n1, n1), (0.0, 0.0, 0.0),
+                                          (Kb * n1 - 1.0, n1 - 1.0, n1 - 1.0))
+        if cr.points.shape[0] == 0:
+            continue
+        i1 = cr.points[:, 0]
+        blk = torch.floor(i1 / n1)
+        li1 = i1 - blk * n1
+        keep = ~((li1 > r - 1e-9) & (cr.direction.abs() != 1))
+        local = torch.stack([li1, cr.points[:, 1], cr.points[:, 2]], 1)[keep]
+        found.append(origin[blk[keep].long()] + local * box.h_fine)
+    if not found:
         return torch.zeros((0, 3), dtype=torch.float64, device=c.device)
-    i1 = cr.points[:, 0]
-    blk = torch.floor(i1 / n1)
-    li1 = i1 - blk * n1
-    straddle = (li1 > r - 1e-9) & (cr.direction.abs() != 1)
-    keep = ~straddle
-    local = torch.stack([li1, cr.points[:, 1], cr.points[:, 2]], 1)[keep]
-    pts = origin[blk[keep].long()] + local * box.h_fine
+    pts = torch.cat(found)
+    if pts.shape[0] > plan.capacity:
+        raise ValueError("more crossings than the plan's capacity")
     res = newton.locate(plan, c, pts.contiguous(), precomputed=True)
     return res.x[res.status == newton.CONVERGED]

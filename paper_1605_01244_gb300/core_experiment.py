@@ -30,11 +30,22 @@ import torch
 from . import cnn, judge, workloads
 
 
+# Offset of the lattices from the native grid nodes, in fine spacings per
+# dimension.  The ansatz's core lines lie in the coordinate planes x2 = 0 and
+# x3 = 0 (and on grid nodes for some a); a lattice through those planes puts
+# cores exactly on lattice faces' edges, where the winding test is decided by
+# rounding.  Shifting by fractions of a fine cell keeps every crossing inside
+# a face.
+LATTICE_SHIFT = (0.313, 0.471, 0.229)
+
+
 def make_box(N: int, L: float, half_width_phys: float, r: int) -> cnn.Box:
-    """Coarse nodes at the native lattice spacing covering [-w, w]^3 (physical)."""
+    """Coarse nodes at the native lattice spacing covering [-w, w]^3 (physical),
+    shifted by LATTICE_SHIFT fine spacings."""
     h = 1.0 / N                               # native spacing on the torus (2L/N physical)
     k = int(np.ceil(half_width_phys / (2 * L) / h))
-    return cnn.Box(lo=(-k * h,) * 3, h_coarse=h, Dn=2 * k + 1, r=r)
+    lo = tuple(-k * h + f * h / r for f in LATTICE_SHIFT)
+    return cnn.Box(lo=lo, h_coarse=h, Dn=2 * k + 1, r=r)
 
 
 def timed(fn):
@@ -66,13 +77,13 @@ def cell_labels_for(cr, cores, box):
 def train(model: cnn.CoreCNN, snaps, steps: int, lr: float = 3e-3, lam: float = 0.5,
           pos_weight: float | None = None):
     """Adam with a decaying rate; positives weighted by a tenth of the class
-    imbalance (at least 1) unless pos_weight is given."""
+    imbalance (at least 8) unless pos_weight is given."""
     x = torch.stack([s["feat"] for s in snaps]).contiguous()
     t = torch.stack([s["target"] for s in snaps]).contiguous()
     o = torch.stack([s["off"] for s in snaps]).contiguous()
     if pos_weight is None:
         npos = float(t.sum().item())
-        pos_weight = max(1.0, 0.1 * (t.numel() - npos) / max(npos, 1.0))
+        pos_weight = max(8.0, 0.1 * (t.numel() - npos) / max(npos, 1.0))
     losses = []
     for i in range(steps):
         lr_i = lr * (0.1 ** (i / max(steps - 1, 1)))
@@ -94,16 +105,22 @@ def cell_recall(cells: torch.Tensor, snap, box: cnn.Box) -> float:
     return float(mark[idx[:, 0], idx[:, 1], idx[:, 2]].float().mean().item())
 
 
-def choose_tau(model, snaps, box, target_recall=0.995):
-    """Largest threshold reaching the target cell recall on every given snapshot."""
+def choose_tau(model, snaps, box, target_recall=1.0):
+    """Largest threshold reaching the target cell recall on every given
+    snapshot; if none does, the threshold with the best worst-case recall
+    (the largest such threshold, i.e. the fewest cells)."""
     probs = [model.predict(s["feat"][None])[0][0] for s in snaps]
+    best = (-1.0, 0.01)
     for tau in np.linspace(0.9, 0.01, 90):
-        if all(cell_recall(cnn.proposals(p, float(tau)), s, box) >= target_recall for p, s in zip(probs, snaps)):
+        worst = min(cell_recall(cnn.proposals(p, float(tau)), s, box) for p, s in zip(probs, snaps))
+        if worst >= target_recall:
             return float(tau)
-    return 0.01
+        if worst > best[0] + 1e-12:
+            best = (worst, float(tau))
+    return best[1]
 
 
-def choose_rho(snaps, box, target_recall=0.995):
+def choose_rho(snaps, box, target_recall=1.0):
     """Smallest rho level reaching the target cell recall on every given snapshot."""
     for rho in np.geomspace(1e-4, 2.0, 200):
         if all(cell_recall(cnn.rho_proposals(s["feat"], float(rho)), s, box) >= target_recall for s in snaps):

@@ -9,9 +9,12 @@
 // dimensions (coefficients staged in shared memory), then w1 and w2 are
 // broadcast to the group's registers by shuffles, once per point.
 //
-// The kernels read a ghost-padded copy of the grid, P[p] = g[p mod n] for
-// p in [0, n + 2m) per dimension (written by pad_grid_*), so a stencil never
-// wraps and a row's address is a pointer increment.
+// The kernels read a ghost-padded copy of the grid, P[p] = g[(p - shift) mod n]
+// for p in [0, n + 2m) per dimension (written by pad_grid_*), so a stencil
+// never wraps and a row's address is a pointer increment.  shift = 0 (the
+// column kernels): a stencil with first node l0 starts at padded index l0.
+// shift = m (the tile-staged kernel): it starts at its centre (l0 + m) mod n,
+// so all points of an 8^3 tile of centres read one contiguous box.
 //
 // Two arithmetic variants: FP32 (mixed family) and double-float on the FP32
 // pipe (FP64 family; see gather_df.cu for the arithmetic).
@@ -104,7 +107,7 @@ __global__ void __launch_bounds__(256) gather_col_f32_kernel(const float2 *__res
         w1[a] = __shfl_sync(0xffffffffu, myw[0], gbase + a);
         w2[a] = __shfl_sync(0xffffffffu, myw[1], gbase + a);
     }
-    // pg: padded dims; the stencil origin key.{x,y,z} is a padded index too
+    // pg: padded dims (origin layout): the stencil starts at padded index l0
     const int64_t s1 = (int64_t)pg.n2 * pg.n3, gsz = (int64_t)pg.n1 * s1;
     const float2 *base = G + (int64_t)key.x * s1 + (int64_t)key.y * pg.n3 + key.z + tap;
     float T[NG][2];
@@ -160,8 +163,12 @@ __global__ void __launch_bounds__(256) gather_col_f32_kernel(const float2 *__res
 }
 
 // ---- double-float (FP64 family) ----------------------------------------------
+#ifndef GBNFFT_DF_MINB
+#define GBNFFT_DF_MINB 3   // resident 256-thread blocks per SM the value kernel is compiled for
+#endif
+
 template <int MM, int NG>
-__global__ void __launch_bounds__(256) gather_col_df_kernel(const float4 *__restrict__ G, Grid3 pg,
+__global__ void __launch_bounds__(256, NG == 1 ? GBNFFT_DF_MINB : 2) gather_col_df_kernel(const float4 *__restrict__ G, Grid3 pg,
                                                             PointsView<double> pts,
                                                             const __grid_constant__ PolyDF<MM> P,
                                                             double2 *__restrict__ f,
@@ -274,54 +281,78 @@ __global__ void __launch_bounds__(256) gather_col_df_kernel(const float4 *__rest
     }
 }
 
-// P[p1, p2, p3] = g[p1 mod n1, p2 mod n2, p3 mod n3] for ng grids; FP32 copy.
+// Padded copies P[p1, p2, p3] = g[p1 mod n1, p2 mod n2, p3 mod n3] of ng grids:
+// one block per padded row (q, p1, p2), threads along p3.
+
+// Split an FP64 value into floats hi + lo without FP64 arithmetic: hi keeps
+// the leading 24 significant bits (exact truncation), lo is the remaining 29
+// bits rounded to a float, so hi + lo carries ~48 bits.  Values below 2^-100
+// in magnitude (never reached by the normalised grids) are flushed to zero.
+__device__ __forceinline__ void split_df(double v, float &hi, float &lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned int sign = (unsigned int)(b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 1023 - 100) {
+        hi = __int_as_float(sign);
+        lo = hi;
+        return;
+    }
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    hi = __int_as_float((int)(sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)(mant >> 29)));
+    const int low = (int)(mant & 0x1FFFFFFFull);
+    // low * 2^(e - 1023 - 52), with the sign of v
+    const float lf = ldexpf(__int2float_rn(low), e - 1075);
+    lo = sign ? -lf : lf;
+}
+
+// source index of padded index p: (p - shift) mod n, for p in [0, n + 2m)
+__device__ __forceinline__ int pad_src(int p, int m, int n) {
+    int s = p - m;
+    while (s < 0) s += n;
+    while (s >= n) s -= n;
+    return s;
+}
+
 __global__ void pad_grid_f32_kernel(const float2 *__restrict__ G, Grid3 g, float2 *__restrict__ P,
-                                    Grid3 pg, int ng) {
-    const int64_t psz = (int64_t)pg.n1 * pg.n2 * pg.n3, gsz = (int64_t)g.n1 * g.n2 * g.n3;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ng * psz;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int q = (int)(e / psz);
-        const int64_t r = e - q * psz;
-        int p3 = (int)(r % pg.n3);
-        const int64_t r2 = r / pg.n3;
-        int p2 = (int)(r2 % pg.n2);
-        int p1 = (int)(r2 / pg.n2);
-        while (p1 >= g.n1) p1 -= g.n1;
-        while (p2 >= g.n2) p2 -= g.n2;
-        while (p3 >= g.n3) p3 -= g.n3;
-        P[e] = G[q * gsz + ((int64_t)p1 * g.n2 + p2) * g.n3 + p3];
+                                    Grid3 pg, int ng, int m) {
+    // m here is the layout shift (0 or the window cutoff)
+    const int64_t rows = (int64_t)ng * pg.n1 * pg.n2;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int p2 = (int)(row % pg.n2);
+        const int64_t r = row / pg.n2;
+        const int p1 = (int)(r % pg.n1);
+        const int q = (int)(r / pg.n1);
+        const int s1 = pad_src(p1, m, g.n1), s2 = pad_src(p2, m, g.n2);
+        const float2 *src = G + ((int64_t)q * g.n1 + s1) * g.n2 * g.n3 + (int64_t)s2 * g.n3;
+        float2 *dst = P + row * pg.n3;
+        for (int p3 = threadIdx.x; p3 < pg.n3; p3 += blockDim.x) dst[p3] = src[pad_src(p3, m, g.n3)];
     }
 }
 
-// FP64 grids to padded double-float: P[p] = split(g[p mod n]) as (re_hi, re_lo, im_hi, im_lo).
+// FP64 grids to padded double-float (re_hi, re_lo, im_hi, im_lo).
 __global__ void pad_grid_df_kernel(const double2 *__restrict__ G, Grid3 g, float4 *__restrict__ P,
-                                   Grid3 pg, int ng) {
-    const int64_t psz = (int64_t)pg.n1 * pg.n2 * pg.n3, gsz = (int64_t)g.n1 * g.n2 * g.n3;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ng * psz;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int q = (int)(e / psz);
-        const int64_t r = e - q * psz;
-        int p3 = (int)(r % pg.n3);
-        const int64_t r2 = r / pg.n3;
-        int p2 = (int)(r2 % pg.n2);
-        int p1 = (int)(r2 / pg.n2);
-        while (p1 >= g.n1) p1 -= g.n1;
-        while (p2 >= g.n2) p2 -= g.n2;
-        while (p3 >= g.n3) p3 -= g.n3;
-        const double2 v = G[q * gsz + ((int64_t)p1 * g.n2 + p2) * g.n3 + p3];
-        const float rh = __double2float_rn(v.x);
-        const float ih = __double2float_rn(v.y);
-        P[e] = make_float4(rh, __double2float_rn(v.x - (double)rh), ih,
-                           __double2float_rn(v.y - (double)ih));
+                                   Grid3 pg, int ng, int m) {
+    const int64_t rows = (int64_t)ng * pg.n1 * pg.n2;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int p2 = (int)(row % pg.n2);
+        const int64_t r = row / pg.n2;
+        const int p1 = (int)(r % pg.n1);
+        const int q = (int)(r / pg.n1);
+        const int s1 = pad_src(p1, m, g.n1), s2 = pad_src(p2, m, g.n2);
+        const double2 *src = G + ((int64_t)q * g.n1 + s1) * g.n2 * g.n3 + (int64_t)s2 * g.n3;
+        float4 *dst = P + row * pg.n3;
+        for (int p3 = threadIdx.x; p3 < pg.n3; p3 += blockDim.x) {
+            const double2 v = src[pad_src(p3, m, g.n3)];
+            float4 o;
+            split_df(v.x, o.x, o.y);
+            split_df(v.y, o.z, o.w);
+            dst[p3] = o;
+        }
     }
 }
 
-int pad_blocks(int64_t total) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t want = (total + 255) / 256, cap = (int64_t)sms * 16;
-    return (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+int pad_blocks(int64_t rows) {
+    return (int)(rows < (int64_t)1 << 30 ? rows : (int64_t)1 << 30);
 }
 
 template <int MM, int NG>
@@ -382,17 +413,17 @@ cudaError_t col_df_select(const float4 *G, Grid3 g, int m, PointsView<double> pt
 
 }  // namespace
 
-cudaError_t launch_pad_grid_f32(const float2 *G, Grid3 g, float2 *P, Grid3 pg, int ng,
+cudaError_t launch_pad_grid_f32(const float2 *G, Grid3 g, float2 *P, Grid3 pg, int ng, int shift,
                                 cudaStream_t st) {
-    const int64_t total = (int64_t)ng * pg.n1 * pg.n2 * pg.n3;
-    pad_grid_f32_kernel<<<pad_blocks(total), 256, 0, st>>>(G, g, P, pg, ng);
+    const int64_t rows = (int64_t)ng * pg.n1 * pg.n2;
+    pad_grid_f32_kernel<<<pad_blocks(rows), 128, 0, st>>>(G, g, P, pg, ng, shift);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pad_grid_df(const double2 *G, Grid3 g, float4 *P, Grid3 pg, int ng,
+cudaError_t launch_pad_grid_df(const double2 *G, Grid3 g, float4 *P, Grid3 pg, int ng, int shift,
                                cudaStream_t st) {
-    const int64_t total = (int64_t)ng * pg.n1 * pg.n2 * pg.n3;
-    pad_grid_df_kernel<<<pad_blocks(total), 256, 0, st>>>(G, g, P, pg, ng);
+    const int64_t rows = (int64_t)ng * pg.n1 * pg.n2;
+    pad_grid_df_kernel<<<pad_blocks(rows), 128, 0, st>>>(G, g, P, pg, ng, shift);
     return cudaGetLastError();
 }
 

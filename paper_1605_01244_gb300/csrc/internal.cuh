@@ -97,11 +97,12 @@ cudaError_t launch_gather_grad_df(const float4 *G4, Grid3 g, int m, PointsView<d
                                   const WinTableDF &w, double2 *f, double2 *grad, cudaStream_t st);
 
 // ---- launchers implemented in gather_col.cu (ng = 1: value, 4: value+gradient)
-// Padded copy P (dims pg = n + 2m) of ng grids: P[p] = g[p mod n]; the _df
-// variant also splits FP64 values into double-float (re_hi, re_lo, im_hi, im_lo).
-cudaError_t launch_pad_grid_f32(const float2 *G, Grid3 g, float2 *P, Grid3 pg, int ng,
+// Padded copy P (dims pg = n + 2m) of ng grids: P[p] = g[(p - shift) mod n]
+// (shift 0: column kernels; shift m: tile-staged kernel); the _df variant also
+// splits FP64 values into double-float (re_hi, re_lo, im_hi, im_lo).
+cudaError_t launch_pad_grid_f32(const float2 *G, Grid3 g, float2 *P, Grid3 pg, int ng, int shift,
                                 cudaStream_t st);
-cudaError_t launch_pad_grid_df(const double2 *G, Grid3 g, float4 *P, Grid3 pg, int ng,
+cudaError_t launch_pad_grid_df(const double2 *G, Grid3 g, float4 *P, Grid3 pg, int ng, int shift,
                                cudaStream_t st);
 // Column-parallel gathers over the padded grid (G = P, g = pg).
 cudaError_t launch_gather_col_f32(const float2 *G, Grid3 g, int m, PointsView<float> pts,
@@ -149,11 +150,31 @@ struct PointsBuild {
     int *rank;              // M
     int *scan_tmp;          // scan partials
     int *status;            // device status word (bit 0: non-finite coordinate)
+    void *scratch;          // unsorted reduced points: M_cap int4 + 3 M_cap reals
+    int64_t M_cap;
+    // work list of the tile-staged gather: chunks of <= kChunk points of one tile
+    int *chunk_count;       // ntile + 1 (chunks per tile; last entry 0)
+    int *chunk_start;       // ntile + 1 (exclusive scan; last entry = number of chunks)
+    int4 *chunks;           // (tile, first sorted point, count, 0), chunk_cap entries
+    int64_t chunk_cap;
 };
+
+constexpr int kChunk = 128;   // points per chunk of the tile-staged gather
+
+// Tile-staged FP32 gather (gather_tma.cu).  tmap: a CUtensorMap (128 bytes)
+// from encode_padded_tmap for the padded grid.
+int encode_padded_tmap(void *tmap_out, const void *P, Grid3 pg, int m);
+cudaError_t launch_gather_tma_f32(const void *tmap, const int4 *chunks, int nchunks, int nt2, int nt3,
+                                  Grid3 g, int m, PointsView<float> pts, const WinTable<float> &w,
+                                  float2 *f, int *status, cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R *s2, R *s3,
                           cudaStream_t st);
+
+// Chunk list from tile_start (after launch_points); the number of chunks is
+// left in chunk_start[ntile].
+cudaError_t launch_chunks(PointsBuild &pb, cudaStream_t st);
 
 size_t scan_tmp_ints(int64_t n);
 int scan_launches(int64_t n);   // kernels exclusive_scan enqueues for n entries

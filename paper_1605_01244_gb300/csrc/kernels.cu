@@ -37,9 +37,10 @@ template <typename C> __device__ __forceinline__ C cmul_real(C z, decltype(z.x) 
 
 // ----------------------------------------------------------------------------
 // (a) deconvolve and zero-pad: G[l] = c_k D1[k1] D2[k2] D3[k3] at l = k mod n,
-// zero elsewhere.  One thread per grid element, grid-stride; the fastest
-// dimension is contiguous in both c and G.  With with_grad, four grids are
-// written back to back: G, then 2 pi i k_d G for d = 1..3.
+// zero elsewhere.  One block per grid row (l1, l2), threads along the
+// contiguous dimension l3; whether the row lies in the band |k1|, |k2| < N/2
+// is decided once per row.  With with_grad, four grids are written back to
+// back: G, then 2 pi i k_d G for d = 1..3.
 // ----------------------------------------------------------------------------
 template <typename R>
 __global__ void deconv_scatter_kernel(const typename Cplx<R>::T *__restrict__ c, int N1, int N2,
@@ -49,36 +50,49 @@ __global__ void deconv_scatter_kernel(const typename Cplx<R>::T *__restrict__ c,
     using C = typename Cplx<R>::T;
     const int64_t total = (int64_t)g.n1 * g.n2 * g.n3;
     const R two_pi = (R)6.283185307179586476925286766559;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int l3 = (int)(e % g.n3);
-        const int64_t r = e / g.n3;
-        const int l2 = (int)(r % g.n2);
-        const int l1 = (int)(r / g.n2);
+    const int64_t rows = (int64_t)g.n1 * g.n2;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int l2 = (int)(row % g.n2);
+        const int l1 = (int)(row / g.n2);
         // frequency of grid index l: k = l (l < N/2) or l - n (l >= n - N/2)
-        int k1 = l1 < N1 / 2 ? l1 : (l1 >= g.n1 - N1 / 2 ? l1 - g.n1 : INT32_MIN);
-        int k2 = l2 < N2 / 2 ? l2 : (l2 >= g.n2 - N2 / 2 ? l2 - g.n2 : INT32_MIN);
-        int k3 = l3 < N3 / 2 ? l3 : (l3 >= g.n3 - N3 / 2 ? l3 - g.n3 : INT32_MIN);
-        C v;
-        v.x = 0;
-        v.y = 0;
-        const bool in_band = (k1 != INT32_MIN) && (k2 != INT32_MIN) && (k3 != INT32_MIN);
-        if (in_band) {
-            const int i1 = k1 + N1 / 2, i2 = k2 + N2 / 2, i3 = k3 + N3 / 2;
-            const C cv = c[((int64_t)i1 * N2 + i2) * N3 + i3];
-            const R d = D1[i1] * D2[i2] * D3[i3];
-            v = cmul_real(cv, d);
+        const int k1 = l1 < N1 / 2 ? l1 : (l1 >= g.n1 - N1 / 2 ? l1 - g.n1 : INT32_MIN);
+        const int k2 = l2 < N2 / 2 ? l2 : (l2 >= g.n2 - N2 / 2 ? l2 - g.n2 : INT32_MIN);
+        const bool row_in = k1 != INT32_MIN && k2 != INT32_MIN;
+        C *out = G + row * g.n3;
+        if (!row_in) {
+            C z;
+            z.x = 0;
+            z.y = 0;
+            for (int l3 = threadIdx.x; l3 < g.n3; l3 += blockDim.x) {
+                out[l3] = z;
+                if (with_grad)
+                    for (int d = 1; d < 4; ++d) out[d * total + l3] = z;
+            }
+            continue;
         }
-        G[e] = v;
-        if (with_grad) {
-            const R kk[3] = {(R)(in_band ? k1 : 0), (R)(in_band ? k2 : 0), (R)(in_band ? k3 : 0)};
+        const int i1 = k1 + N1 / 2, i2 = k2 + N2 / 2;
+        const R d12 = D1[i1] * D2[i2];
+        const C *crow = c + ((int64_t)i1 * N2 + i2) * N3;
+        for (int l3 = threadIdx.x; l3 < g.n3; l3 += blockDim.x) {
+            const int k3 = l3 < N3 / 2 ? l3 : (l3 >= g.n3 - N3 / 2 ? l3 - g.n3 : INT32_MIN);
+            C v;
+            v.x = 0;
+            v.y = 0;
+            if (k3 != INT32_MIN) {
+                const int i3 = k3 + N3 / 2;
+                v = cmul_real(crow[i3], d12 * D3[i3]);
+            }
+            out[l3] = v;
+            if (with_grad) {
+                const R kk[3] = {(R)k1, (R)k2, (R)(k3 != INT32_MIN ? k3 : 0)};
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                // 2 pi i k_d v
-                C t;
-                t.x = -two_pi * kk[d] * v.y;
-                t.y = two_pi * kk[d] * v.x;
-                G[(d + 1) * total + e] = t;
+                for (int d = 0; d < 3; ++d) {
+                    // 2 pi i k_d v
+                    C t;
+                    t.x = -two_pi * kk[d] * v.y;
+                    t.y = two_pi * kk[d] * v.x;
+                    out[(d + 1) * total + l3] = t;
+                }
             }
         }
     }
@@ -285,9 +299,9 @@ template <typename R>
 cudaError_t launch_deconv_scatter(const typename Cplx<R>::T *c, int N1, int N2, int N3,
                                   const R *D1, const R *D2, const R *D3, typename Cplx<R>::T *G,
                                   Grid3 g, int with_grad, cudaStream_t st) {
-    const int threads = 256;
-    const int64_t total = (int64_t)g.n1 * g.n2 * g.n3;
-    deconv_scatter_kernel<R><<<grid_blocks(total, threads), threads, 0, st>>>(
+    const int threads = 128;
+    const int64_t rows = (int64_t)g.n1 * g.n2;
+    deconv_scatter_kernel<R><<<(unsigned)(rows < (1ll << 30) ? rows : (1ll << 30)), threads, 0, st>>>(
         c, N1, N2, N3, D1, D2, D3, G, g, with_grad);
     return cudaGetLastError();
 }

@@ -283,11 +283,17 @@ void release(nfft3_plan p) {
     v = p->pb.rank; dev_free(v);
     v = p->pb.scan_tmp; dev_free(v);
     v = p->pb.status; dev_free(v);
+    dev_free(p->pb.scratch);
+    v = p->pb.chunk_count; dev_free(v);
+    v = p->pb.chunk_start; dev_free(v);
+    v = p->pb.chunks; dev_free(v);
     v = p->x_dev; dev_free(v);
     dev_free(p->c_dev);
     dev_free(p->f_dev);
     if (p->fft1) cufftDestroy(p->fft1);
     if (p->have_fft4) cufftDestroy(p->fft4);
+    if (p->fft2d) cufftDestroy(p->fft2d);
+    if (p->fft1d) cufftDestroy(p->fft1d);
     for (int r = 0; r < kTimingRecords; ++r)
         if (p->ev_ready[r])
             for (int i = 0; i < kTimingMarks; ++i) cudaEventDestroy(p->ev[r][i]);
@@ -335,12 +341,18 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
     }
     build_window_tables(p);
     {
-        // gather variant: col (default) = column-parallel groups (FP32, or
-        // double-float for the FP64 family); thread = one thread per point
-        // (FP32 / double-float); native = one thread per point in the
-        // family's own precision (FP64 on the FP64 pipe)
+        // gather variant: default (col) = column-parallel groups over the
+        // padded grid (FP32, or double-float for the FP64 family); tma = the
+        // same, with mixed-family values read from TMA-staged shared-memory
+        // tiles; thread = one thread per point (FP32 / double-float);
+        // native = one thread per point in the family's own precision (FP64
+        // on the FP64 pipe)
         const char *g = std::getenv("GBNFFT_GATHER");
-        p->gather_mode = !g ? 0 : !std::strcmp(g, "thread") ? 1 : !std::strcmp(g, "native") ? 2 : 0;
+        p->gather_mode = !g                           ? 3
+                         : !std::strcmp(g, "thread") ? 1
+                         : !std::strcmp(g, "native") ? 2
+                         : !std::strcmp(g, "tma")    ? 0
+                                                     : 3;
     }
     const size_t rs = prec == 64 ? sizeof(double) : sizeof(float);
     int st = NFFT3_OK;
@@ -379,7 +391,7 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         p->grid_count = 1;
         st = dev_alloc(p, &p->grid, 2 * rs * nn);
     }
-    if (st == NFFT3_OK && p->gather_mode == 0) st = ensure_pgrid(p, 1);
+    if (st == NFFT3_OK && (p->gather_mode == 0 || p->gather_mode == 3)) st = ensure_pgrid(p, 1);
     if (st == NFFT3_OK) {
         if (p->fault == kFaultFftPlan) {
             st = NFFT3_ERR_CUFFT;
@@ -390,6 +402,22 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         } else if (cufftSetStream(p->fft1, p->stream) != CUFFT_SUCCESS) {
             st = NFFT3_ERR_CUFFT;
         }
+    }
+    if (st == NFFT3_OK) {
+        const char *f = std::getenv("GBNFFT_FFT");
+        p->fft_pruned = !(f && !std::strcmp(f, "full"));
+    }
+    if (st == NFFT3_OK && p->fft_pruned) {
+        const cufftType ty = prec == 64 ? CUFFT_Z2Z : CUFFT_C2C;
+        int n2d[2] = {p->n[1], p->n[2]};
+        int n1d[1] = {p->n[0]};
+        const int plane = p->n[1] * p->n[2];
+        if (cufftPlanMany(&p->fft2d, 2, n2d, nullptr, 1, 0, nullptr, 1, 0, ty, p->N[0] / 2) !=
+                CUFFT_SUCCESS ||
+            cufftPlanMany(&p->fft1d, 1, n1d, n1d, plane, 1, n1d, plane, 1, ty, plane) != CUFFT_SUCCESS ||
+            cufftSetStream(p->fft2d, p->stream) != CUFFT_SUCCESS ||
+            cufftSetStream(p->fft1d, p->stream) != CUFFT_SUCCESS)
+            st = NFFT3_ERR_CUFFT;
     }
     // points
     if (st == NFFT3_OK) {
@@ -408,6 +436,12 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (M + 1)), pb.rank = (int *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * scan_tmp_ints(pb.ntile + 1)), pb.scan_tmp = (int *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int)), pb.status = (int *)v;
+        pb.M_cap = M;
+        if (st == NFFT3_OK) st = dev_alloc(p, &pb.scratch, (sizeof(int4) + 3 * rs) * (M + 1));
+        pb.chunk_cap = pb.ntile + M / kChunk + 1;
+        if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1)), pb.chunk_count = (int *)v;
+        if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1)), pb.chunk_start = (int *)v;
+        if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int4) * pb.chunk_cap), pb.chunks = (int4 *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int4) * (M + 1)), p->key = (int4 *)v;
         for (int d = 0; d < 3 && st == NFFT3_OK; ++d) st = dev_alloc(p, &p->s[d], rs * (M + 1));
     }
@@ -438,6 +472,34 @@ int exec_fft(cufftHandle h, void *data, int prec, int direction) {
     return r == CUFFT_SUCCESS ? NFFT3_OK : NFFT3_ERR_CUFFT;
 }
 
+// Oversampled transform of ng consecutive grids.  Full: the 3D plan (batched
+// for ng = 4).  Pruned, inverse: only the planes l1 with |k1| < N1/2 can be
+// nonzero, so 2D FFTs run over those two plane ranges, then 1D FFTs along l1;
+// pruned, forward (adjoint): 1D FFTs along l1, then 2D FFTs over the planes
+// whose output is kept.
+int exec_grid_fft(nfft3_plan p, void *data, int prec, int direction, int ng) {
+    if (!p->fft_pruned) return exec_fft(ng == 4 ? p->fft4 : p->fft1, data, prec, direction);
+    const int64_t plane = (int64_t)p->n[1] * p->n[2];
+    const int64_t nn = plane * p->n[0];
+    const size_t esz = prec == 64 ? sizeof(double2) : sizeof(float2);
+    for (int q = 0; q < ng; ++q) {
+        char *g = (char *)data + esz * nn * q;
+        char *lo = g;                                                // l1 in [0, N1/2)
+        char *hi = g + esz * plane * (int64_t)(p->n[0] - p->N[0] / 2);  // l1 in [n1 - N1/2, n1)
+        int st;
+        if (direction == CUFFT_INVERSE) {
+            if ((st = exec_fft(p->fft2d, lo, prec, direction)) != NFFT3_OK) return st;
+            if ((st = exec_fft(p->fft2d, hi, prec, direction)) != NFFT3_OK) return st;
+            if ((st = exec_fft(p->fft1d, g, prec, direction)) != NFFT3_OK) return st;
+        } else {
+            if ((st = exec_fft(p->fft1d, g, prec, direction)) != NFFT3_OK) return st;
+            if ((st = exec_fft(p->fft2d, lo, prec, direction)) != NFFT3_OK) return st;
+            if ((st = exec_fft(p->fft2d, hi, prec, direction)) != NFFT3_OK) return st;
+        }
+    }
+    return NFFT3_OK;
+}
+
 int set_points_impl(nfft3_plan p, const double *x, int prec) {
     if (!p || p->prec != prec) return NFFT3_ERR_ARG;
     if (!x && p->M > 0) return NFFT3_ERR_ARG;
@@ -452,14 +514,20 @@ int set_points_impl(nfft3_plan p, const double *x, int prec) {
                                  (float *)p->s[2], p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     p->launches += p->M > 0 ? 2 + scan_launches(p->pb.ntile + 1) : scan_launches(p->pb.ntile + 1);
+    if (launch_chunks(p->pb, p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
+    p->launches += 2 + scan_launches(p->pb.ntile + 1);
     rec_mark(p, rec, 1);
     rec_end(p, rec, 1);
-    int status = 0;
+    int status = 0, nch = 0;
     if (cudaMemcpyAsync(&status, p->pb.status, sizeof(int), cudaMemcpyDeviceToHost, p->stream) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaMemcpyAsync(&nch, p->pb.chunk_start + p->pb.ntile, sizeof(int), cudaMemcpyDeviceToHost,
+                        p->stream) != cudaSuccess)
         return NFFT3_ERR_CUDA;
     if (cudaStreamSynchronize(p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
+    if (status & 2) return NFFT3_ERR_CUDA;   // a tile-staged gather timed out on its copy
     if (status & 1) return NFFT3_ERR_POINTS;
+    p->nchunks = nch <= p->pb.chunk_cap ? nch : 0;
     p->points_ok = 1;
     return NFFT3_OK;
 }
@@ -475,7 +543,34 @@ int ensure_pgrid(nfft3_plan p, int ng) {
     dev_free(p->pgrid);
     p->pgrid = v;
     p->pgrid_count = ng;
+    p->tmap_ok = 0;
+    if (p->prec == 32) {
+        const Grid3 pg{p->n[0] + 2 * p->m, p->n[1] + 2 * p->m, p->n[2] + 2 * p->m};
+        p->tmap_ok = encode_padded_tmap(p->tmap, p->pgrid, pg, p->m) == 0;
+    }
     return NFFT3_OK;
+}
+
+// Layout shift of the padded grid: the tile-staged mode needs the stencil
+// centre as origin (shift m), the column kernels read from the first node.
+int pad_shift(nfft3_plan p) { return p->gather_mode == 0 && p->prec == 32 ? p->m : 0; }
+
+// Gather from the padded grid(s): mixed-family values from TMA-staged tiles
+// (tma mode), otherwise the column-parallel kernels.
+template <typename R>
+cudaError_t gather_padded(nfft3_plan p, int ng, typename Cplx<R>::T *f, typename Cplx<R>::T *grad) {
+    constexpr int prec = sizeof(R) == 8 ? 64 : 32;
+    const Grid3 g{p->n[0], p->n[1], p->n[2]};
+    const Grid3 pg{g.n1 + 2 * p->m, g.n2 + 2 * p->m, g.n3 + 2 * p->m};
+    p->launches += 1;
+    if (prec == 64)
+        return launch_gather_col_df((const float4 *)p->pgrid, pg, p->m, points_view<double>(p), p->wtdf,
+                                    (double2 *)f, (double2 *)grad, ng, p->stream);
+    if (ng == 1 && p->gather_mode == 0 && p->tmap_ok && p->nchunks > 0)
+        return launch_gather_tma_f32(p->tmap, p->pb.chunks, p->nchunks, p->pb.nt2, p->pb.nt3, g, p->m,
+                                     points_view<float>(p), p->wt32, (float2 *)f, p->pb.status, p->stream);
+    return launch_gather_col_f32((const float2 *)p->pgrid, pg, p->m, points_view<float>(p), p->wt32,
+                                 (float2 *)f, (float2 *)grad, ng, p->stream);
 }
 
 // Window gather of ng grids (1: value, 4: value + gradient) after the FFT:
@@ -488,23 +583,19 @@ cudaError_t gather_stage(nfft3_plan p, typename Cplx<R>::T *G, int ng, typename 
     const Grid3 g{p->n[0], p->n[1], p->n[2]};
     const int64_t nn = (int64_t)g.n1 * g.n2 * g.n3;
     cudaError_t e;
-    if (p->gather_mode == 0) {
+    if (p->gather_mode == 0 || p->gather_mode == 3) {
         // padded copy (FP64: split into double-float), then the column gather
         const int st = ensure_pgrid(p, ng);
         if (st != NFFT3_OK) return cudaErrorMemoryAllocation;
         const Grid3 pg{g.n1 + 2 * p->m, g.n2 + 2 * p->m, g.n3 + 2 * p->m};
         if (prec == 64)
-            e = launch_pad_grid_df((const double2 *)G, g, (float4 *)p->pgrid, pg, ng, p->stream);
+            e = launch_pad_grid_df((const double2 *)G, g, (float4 *)p->pgrid, pg, ng, pad_shift(p), p->stream);
         else
-            e = launch_pad_grid_f32((const float2 *)G, g, (float2 *)p->pgrid, pg, ng, p->stream);
+            e = launch_pad_grid_f32((const float2 *)G, g, (float2 *)p->pgrid, pg, ng, pad_shift(p), p->stream);
         if (e != cudaSuccess) return e;
         rec_mark(p, rec, 3);
-        p->launches += 2;
-        if (prec == 64)
-            return launch_gather_col_df((const float4 *)p->pgrid, pg, p->m, points_view<double>(p),
-                                        p->wtdf, (double2 *)f, (double2 *)grad, ng, p->stream);
-        return launch_gather_col_f32((const float2 *)p->pgrid, pg, p->m, points_view<float>(p),
-                                     p->wt32, (float2 *)f, (float2 *)grad, ng, p->stream);
+        p->launches += 1;
+        return gather_padded<R>(p, ng, f, grad);
     }
     if (prec == 64 && p->gather_mode == 1) {
         e = launch_grid_to_df((double2 *)G, ng * nn, p->stream);
@@ -541,7 +632,7 @@ template <typename R> int eval_impl(nfft3_plan p, const R *c, R *f) {
                                              (const R *)p->D[2], G, g, 0, p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     rec_mark(p, rec, 1);
-    int st = exec_fft(p->fft1, G, prec, CUFFT_INVERSE);
+    int st = exec_grid_fft(p, G, prec, CUFFT_INVERSE, 1);
     if (st != NFFT3_OK) return st;
     p->launches += 1;  // deconv
     rec_mark(p, rec, 2);
@@ -552,26 +643,31 @@ template <typename R> int eval_impl(nfft3_plan p, const R *c, R *f) {
 
 template <typename R> int ensure_grad_grids(nfft3_plan p) {
     constexpr int prec = sizeof(R) == 8 ? 64 : 32;
-    if (p->grid_count == 4 && p->have_fft4) return NFFT3_OK;
+    if (p->grid_count == 4 && (p->have_fft4 || p->fft_pruned)) return NFFT3_OK;
     const int64_t nn = (int64_t)p->n[0] * p->n[1] * p->n[2];
     void *g4 = nullptr;
     int st = dev_alloc(p, &g4, 2 * sizeof(R) * nn * 4);
     if (st != NFFT3_OK) return st;
-    int dims[3] = {p->n[0], p->n[1], p->n[2]};
-    cufftHandle h;
-    if (p->fault == kFaultFftPlan ||
-        cufftPlanMany(&h, 3, dims, nullptr, 1, (int)0, nullptr, 1, 0,
-                      prec == 64 ? CUFFT_Z2Z : CUFFT_C2C, 4) != CUFFT_SUCCESS) {
+    if (p->fault == kFaultFftPlan) {
         cudaFree(g4);
         return NFFT3_ERR_CUFFT;
     }
-    cufftSetStream(h, p->stream);
-    // the batched plan uses the default layout: distance n1 n2 n3 between transforms
+    if (!p->fft_pruned) {
+        // batched 3D plan; default layout: distance n1 n2 n3 between transforms
+        int dims[3] = {p->n[0], p->n[1], p->n[2]};
+        cufftHandle h;
+        if (cufftPlanMany(&h, 3, dims, nullptr, 1, (int)0, nullptr, 1, 0,
+                          prec == 64 ? CUFFT_Z2Z : CUFFT_C2C, 4) != CUFFT_SUCCESS) {
+            cudaFree(g4);
+            return NFFT3_ERR_CUFFT;
+        }
+        cufftSetStream(h, p->stream);
+        p->fft4 = h;
+        p->have_fft4 = 1;
+    }
     dev_free(p->grid);
     p->grid = g4;
     p->grid_count = 4;
-    p->fft4 = h;
-    p->have_fft4 = 1;
     return NFFT3_OK;
 }
 
@@ -593,7 +689,7 @@ template <typename R> int eval_grad_impl(nfft3_plan p, const R *c, R *f, R *grad
                                              (const R *)p->D[2], G, g, 1, p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     rec_mark(p, rec, 1);
-    st = exec_fft(p->fft4, G, prec, CUFFT_INVERSE);
+    st = exec_grid_fft(p, G, prec, CUFFT_INVERSE, 4);
     if (st != NFFT3_OK) return st;
     p->launches += 1;  // deconv
     rec_mark(p, rec, 2);
@@ -608,7 +704,7 @@ template <typename R> int eval_grad_impl(nfft3_plan p, const R *c, R *f, R *grad
 template <typename R> int precompute_impl(nfft3_plan p, const R *c, int with_grad) {
     using C = typename Cplx<R>::T;
     constexpr int prec = sizeof(R) == 8 ? 64 : 32;
-    if (!p || p->prec != prec || !c || p->gather_mode != 0) return NFFT3_ERR_ARG;
+    if (!p || p->prec != prec || !c || (p->gather_mode != 0 && p->gather_mode != 3)) return NFFT3_ERR_ARG;
     const int ng = with_grad ? 4 : 1;
     int st = ng == 4 ? ensure_grad_grids<R>(p) : NFFT3_OK;
     if (st == NFFT3_OK) st = ensure_pgrid(p, ng);
@@ -621,12 +717,12 @@ template <typename R> int precompute_impl(nfft3_plan p, const R *c, int with_gra
                                              (const R *)p->D[0], (const R *)p->D[1],
                                              (const R *)p->D[2], G, g, ng == 4, p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
-    st = exec_fft(ng == 4 ? p->fft4 : p->fft1, G, prec, CUFFT_INVERSE);
+    st = exec_grid_fft(p, G, prec, CUFFT_INVERSE, ng);
     if (st != NFFT3_OK) return st;
     if (prec == 64)
-        e = launch_pad_grid_df((const double2 *)G, g, (float4 *)p->pgrid, pg, ng, p->stream);
+        e = launch_pad_grid_df((const double2 *)G, g, (float4 *)p->pgrid, pg, ng, pad_shift(p), p->stream);
     else
-        e = launch_pad_grid_f32((const float2 *)G, g, (float2 *)p->pgrid, pg, ng, p->stream);
+        e = launch_pad_grid_f32((const float2 *)G, g, (float2 *)p->pgrid, pg, ng, pad_shift(p), p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     p->launches += 2;
     p->stored_ng = ng;
@@ -640,21 +736,12 @@ template <typename R> int eval_stored_impl(nfft3_plan p, R *f, R *grad, int ng) 
     if (!p->points_ok) return NFFT3_ERR_NO_POINTS;
     if (p->M == 0) return NFFT3_OK;
     if ((ng == 1 && !f) || (ng == 4 && !grad)) return NFFT3_ERR_ARG;
-    const Grid3 g{p->n[0], p->n[1], p->n[2]};
-    const Grid3 pg{g.n1 + 2 * p->m, g.n2 + 2 * p->m, g.n3 + 2 * p->m};
     const int rec = rec_begin(p, ng == 4 ? kRecGrad : kRecEval);
     rec_mark(p, rec, 1);
     rec_mark(p, rec, 2);
     rec_mark(p, rec, 3);
-    cudaError_t e;
-    if (prec == 64)
-        e = launch_gather_col_df((const float4 *)p->pgrid, pg, p->m, points_view<double>(p), p->wtdf,
-                                 (double2 *)f, (double2 *)grad, ng, p->stream);
-    else
-        e = launch_gather_col_f32((const float2 *)p->pgrid, pg, p->m, points_view<float>(p), p->wt32,
-                                  (float2 *)f, (float2 *)grad, ng, p->stream);
+    const cudaError_t e = gather_padded<R>(p, ng, (typename Cplx<R>::T *)f, (typename Cplx<R>::T *)grad);
     rec_mark(p, rec, 4);
-    p->launches += 1;
     return finish(p, cuda_status(e));
 }
 
@@ -674,7 +761,7 @@ template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
     e = launch_spread<R>((const C *)f, g, p->m, points_view<R>(p), win_table<R>(p), H, p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     rec_mark(p, rec, 1);
-    int st = exec_fft(p->fft1, H, prec, CUFFT_FORWARD);
+    int st = exec_grid_fft(p, H, prec, CUFFT_FORWARD, 1);
     if (st != NFFT3_OK) return st;
     rec_mark(p, rec, 2);
     e = launch_deconv_gather<R>(H, g, (const R *)p->D[0], (const R *)p->D[1], (const R *)p->D[2],
@@ -833,7 +920,12 @@ int nfft3_set_stream(nfft3_plan p, void *stream) {
 
 int nfft3_sync(nfft3_plan p) {
     if (!p) return NFFT3_ERR_ARG;
+    int status = 0;
+    if (cudaMemcpyAsync(&status, p->pb.status, sizeof(int), cudaMemcpyDeviceToHost, p->stream) !=
+        cudaSuccess)
+        return NFFT3_ERR_CUDA;
     if (cudaStreamSynchronize(p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
+    if (status & 2) return NFFT3_ERR_CUDA;   // a tile-staged gather gave up waiting for its copy
     return cudaGetLastError() == cudaSuccess ? NFFT3_OK : NFFT3_ERR_CUDA;
 }
 

@@ -31,9 +31,17 @@ struct nfft3_plan_s {
     void *pgrid;              // ghost-padded copy for the column gathers, (n+2m)^3 x pgrid_count
     int pgrid_count;
     int stored_ng;            // grids precomputed by nfft3*_precompute (0: none valid)
+    alignas(64) unsigned char tmap[128];  // CUtensorMap of the padded FP32 grid (tile-staged gather)
+    int tmap_ok;
+    int nchunks;              // chunks of the tile-staged gather for the current points
     cufftHandle fft1;
     cufftHandle fft4;
     int have_fft4;
+    // pruned transform (default; GBNFFT_FFT=full uses fft1/fft4): batched 2D
+    // FFTs over the planes l1 with |k1| < N1/2, then 1D FFTs along l1
+    int fft_pruned;
+    cufftHandle fft2d;        // n2 x n3, batch N1/2 planes
+    cufftHandle fft1d;        // length n1, stride n2 n3, batch n2 n3
     // points
     int points_ok;
     int4 *key;

@@ -22,8 +22,13 @@ __device__ __forceinline__ Reduced reduce_coord(double x, int n, int m, int *sta
         x = 0.0;
     }
     // explicit round-to-nearest steps: no contraction into FMAs, so that the
-    // stencil choice at exact half-integer u is reproducible
-    const double xw = __dsub_rn(x, floor(__dadd_rn(x, 0.5)));
+    // stencil choice at exact half-integer u is reproducible.  Coordinates
+    // already in [-1/2, 1/2) (|x| < 1/2, or x = -1/2; tested on the bits,
+    // without FP64 arithmetic) skip the wrap, whose result they equal.
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long mag = bits & 0x7FFFFFFFFFFFFFFFull;
+    const bool in_range = mag < 0x3FE0000000000000ull || bits == 0xBFE0000000000000ull;
+    const double xw = in_range ? x : __dsub_rn(x, floor(__dadd_rn(x, 0.5)));
     const double u = __dmul_rn((double)n, __dadd_rn(xw, 0.5));
     const double v = __dsub_rn(u, (double)m + 0.5);
     const double l0 = ceil(v);
@@ -43,7 +48,12 @@ __device__ __forceinline__ int tile_coord(int l0, int m, int n) {
     return c / kTile;
 }
 
-__global__ void points_count_kernel(const double *__restrict__ x, PointsBuild pb) {
+// Pass 1: reduce every point once (FP64), store the result unsorted in the
+// scratch arrays (key with the point's tile in .w, offsets), and count the
+// points per tile; the returned count is the point's rank within its tile.
+template <typename R>
+__global__ void points_count_kernel(const double *__restrict__ x, PointsBuild pb,
+                                    int4 *__restrict__ key_tmp, R *__restrict__ s_tmp) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < pb.M;
          j += (int64_t)gridDim.x * blockDim.x) {
         const Reduced r1 = reduce_coord(x[3 * j + 0], pb.g.n1, pb.m, pb.status);
@@ -54,27 +64,26 @@ __global__ void points_count_kernel(const double *__restrict__ x, PointsBuild pb
         const int t3 = tile_coord(r3.l0, pb.m, pb.g.n3);
         const int64_t t = ((int64_t)t1 * pb.nt2 + t2) * pb.nt3 + t3;
         pb.rank[j] = atomicAdd(&pb.tile_count[t], 1);
+        key_tmp[j] = make_int4(r1.l0, r2.l0, r3.l0, (int)t);
+        s_tmp[3 * j + 0] = (R)r1.s;
+        s_tmp[3 * j + 1] = (R)r2.s;
+        s_tmp[3 * j + 2] = (R)r3.s;
     }
 }
 
+// Pass 2: move every point to tile_start[tile] + rank.
 template <typename R>
-__global__ void points_scatter_kernel(const double *__restrict__ x, PointsBuild pb,
-                                      int4 *__restrict__ key, R *__restrict__ s1,
-                                      R *__restrict__ s2, R *__restrict__ s3) {
+__global__ void points_scatter_kernel(PointsBuild pb, const int4 *__restrict__ key_tmp,
+                                      const R *__restrict__ s_tmp, int4 *__restrict__ key,
+                                      R *__restrict__ s1, R *__restrict__ s2, R *__restrict__ s3) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < pb.M;
          j += (int64_t)gridDim.x * blockDim.x) {
-        const Reduced r1 = reduce_coord(x[3 * j + 0], pb.g.n1, pb.m, pb.status);
-        const Reduced r2 = reduce_coord(x[3 * j + 1], pb.g.n2, pb.m, pb.status);
-        const Reduced r3 = reduce_coord(x[3 * j + 2], pb.g.n3, pb.m, pb.status);
-        const int t1 = tile_coord(r1.l0, pb.m, pb.g.n1);
-        const int t2 = tile_coord(r2.l0, pb.m, pb.g.n2);
-        const int t3 = tile_coord(r3.l0, pb.m, pb.g.n3);
-        const int64_t t = ((int64_t)t1 * pb.nt2 + t2) * pb.nt3 + t3;
-        const int64_t pos = (int64_t)pb.tile_start[t] + pb.rank[j];
-        key[pos] = make_int4(r1.l0, r2.l0, r3.l0, (int)j);
-        s1[pos] = (R)r1.s;
-        s2[pos] = (R)r2.s;
-        s3[pos] = (R)r3.s;
+        const int4 k = key_tmp[j];
+        const int64_t pos = (int64_t)pb.tile_start[k.w] + pb.rank[j];
+        key[pos] = make_int4(k.x, k.y, k.z, (int)j);
+        s1[pos] = s_tmp[3 * j + 0];
+        s2[pos] = s_tmp[3 * j + 1];
+        s3[pos] = s_tmp[3 * j + 2];
     }
 }
 
@@ -158,6 +167,26 @@ cudaError_t exclusive_scan(const int *in, int *out, int64_t n, int *tmp, cudaStr
     return cudaGetLastError();
 }
 
+__global__ void chunk_count_kernel(PointsBuild pb) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= pb.ntile;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int cnt = t < pb.ntile ? pb.tile_start[t + 1] - pb.tile_start[t] : 0;
+        pb.chunk_count[t] = (cnt + kChunk - 1) / kChunk;
+    }
+}
+
+__global__ void chunk_fill_kernel(PointsBuild pb) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < pb.ntile;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int first = pb.tile_start[t], cnt = pb.tile_start[t + 1] - first;
+        const int base = pb.chunk_start[t];
+        for (int k = 0; k * kChunk < cnt; ++k) {
+            const int n = cnt - k * kChunk < kChunk ? cnt - k * kChunk : kChunk;
+            if (base + k < pb.chunk_cap) pb.chunks[base + k] = make_int4((int)t, first + k * kChunk, n, 0);
+        }
+    }
+}
+
 int point_blocks(int64_t M) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -193,17 +222,30 @@ cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R 
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(pb.status, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
+    int4 *key_tmp = (int4 *)pb.scratch;
+    R *s_tmp = (R *)((char *)pb.scratch + sizeof(int4) * pb.M_cap);
     if (pb.M > 0) {
-        points_count_kernel<<<point_blocks(pb.M), 256, 0, st>>>(x, pb);
+        points_count_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(x, pb, key_tmp, s_tmp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     e = exclusive_scan(pb.tile_count, pb.tile_start, pb.ntile + 1, pb.scan_tmp, st);
     if (e != cudaSuccess) return e;
     if (pb.M > 0) {
-        points_scatter_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(x, pb, key, s1, s2, s3);
+        points_scatter_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(pb, key_tmp, s_tmp, key, s1, s2, s3);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_chunks(PointsBuild &pb, cudaStream_t st) {
+    const int64_t n = pb.ntile + 1;
+    chunk_count_kernel<<<point_blocks(n), 256, 0, st>>>(pb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = exclusive_scan(pb.chunk_count, pb.chunk_start, n, pb.scan_tmp, st);
+    if (e != cudaSuccess) return e;
+    chunk_fill_kernel<<<point_blocks(pb.ntile), 256, 0, st>>>(pb);
+    return cudaGetLastError();
 }
 
 template cudaError_t launch_points<double>(const double *, PointsBuild &, int4 *, double *,

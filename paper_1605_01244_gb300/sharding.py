@@ -1,0 +1,36 @@
+"""Multi-GPU sharding of the evaluation: independent point batches per rank.
+
+Points are independent once the oversampled grid exists, so the evaluation
+shards by points with no data-path collective: every rank holds the same
+coefficients and evaluates its own points (weak scaling: a fixed number of
+points per rank).  The only collective is the timing reduction, the
+maximum step time over ranks.  (The adjoint would need a sum all-reduce of
+the N^3 coefficients; it is not part of the timed step.)
+"""
+from __future__ import annotations
+
+import torch
+
+
+def point_seed(rank: int, base: int = 100) -> int:
+    """Seed of rank r's point batch (distinct batches per rank)."""
+    return base + 7919 * rank
+
+
+def shard_range(M_total: int, rank: int, world: int):
+    """Contiguous [start, stop) slice of M_total points owned by ``rank``
+    (a strong-scaling split of one point set; sizes differ by at most one)."""
+    q, r = divmod(M_total, world)
+    start = rank * q + min(rank, r)
+    return start, start + q + (1 if rank < r else 0)
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Maximum of a per-rank scalar (e.g. a step time) over the process group;
+    the value itself when torch.distributed is not initialised."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())

@@ -244,19 +244,22 @@ def test_window_polynomials_accuracy(prec, tol):
 
 @pytest.mark.parametrize("m", [2, 3, 6, 8])
 def test_gather_variants_agree(m, monkeypatch):
-    """Gather variants selected by GBNFFT_GATHER: col (default: column-parallel
-    groups; FP32 for the mixed family, double-float on the FP32 pipe for the
-    FP64 family), thread (one thread per point) and native (FP64 family on
-    the FP64 pipe).  Every variant must match the CPU NFFT, for eval and
+    """Gather variants selected by GBNFFT_GATHER: default (column-parallel
+    groups over the padded grid; double-float on the FP32 pipe for the FP64
+    family), tma (mixed-family values from TMA-staged shared-memory tiles),
+    thread (one thread per point) and native (FP64 family on the FP64 pipe).  Every variant must match the CPU NFFT, for eval and
     eval_grad: to rounding in FP64, to FP32 accuracy in the mixed family."""
     from paper_1605_01244_gb300 import Plan
     N = (12, 16, 10)
     c = wl.gaussian_coeffs(N, 1e9, seed=30 + m)
     x = wl.mixed_points(900, 0.03, seed=31)
     ref = None
-    for prec, modes in (("f64", ("col", "thread", "native")), ("f32", ("col", "thread"))):
+    for prec, modes in (("f64", ("default", "thread", "native")), ("f32", ("default", "tma", "thread"))):
         for mode in modes:
-            monkeypatch.setenv("GBNFFT_GATHER", mode)
+            if mode == "default":
+                monkeypatch.delenv("GBNFFT_GATHER", raising=False)
+            else:
+                monkeypatch.setenv("GBNFFT_GATHER", mode)
             plan = Plan(N, len(x), m=m, precision=prec)
             plan.set_points(to_dev(x))
             f = to_np(plan.eval(to_dev(c, CD[prec]))).astype(np.complex128)
@@ -311,3 +314,35 @@ def test_precompute_then_stored_evaluations(prec):
         plan.eval_stored()
     with pytest.raises(ValueError):
         plan.set_num_points(1001)
+
+
+@pytest.mark.parametrize("sigma", [2.0, 1.5])
+def test_pruned_and_full_fft_agree(sigma, monkeypatch):
+    """The default transform skips the planes l1 outside the band (2D FFTs on
+    the in-band planes, then 1D along l1); GBNFFT_FFT=full uses one 3D plan.
+    eval, eval_grad and adjoint must agree with each other and the CPU NFFT."""
+    from paper_1605_01244_gb300 import Plan
+    N = (12, 10, 14)
+    c = wl.gaussian_coeffs(N, 1e9, seed=40)
+    x = wl.mixed_points(700, 0.05, seed=41)
+    fr = wl.rng(42).standard_normal(700) + 0j
+    out = {}
+    for mode in ("pruned", "full"):
+        if mode == "full":
+            monkeypatch.setenv("GBNFFT_FFT", "full")
+        else:
+            monkeypatch.delenv("GBNFFT_FFT", raising=False)
+        plan = Plan(N, len(x), m=5, sigma=sigma, precision="f64")
+        plan.set_points(to_dev(x))
+        f = to_np(plan.eval(to_dev(c)))
+        _, g = plan.eval_grad(to_dev(c))
+        h = to_np(plan.adjoint(to_dev(fr)))
+        out[mode] = (f, to_np(g), h)
+    fc, gc = nfft_cpu.forward_grad(c, x, plan.n, 5)
+    hc = nfft_cpu.adjoint(fr, x, N, plan.n, 5)
+    # 7-smooth, non-power-of-two sizes at sigma = 1.5 round a little more
+    for mode in out:
+        f, g, h = out[mode]
+        assert max_rel(f, fc) <= 3e-13, mode
+        assert max_rel(g, gc) <= 3e-13, mode
+        assert max_rel(h, hc) <= 1e-12, mode
