@@ -551,9 +551,15 @@ int ensure_pgrid(nfft3_plan p, int ng) {
     return NFFT3_OK;
 }
 
-// Layout shift of the padded grid: the tile-staged mode needs the stencil
-// centre as origin (shift m), the column kernels read from the first node.
-int pad_shift(nfft3_plan p) { return p->gather_mode == 0 && p->prec == 32 ? p->m : 0; }
+// Layout shift of the padded grid: the tile-staged kernel (single mixed-family
+// grid, tma mode, tensor map and chunk list ready) needs the stencil centre as
+// origin (shift m); the column kernels read from the first node (shift 0).
+// The choice is recorded so that a stored grid is read the way it was written.
+int pad_shift(nfft3_plan p, int ng) {
+    const bool tile = ng == 1 && p->prec == 32 && p->gather_mode == 0 && p->tmap_ok && p->nchunks > 0;
+    p->pgrid_shift = tile ? p->m : 0;
+    return p->pgrid_shift;
+}
 
 // Gather from the padded grid(s): mixed-family values from TMA-staged tiles
 // (tma mode), otherwise the column-parallel kernels.
@@ -566,9 +572,10 @@ cudaError_t gather_padded(nfft3_plan p, int ng, typename Cplx<R>::T *f, typename
     if (prec == 64)
         return launch_gather_col_df((const float4 *)p->pgrid, pg, p->m, points_view<double>(p), p->wtdf,
                                     (double2 *)f, (double2 *)grad, ng, p->stream);
-    if (ng == 1 && p->gather_mode == 0 && p->tmap_ok && p->nchunks > 0)
+    if (ng == 1 && p->pgrid_shift != 0 && p->tmap_ok && p->nchunks > 0)
         return launch_gather_tma_f32(p->tmap, p->pb.chunks, p->nchunks, p->pb.nt2, p->pb.nt3, g, p->m,
                                      points_view<float>(p), p->wt32, (float2 *)f, p->pb.status, p->stream);
+    if (p->pgrid_shift != 0) return cudaErrorInvalidValue;  // centre layout, no tile list: not reachable
     return launch_gather_col_f32((const float2 *)p->pgrid, pg, p->m, points_view<float>(p), p->wt32,
                                  (float2 *)f, (float2 *)grad, ng, p->stream);
 }
@@ -589,9 +596,9 @@ cudaError_t gather_stage(nfft3_plan p, typename Cplx<R>::T *G, int ng, typename 
         if (st != NFFT3_OK) return cudaErrorMemoryAllocation;
         const Grid3 pg{g.n1 + 2 * p->m, g.n2 + 2 * p->m, g.n3 + 2 * p->m};
         if (prec == 64)
-            e = launch_pad_grid_df((const double2 *)G, g, (float4 *)p->pgrid, pg, ng, pad_shift(p), p->stream);
+            e = launch_pad_grid_df((const double2 *)G, g, (float4 *)p->pgrid, pg, ng, pad_shift(p, ng), p->stream);
         else
-            e = launch_pad_grid_f32((const float2 *)G, g, (float2 *)p->pgrid, pg, ng, pad_shift(p), p->stream);
+            e = launch_pad_grid_f32((const float2 *)G, g, (float2 *)p->pgrid, pg, ng, pad_shift(p, ng), p->stream);
         if (e != cudaSuccess) return e;
         rec_mark(p, rec, 3);
         p->launches += 1;
@@ -720,9 +727,9 @@ template <typename R> int precompute_impl(nfft3_plan p, const R *c, int with_gra
     st = exec_grid_fft(p, G, prec, CUFFT_INVERSE, ng);
     if (st != NFFT3_OK) return st;
     if (prec == 64)
-        e = launch_pad_grid_df((const double2 *)G, g, (float4 *)p->pgrid, pg, ng, pad_shift(p), p->stream);
+        e = launch_pad_grid_df((const double2 *)G, g, (float4 *)p->pgrid, pg, ng, pad_shift(p, ng), p->stream);
     else
-        e = launch_pad_grid_f32((const float2 *)G, g, (float2 *)p->pgrid, pg, ng, pad_shift(p), p->stream);
+        e = launch_pad_grid_f32((const float2 *)G, g, (float2 *)p->pgrid, pg, ng, pad_shift(p, ng), p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     p->launches += 2;
     p->stored_ng = ng;

@@ -30,6 +30,7 @@ struct nfft3_plan_s {
     int grid_count;           // 1 or 4
     void *pgrid;              // ghost-padded copy for the column gathers, (n+2m)^3 x pgrid_count
     int pgrid_count;
+    int pgrid_shift;          // layout shift of its current contents (0 or m)
     int stored_ng;            // grids precomputed by nfft3*_precompute (0: none valid)
     alignas(64) unsigned char tmap[128];  // CUtensorMap of the padded FP32 grid (tile-staged gather)
     int tmap_ok;
