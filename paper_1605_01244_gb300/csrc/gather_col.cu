@@ -207,13 +207,11 @@ __global__ void __launch_bounds__(256, NG == 1 ? GBNFFT_DF_MINB : 2) gather_col_
             mwl[d] = sub < W ? vl : 0.f;
         }
     }
-    float w1h[W], w1l[W], w2h[W], w2l[W];
+    float w2h[W], w2l[W];
 #pragma unroll
-    for (int a = 0; a < W; ++a) {
-        w1h[a] = __shfl_sync(0xffffffffu, mwh[0], gbase + a);
-        w1l[a] = __shfl_sync(0xffffffffu, mwl[0], gbase + a);
-        w2h[a] = __shfl_sync(0xffffffffu, mwh[1], gbase + a);
-        w2l[a] = __shfl_sync(0xffffffffu, mwl[1], gbase + a);
+    for (int b = 0; b < W; ++b) {
+        w2h[b] = __shfl_sync(0xffffffffu, mwh[1], gbase + b);
+        w2l[b] = __shfl_sync(0xffffffffu, mwl[1], gbase + b);
     }
     const int64_t s1 = (int64_t)pg.n2 * pg.n3, gsz = (int64_t)pg.n1 * s1;
     const float4 *base = G + (int64_t)key.x * s1 + (int64_t)key.y * pg.n3 + key.z + tap;
@@ -236,17 +234,14 @@ __global__ void __launch_bounds__(256, NG == 1 ? GBNFFT_DF_MINB : 2) gather_col_
             }
             row += pg.n3;
         }
+        const float w1h = __shfl_sync(0xffffffffu, mwh[0], gbase + a);
+        const float w1l = __shfl_sync(0xffffffffu, mwl[0], gbase + a);
 #pragma unroll
         for (int q = 0; q < NG; ++q) {
             df_norm(S[q][0], S[q][1]);
             df_norm(S[q][2], S[q][3]);
-            df_mac(T[q][0], T[q][1], S[q][0], S[q][1], w1h[0], w1l[0]);
-            df_mac(T[q][2], T[q][3], S[q][2], S[q][3], w1h[0], w1l[0]);
-        }
-#pragma unroll
-        for (int k = 0; k < W - 1; ++k) {
-            w1h[k] = w1h[k + 1];
-            w1l[k] = w1l[k + 1];
+            df_mac(T[q][0], T[q][1], S[q][0], S[q][1], w1h, w1l);
+            df_mac(T[q][2], T[q][3], S[q][2], S[q][3], w1h, w1l);
         }
         base += s1;
     }

@@ -35,9 +35,12 @@ __device__ __forceinline__ Reduced reduce_coord(double x, int n, int m, int *sta
     Reduced r;
     r.s = __dsub_rn(l0, v);
     if (r.s >= 1.0) r.s = 0.0;  // cannot happen for finite v; keeps s in [0, 1) regardless
-    long long li = (long long)l0 % n;
-    if (li < 0) li += n;
-    r.l0 = (int)li;
+    // xw lies in [-1/2, 1/2], so u in [0, n] and l0 in [-m, n - m]: one
+    // add wraps it unless n < m (small grids loop a few times)
+    int li = __double2int_rn(l0);
+    while (li < 0) li += n;
+    while (li >= n) li -= n;
+    r.l0 = li;
     return r;
 }
 
