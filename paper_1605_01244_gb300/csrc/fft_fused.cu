@@ -1,0 +1,492 @@
+// Forward-path grid transform, fused: deconvolution, the unnormalised inverse
+// DFT of the oversampled grid and the ghost-padded layout the column gathers
+// read, for power-of-two grid sizes (16 <= n_d <= 2048).
+//
+//   g_l = sum_{k in I_N} c_k D1[k1] D2[k2] D3[k3] exp(+2 pi i k.l / n)
+//
+// computed as three passes of 1D DFTs over the nonzero band only:
+//   rows   (along l3): one line per in-band (k1, k2), input c deconvolved;
+//   cols2  (along l2): one line per (k1, l3);
+//   out    (along l1): one line per (l2, l3), written to every padded
+//                      position p = l + shift + t n in [0, n + 2m) (t = -1, 0, 1).
+// Each line is transformed in shared memory by radix-8 (then 4 or 2) Stockham
+// passes.  The FP64 family computes in double-float on the FP32 pipe (the
+// grid values enter as FP64 products and are split into float pairs), and
+// the mixed family in FP32; the padded output is what the gathers expect
+// (float4 re_hi, re_lo, im_hi, im_lo, or float2).
+// With ng = 4 the same passes also produce the gradient grids 2 pi i k_d g.
+#include "internal.cuh"
+
+namespace gbnfft {
+namespace {
+
+constexpr int kLineThreads = 512;   // threads per block
+constexpr int kLineElems = 4096;    // line elements per block (lines x length)
+
+// ---- double-float arithmetic (FP64-accurate on the FP32 pipe) ---------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ void dd_add(float ah, float al, float bh, float bl, float &h, float &l) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    fast_two_sum(s, e, h, l);
+}
+__device__ __forceinline__ void dd_mul(float ah, float al, float bh, float bl, float &h, float &l) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    fast_two_sum(p, e, h, l);
+}
+
+struct ArithDF {
+    struct C {
+        float rh, rl, ih, il;
+    };
+    using S = float4;
+    static constexpr int kPadShift = 3;   // 16-byte elements: one pad per 8
+    static __device__ __forceinline__ C ld(const S &s) { return C{s.x, s.y, s.z, s.w}; }
+    static __device__ __forceinline__ S st(const C &c) { return make_float4(c.rh, c.rl, c.ih, c.il); }
+    static __device__ __forceinline__ C zero() { return C{0.f, 0.f, 0.f, 0.f}; }
+    static __device__ __forceinline__ C add(const C &a, const C &b) {
+        C o;
+        dd_add(a.rh, a.rl, b.rh, b.rl, o.rh, o.rl);
+        dd_add(a.ih, a.il, b.ih, b.il, o.ih, o.il);
+        return o;
+    }
+    static __device__ __forceinline__ C sub(const C &a, const C &b) {
+        C o;
+        dd_add(a.rh, a.rl, -b.rh, -b.rl, o.rh, o.rl);
+        dd_add(a.ih, a.il, -b.ih, -b.il, o.ih, o.il);
+        return o;
+    }
+    // a * w (w a table twiddle)
+    static __device__ __forceinline__ C mul(const C &a, const S &w) {
+        float t1h, t1l, t2h, t2l, t3h, t3l, t4h, t4l;
+        dd_mul(a.rh, a.rl, w.x, w.y, t1h, t1l);   // ar wr
+        dd_mul(a.ih, a.il, w.z, w.w, t2h, t2l);   // ai wi
+        dd_mul(a.rh, a.rl, w.z, w.w, t3h, t3l);   // ar wi
+        dd_mul(a.ih, a.il, w.x, w.y, t4h, t4l);   // ai wr
+        C o;
+        dd_add(t1h, t1l, -t2h, -t2l, o.rh, o.rl);
+        dd_add(t3h, t3l, t4h, t4l, o.ih, o.il);
+        return o;
+    }
+    static __device__ __forceinline__ C mul_i(const C &a) { return C{-a.ih, -a.il, a.rh, a.rl}; }
+    // a * (1 + i) / sqrt 2 and a * (-1 + i) / sqrt 2
+    static __device__ __forceinline__ C mul_w8(const C &a) {
+        float dh, dl, sh, sl;
+        dd_add(a.rh, a.rl, -a.ih, -a.il, dh, dl);
+        dd_add(a.rh, a.rl, a.ih, a.il, sh, sl);
+        C o;
+        dd_mul(dh, dl, kR2h, kR2l, o.rh, o.rl);
+        dd_mul(sh, sl, kR2h, kR2l, o.ih, o.il);
+        return o;
+    }
+    static __device__ __forceinline__ C mul_w83(const C &a) {
+        float dh, dl, sh, sl;
+        dd_add(a.rh, a.rl, -a.ih, -a.il, dh, dl);
+        dd_add(a.rh, a.rl, a.ih, a.il, sh, sl);
+        C o;
+        dd_mul(-sh, -sl, kR2h, kR2l, o.rh, o.rl);
+        dd_mul(dh, dl, kR2h, kR2l, o.ih, o.il);
+        return o;
+    }
+    static constexpr double kR2 = 0.70710678118654752440;
+    static constexpr float kR2h = (float)kR2;
+    static constexpr float kR2l = (float)(kR2 - (double)(float)kR2);
+};
+
+struct ArithF32 {
+    struct C {
+        float r, i;
+    };
+    using S = float2;
+    static constexpr int kPadShift = 4;   // 8-byte elements: one pad per 16
+    static __device__ __forceinline__ C ld(const S &s) { return C{s.x, s.y}; }
+    static __device__ __forceinline__ S st(const C &c) { return make_float2(c.r, c.i); }
+    static __device__ __forceinline__ C zero() { return C{0.f, 0.f}; }
+    static __device__ __forceinline__ C add(const C &a, const C &b) { return C{a.r + b.r, a.i + b.i}; }
+    static __device__ __forceinline__ C sub(const C &a, const C &b) { return C{a.r - b.r, a.i - b.i}; }
+    static __device__ __forceinline__ C mul(const C &a, const S &w) {
+        return C{fmaf(a.r, w.x, -a.i * w.y), fmaf(a.r, w.y, a.i * w.x)};
+    }
+    static __device__ __forceinline__ C mul_i(const C &a) { return C{-a.i, a.r}; }
+    static __device__ __forceinline__ C mul_w8(const C &a) {
+        constexpr float r2 = 0.70710678118654752440f;
+        return C{(a.r - a.i) * r2, (a.r + a.i) * r2};
+    }
+    static __device__ __forceinline__ C mul_w83(const C &a) {
+        constexpr float r2 = 0.70710678118654752440f;
+        return C{-(a.r + a.i) * r2, (a.r - a.i) * r2};
+    }
+};
+
+// ---- radix-R DFTs with the inverse sign: X_k = sum_a x_a exp(+2 pi i a k / R) --
+template <class A> __device__ __forceinline__ void dft2(typename A::C &x0, typename A::C &x1) {
+    const typename A::C s = A::add(x0, x1), d = A::sub(x0, x1);
+    x0 = s;
+    x1 = d;
+}
+template <class A>
+__device__ __forceinline__ void dft4(typename A::C &y0, typename A::C &y1, typename A::C &y2,
+                                     typename A::C &y3) {
+    const typename A::C s0 = A::add(y0, y2), s1 = A::sub(y0, y2), s2 = A::add(y1, y3),
+                        s3 = A::mul_i(A::sub(y1, y3));
+    y0 = A::add(s0, s2);
+    y1 = A::add(s1, s3);
+    y2 = A::sub(s0, s2);
+    y3 = A::sub(s1, s3);
+}
+// X_{2k} = DFT4(x_a + x_{a+4}), X_{2k+1} = DFT4((x_a - x_{a+4}) w8^a)
+template <class A> __device__ __forceinline__ void dft8(typename A::C (&x)[8]) {
+    using C = typename A::C;
+    C u[4], v[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        u[a] = A::add(x[a], x[a + 4]);
+        v[a] = A::sub(x[a], x[a + 4]);
+    }
+    v[1] = A::mul_w8(v[1]);
+    v[2] = A::mul_i(v[2]);
+    v[3] = A::mul_w83(v[3]);
+    dft4<A>(u[0], u[1], u[2], u[3]);
+    dft4<A>(v[0], v[1], v[2], v[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        x[2 * k] = u[k];
+        x[2 * k + 1] = v[k];
+    }
+}
+
+template <class A> __device__ __forceinline__ int pidx(int i) { return i + (i >> A::kPadShift); }
+
+// One Stockham pass of radix R = 2^LOGR over a line x of length L = 2^logL
+// (element i at pidx(i)), by the line's T = L/8 threads, each taking 8/R
+// butterflies: butterfly j reads x[j + r L/R], applies w_{Ns R}^{r (j mod Ns)}
+// (w_n = exp(2 pi i / n), table tw[i] = w_L^i), and writes
+// x'[(j / Ns) Ns R + j mod Ns + r Ns].  In place: all reads, a barrier, all writes.
+template <class A, int LOGR>
+__device__ __forceinline__ void stockham_pass(typename A::S *x, const typename A::S *tw, int logL, int logNs,
+                                              int u, int T) {
+    using C = typename A::C;
+    constexpr int R = 1 << LOGR, PER = 8 / R;
+    const int nb = 1 << (logL - LOGR);
+    const int Ns = 1 << logNs;
+    C v[8];
+#pragma unroll
+    for (int b = 0; b < PER; ++b) {
+        const int j = u + b * T;
+        const int k = j & (Ns - 1);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            C t = A::ld(x[pidx<A>(j + r * nb)]);
+            if (r > 0 && k > 0) t = A::mul(t, tw[(r * k) << (logL - logNs - LOGR)]);
+            v[b * R + r] = t;
+        }
+    }
+    if constexpr (R == 8) {
+        dft8<A>(v);
+    } else if constexpr (R == 4) {
+        dft4<A>(v[0], v[1], v[2], v[3]);
+        dft4<A>(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) dft2<A>(v[2 * b], v[2 * b + 1]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < PER; ++b) {
+        const int j = u + b * T;
+        const int d = ((j >> logNs) << (logNs + LOGR)) + (j & (Ns - 1));
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[pidx<A>(d + r * Ns)] = A::st(v[b * R + r]);
+    }
+    __syncthreads();
+}
+
+// In-place DFT of the block's lines in shared memory: line `line` of length
+// L = 2^logL starts at sm + line * LS, T = L/8 threads per line, radix-8
+// passes then one radix-4 or radix-2 pass for the remaining factor.
+template <class A>
+__device__ void line_dft(typename A::S *sm, const typename A::S *__restrict__ tw, int logL, int LS) {
+    const int T = 1 << (logL - 3);
+    const int line = threadIdx.x / T, u = threadIdx.x - line * T;
+    typename A::S *x = sm + (int64_t)line * LS;
+    int logNs = 0;
+    for (; logL - logNs >= 3; logNs += 3) stockham_pass<A, 3>(x, tw, logL, logNs, u, T);
+    if (logL - logNs == 2) stockham_pass<A, 2>(x, tw, logL, logNs, u, T);
+    else if (logL - logNs == 1) stockham_pass<A, 1>(x, tw, logL, logNs, u, T);
+}
+
+template <class A> __device__ __forceinline__ void load_twiddles(typename A::S *dst, const typename A::S *src, int L) {
+    for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = src[i];
+}
+
+// deconvolved input value of grid q (0: c_k D; d = 1..3: 2 pi i k_d c_k D)
+__device__ __forceinline__ ArithDF::C series_value(ArithDF, double2 c, double d, int q, int kq) {
+    double re = c.x * d, im = c.y * d;
+    if (q > 0) {
+        const double f = 6.283185307179586476925286766559 * (double)kq;
+        const double t = re;
+        re = -f * im;
+        im = f * t;
+    }
+    ArithDF::C o;
+    split_df(re, o.rh, o.rl);
+    split_df(im, o.ih, o.il);
+    return o;
+}
+__device__ __forceinline__ ArithF32::C series_value(ArithF32, float2 c, float d, int q, int kq) {
+    float re = c.x * d, im = c.y * d;
+    if (q > 0) {
+        const float f = 6.283185307179586476925286766559f * (float)kq;
+        const float t = re;
+        re = -f * im;
+        im = f * t;
+    }
+    return ArithF32::C{re, im};
+}
+
+__device__ __forceinline__ int band_pos(int i, int N, int n) {   // k = i - N/2 -> l = k mod n
+    const int k = i - N / 2;
+    return k < 0 ? k + n : k;
+}
+
+struct FusedArgs {
+    int N1, N2, N3, n1, n2, n3;
+    int logn1, logn2, logn3;
+    int m, shift, ng;
+};
+
+// Pass 1: rows along l3 for the in-band (k1, k2); input c deconvolved.
+// A[q][i1 N2 + i2][l3].
+template <class A, typename R>
+__global__ void __launch_bounds__(kLineThreads) fused_rows_kernel(
+    const typename Cplx<R>::T *__restrict__ c, const R *__restrict__ D1, const R *__restrict__ D2,
+    const R *__restrict__ D3, const typename A::S *__restrict__ tw3, typename A::S *__restrict__ out,
+    FusedArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using S = typename A::S;
+    const int L = a.n3, LPB = kLineElems / L;
+    const int LS = L + (L >> A::kPadShift) + 1;
+    S *sm = reinterpret_cast<S *>(smem_raw);
+    S *tws = sm + (int64_t)LPB * LS;
+    const int q = blockIdx.y;
+    const int64_t nrows = (int64_t)a.N1 * a.N2;
+    const int64_t row0 = (int64_t)blockIdx.x * LPB;
+    load_twiddles<A>(tws, tw3, L);
+    // zero the lines, then place the N3 deconvolved coefficients of each row
+    for (int i = threadIdx.x; i < LPB * LS; i += blockDim.x) sm[i] = A::st(A::zero());
+    __syncthreads();
+    for (int e = threadIdx.x; e < LPB * a.N3; e += blockDim.x) {
+        const int line = e / a.N3, i3 = e - line * a.N3;
+        const int64_t row = row0 + line;
+        if (row >= nrows) continue;
+        const int i1 = (int)(row / a.N2), i2 = (int)(row - (int64_t)i1 * a.N2);
+        // frequency k_q of the gradient grid q (unused for q = 0)
+        const int kq = q == 1 ? i1 - a.N1 / 2 : q == 2 ? i2 - a.N2 / 2 : i3 - a.N3 / 2;
+        const R d = D1[i1] * D2[i2] * D3[i3];
+        sm[(int64_t)line * LS + pidx<A>(band_pos(i3, a.N3, a.n3))] =
+            A::st(series_value(A{}, c[row * a.N3 + i3], d, q, kq));
+    }
+    __syncthreads();
+    line_dft<A>(sm, tws, a.logn3, LS);
+    S *o = out + (int64_t)q * nrows * L;
+    for (int e = threadIdx.x; e < LPB * L; e += blockDim.x) {
+        const int line = e / L, l3 = e - line * L;
+        const int64_t row = row0 + line;
+        if (row < nrows) o[row * L + l3] = sm[(int64_t)line * LS + pidx<A>(l3)];
+    }
+}
+
+// Pass 2: lines along l2 for each (k1, l3).  in A[q][i1 N2 + i2][l3],
+// out B[q][i1][l2][l3].  A block takes LPB consecutive l3 of one i1.
+template <class A>
+__global__ void __launch_bounds__(kLineThreads) fused_cols_kernel(const typename A::S *__restrict__ in,
+                                                                  const typename A::S *__restrict__ tw2,
+                                                                  typename A::S *__restrict__ out,
+                                                                  FusedArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using S = typename A::S;
+    const int L = a.n2, LPB = kLineElems / L;
+    const int LS = L + (L >> A::kPadShift) + 1;
+    S *sm = reinterpret_cast<S *>(smem_raw);
+    S *tws = sm + (int64_t)LPB * LS;
+    const int q = blockIdx.y;
+    const int nblk3 = (a.n3 + LPB - 1) / LPB;
+    const int i1 = blockIdx.x / nblk3;
+    const int l30 = (blockIdx.x - i1 * nblk3) * LPB;
+    const int nl = a.n3 - l30 < LPB ? a.n3 - l30 : LPB;
+    load_twiddles<A>(tws, tw2, L);
+    for (int i = threadIdx.x; i < LPB * LS; i += blockDim.x) sm[i] = A::st(A::zero());
+    __syncthreads();
+    const S *src = in + ((int64_t)q * a.N1 + i1) * a.N2 * a.n3;
+    for (int e = threadIdx.x; e < LPB * a.N2; e += blockDim.x) {
+        const int i2 = e / LPB, line = e - i2 * LPB;
+        if (line < nl)
+            sm[(int64_t)line * LS + pidx<A>(band_pos(i2, a.N2, a.n2))] = src[(int64_t)i2 * a.n3 + l30 + line];
+    }
+    __syncthreads();
+    line_dft<A>(sm, tws, a.logn2, LS);
+    S *dst = out + ((int64_t)q * a.N1 + i1) * a.n2 * a.n3;
+    for (int e = threadIdx.x; e < LPB * L; e += blockDim.x) {
+        const int l2 = e / LPB, line = e - l2 * LPB;
+        if (line < nl) dst[(int64_t)l2 * a.n3 + l30 + line] = sm[(int64_t)line * LS + pidx<A>(l2)];
+    }
+}
+
+// Pass 3: lines along l1 for each (l2, l3); in B[q][i1][l2][l3]; out the
+// padded grid P[q][p1][p2][p3], p = l + shift + t n in [0, n + 2m).
+template <class A>
+__global__ void __launch_bounds__(kLineThreads) fused_out_kernel(const typename A::S *__restrict__ in,
+                                                                 const typename A::S *__restrict__ tw1,
+                                                                 typename A::S *__restrict__ P,
+                                                                 FusedArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using S = typename A::S;
+    const int L = a.n1, LPB = kLineElems / L;
+    const int LS = L + (L >> A::kPadShift) + 1;
+    S *sm = reinterpret_cast<S *>(smem_raw);
+    S *tws = sm + (int64_t)LPB * LS;
+    const int q = blockIdx.y;
+    const int nblk3 = (a.n3 + LPB - 1) / LPB;
+    const int l2 = blockIdx.x / nblk3;
+    const int l30 = (blockIdx.x - l2 * nblk3) * LPB;
+    const int nl = a.n3 - l30 < LPB ? a.n3 - l30 : LPB;
+    load_twiddles<A>(tws, tw1, L);
+    for (int i = threadIdx.x; i < LPB * LS; i += blockDim.x) sm[i] = A::st(A::zero());
+    __syncthreads();
+    const S *src = in + (int64_t)q * a.N1 * a.n2 * a.n3 + (int64_t)l2 * a.n3 + l30;
+    for (int e = threadIdx.x; e < LPB * a.N1; e += blockDim.x) {
+        const int i1 = e / LPB, line = e - i1 * LPB;
+        if (line < nl)
+            sm[(int64_t)line * LS + pidx<A>(band_pos(i1, a.N1, a.n1))] =
+                src[(int64_t)i1 * a.n2 * a.n3 + line];
+    }
+    __syncthreads();
+    line_dft<A>(sm, tws, a.logn1, LS);
+    const int m2 = 2 * a.m;
+    const int pn1 = a.n1 + m2, pn2 = a.n2 + m2, pn3 = a.n3 + m2;
+    S *dstq = P + (int64_t)q * pn1 * pn2 * pn3;
+    for (int e = threadIdx.x; e < LPB * L; e += blockDim.x) {
+        const int l1 = e / LPB, line = e - l1 * LPB;
+        if (line >= nl) continue;
+        const S v = sm[(int64_t)line * LS + pidx<A>(l1)];
+        const int l3 = l30 + line;
+#pragma unroll
+        for (int t1 = -1; t1 <= 1; ++t1) {
+            const int p1 = l1 + a.shift + t1 * a.n1;
+            if (p1 < 0 || p1 >= pn1) continue;
+#pragma unroll
+            for (int t2 = -1; t2 <= 1; ++t2) {
+                const int p2 = l2 + a.shift + t2 * a.n2;
+                if (p2 < 0 || p2 >= pn2) continue;
+                S *rowp = dstq + ((int64_t)p1 * pn2 + p2) * pn3;
+#pragma unroll
+                for (int t3 = -1; t3 <= 1; ++t3) {
+                    const int p3 = l3 + a.shift + t3 * a.n3;
+                    if (p3 >= 0 && p3 < pn3) rowp[p3] = v;
+                }
+            }
+        }
+    }
+}
+
+int ilog2(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+template <class A>
+size_t line_smem(int L) {
+    const int LPB = kLineElems / L;
+    const int LS = L + (L >> A::kPadShift) + 1;
+    return sizeof(typename A::S) * ((size_t)LPB * LS + L);
+}
+
+template <class A, typename R>
+cudaError_t run_fused(const typename Cplx<R>::T *c, const R *D1, const R *D2, const R *D3,
+                      const void *const tw[3], void *scratch, void *P, const FusedArgs &a,
+                      cudaStream_t st) {
+    using S = typename A::S;
+    S *Abuf = (S *)scratch;
+    S *Bbuf = Abuf + (int64_t)a.ng * a.N1 * a.N2 * a.n3;
+    const size_t sm1 = line_smem<A>(a.n3), sm2 = line_smem<A>(a.n2), sm3 = line_smem<A>(a.n1);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(fused_rows_kernel<A, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm1)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(fused_cols_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm2)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(fused_out_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm3)) != cudaSuccess)
+        return e;
+    const int64_t rows = (int64_t)a.N1 * a.N2;
+    const int lpb3 = kLineElems / a.n3, lpb2 = kLineElems / a.n2, lpb1 = kLineElems / a.n1;
+    dim3 g1((unsigned)((rows + lpb3 - 1) / lpb3), (unsigned)a.ng);
+    fused_rows_kernel<A, R><<<g1, kLineThreads, sm1, st>>>(c, D1, D2, D3, (const S *)tw[2], Abuf, a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 g2((unsigned)(a.N1 * ((a.n3 + lpb2 - 1) / lpb2)), (unsigned)a.ng);
+    fused_cols_kernel<A><<<g2, kLineThreads, sm2, st>>>(Abuf, (const S *)tw[1], Bbuf, a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 g3((unsigned)(a.n2 * ((a.n3 + lpb1 - 1) / lpb1)), (unsigned)a.ng);
+    fused_out_kernel<A><<<g3, kLineThreads, sm3, st>>>(Bbuf, (const S *)tw[0], (S *)P, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fused_supported(const int n[3]) {
+    for (int d = 0; d < 3; ++d)
+        if (n[d] < 16 || n[d] > 2048 || (n[d] & (n[d] - 1))) return false;
+    return true;
+}
+
+size_t fused_scratch_bytes(const int N[3], const int n[3], int ng, int prec) {
+    const size_t elem = prec == 64 ? 16 : 8;
+    return elem * (size_t)ng * ((size_t)N[0] * N[1] * n[2] + (size_t)N[0] * n[1] * n[2]);
+}
+
+template <typename R>
+cudaError_t launch_fused_series(const typename Cplx<R>::T *c, const int N[3], const int n[3], const R *D1,
+                                const R *D2, const R *D3, const void *const tw[3], void *scratch,
+                                void *P, int m, int shift, int ng, cudaStream_t st) {
+    FusedArgs a;
+    a.N1 = N[0];
+    a.N2 = N[1];
+    a.N3 = N[2];
+    a.n1 = n[0];
+    a.n2 = n[1];
+    a.n3 = n[2];
+    a.logn1 = ilog2(n[0]);
+    a.logn2 = ilog2(n[1]);
+    a.logn3 = ilog2(n[2]);
+    a.m = m;
+    a.shift = shift;
+    a.ng = ng;
+    if constexpr (sizeof(R) == 8)
+        return run_fused<ArithDF, R>(c, D1, D2, D3, tw, scratch, P, a, st);
+    else
+        return run_fused<ArithF32, R>(c, D1, D2, D3, tw, scratch, P, a, st);
+}
+
+template cudaError_t launch_fused_series<double>(const double2 *, const int[3], const int[3],
+                                                 const double *, const double *, const double *,
+                                                 const void *const[3], void *, void *, int, int, int,
+                                                 cudaStream_t);
+template cudaError_t launch_fused_series<float>(const float2 *, const int[3], const int[3], const float *,
+                                                const float *, const float *, const void *const[3],
+                                                void *, void *, int, int, int, cudaStream_t);
+
+}  // namespace gbnfft

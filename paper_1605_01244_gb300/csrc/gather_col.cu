@@ -279,27 +279,6 @@ __global__ void __launch_bounds__(256, NG == 1 ? GBNFFT_DF_MINB : 2) gather_col_
 // Padded copies P[p1, p2, p3] = g[p1 mod n1, p2 mod n2, p3 mod n3] of ng grids:
 // one block per padded row (q, p1, p2), threads along p3.
 
-// Split an FP64 value into floats hi + lo without FP64 arithmetic: hi keeps
-// the leading 24 significant bits (exact truncation), lo is the remaining 29
-// bits rounded to a float, so hi + lo carries ~48 bits.  Values below 2^-100
-// in magnitude (never reached by the normalised grids) are flushed to zero.
-__device__ __forceinline__ void split_df(double v, float &hi, float &lo) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const unsigned int sign = (unsigned int)(b >> 63) << 31;
-    const int e = (int)((b >> 52) & 0x7ff);
-    if (e < 1023 - 100) {
-        hi = __int_as_float(sign);
-        lo = hi;
-        return;
-    }
-    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-    hi = __int_as_float((int)(sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)(mant >> 29)));
-    const int low = (int)(mant & 0x1FFFFFFFull);
-    // low * 2^(e - 1023 - 52), with the sign of v
-    const float lf = ldexpf(__int2float_rn(low), e - 1075);
-    lo = sign ? -lf : lf;
-}
-
 // source index of padded index p: (p - shift) mod n, for p in [0, n + 2m)
 __device__ __forceinline__ int pad_src(int p, int m, int n) {
     int s = p - m;

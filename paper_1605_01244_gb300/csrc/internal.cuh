@@ -89,6 +89,38 @@ template <int MM> PolyDF<MM> make_poly_df(const WinTableDF &t) {
     return p;
 }
 
+// Split an FP64 value into floats hi + lo without FP64 arithmetic: hi keeps
+// the leading 24 significant bits (exact truncation), lo is the remaining 29
+// bits rounded to a float, so hi + lo carries ~48 bits.  Values below 2^-100
+// in magnitude (never reached by the normalised grids) are flushed to zero.
+__device__ __forceinline__ void split_df(double v, float &hi, float &lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned int sign = (unsigned int)(b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 1023 - 100) {
+        hi = __int_as_float(sign);
+        lo = hi;
+        return;
+    }
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    hi = __int_as_float((int)(sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)(mant >> 29)));
+    const int low = (int)(mant & 0x1FFFFFFFull);
+    // low * 2^(e - 1023 - 52), with the sign of v
+    const float lf = ldexpf(__int2float_rn(low), e - 1075);
+    lo = sign ? -lf : lf;
+}
+
+// ---- fused forward transform (fft_fused.cu) -----------------------------------
+// Deconvolve + inverse DFT of the oversampled grid + ghost-padded output
+// P[q][p] = g_q[(p - shift) mod n] for ng grids (q > 0: 2 pi i k_q c_k D), in
+// double-float (R = double) or FP32.  tw[d]: table of exp(2 pi i j / n_d).
+bool fused_supported(const int n[3]);
+size_t fused_scratch_bytes(const int N[3], const int n[3], int ng, int prec);
+template <typename R>
+cudaError_t launch_fused_series(const typename Cplx<R>::T *c, const int N[3], const int n[3], const R *D1,
+                                const R *D2, const R *D3, const void *const tw[3], void *scratch,
+                                void *P, int m, int shift, int ng, cudaStream_t st);
+
 // ---- launchers implemented in gather_df.cu ---------------------------------
 cudaError_t launch_grid_to_df(double2 *G, int64_t total, cudaStream_t st);
 cudaError_t launch_gather_df(const float4 *G, Grid3 g, int m, PointsView<double> pts,

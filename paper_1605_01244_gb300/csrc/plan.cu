@@ -43,6 +43,45 @@ void dev_free(void *&ptr) {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? NFFT3_OK : NFFT3_ERR_CUDA; }
 
+// Twiddle table exp(+2 pi i j / n_d), j in [0, n_d), from long double cos/sin:
+// double-float (cos_hi, cos_lo, sin_hi, sin_lo) for the FP64 family, float2
+// for the mixed family.
+int make_twiddles(nfft3_plan p, int d) {
+    const int L = p->n[d];
+    const size_t elem = p->prec == 64 ? 4 * sizeof(float) : 2 * sizeof(float);
+    float *h = (float *)std::malloc(elem * L);
+    if (!h) return NFFT3_ERR_ALLOC;
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int j = 0; j < L; ++j) {
+        const long double a = two_pi * (long double)j / (long double)L;
+        const long double cr = cosl(a), si = sinl(a);
+        if (p->prec == 64) {
+            const float ch = (float)cr, sh = (float)si;
+            h[4 * j + 0] = ch;
+            h[4 * j + 1] = (float)(cr - (long double)ch);
+            h[4 * j + 2] = sh;
+            h[4 * j + 3] = (float)(si - (long double)sh);
+        } else {
+            h[2 * j + 0] = (float)cr;
+            h[2 * j + 1] = (float)si;
+        }
+    }
+    int st = dev_alloc(p, &p->tw[d], elem * L);
+    if (st == NFFT3_OK) st = cuda_status(cudaMemcpy(p->tw[d], h, elem * L, cudaMemcpyHostToDevice));
+    std::free(h);
+    return st;
+}
+
+// Line-pass buffers of the fused transform for ng grids.
+int ensure_fscratch(nfft3_plan p, int ng) {
+    if (p->fscratch && p->fscratch_ng >= ng) return NFFT3_OK;
+    dev_free(p->fscratch);
+    p->fscratch_ng = 0;
+    const int st = dev_alloc(p, &p->fscratch, fused_scratch_bytes(p->N, p->n, ng, p->prec));
+    if (st == NFFT3_OK) p->fscratch_ng = ng;
+    return st;
+}
+
 // ---- stage timing ----------------------------------------------------------
 // A record holds up to kTimingMarks events of one call; stage i of the call
 // spans marks i..i+1.  Records are folded into stage_ms when the pool fills
@@ -275,6 +314,8 @@ void release(nfft3_plan p) {
     }
     dev_free(p->grid);
     dev_free(p->pgrid);
+    for (int d = 0; d < 3; ++d) dev_free(p->tw[d]);
+    dev_free(p->fscratch);
     void *k = p->key;
     dev_free(k);
     void *v;
@@ -406,7 +447,9 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
     if (st == NFFT3_OK) {
         const char *f = std::getenv("GBNFFT_FFT");
         p->fft_pruned = !(f && !std::strcmp(f, "full"));
+        p->fused = !f && fused_supported(p->n) && (p->gather_mode == 0 || p->gather_mode == 3);
     }
+    for (int d = 0; d < 3 && st == NFFT3_OK && p->fused; ++d) st = make_twiddles(p, d);
     if (st == NFFT3_OK && p->fft_pruned) {
         const cufftType ty = prec == 64 ? CUFFT_Z2Z : CUFFT_C2C;
         int n2d[2] = {p->n[1], p->n[2]};
@@ -623,6 +666,35 @@ cudaError_t gather_stage(nfft3_plan p, typename Cplx<R>::T *G, int ng, typename 
     return launch_gather_grad<R>(G, g, p->m, points_view<R>(p), win_table<R>(p), f, grad, p->stream);
 }
 
+// Fused forward transform of c into the padded grid(s) (ng = 1 or 4): the
+// deconvolution, the three DFT line passes and the padded layout in three
+// launches; the column / tile-staged gathers read the result directly.
+template <typename R> int fused_transform(nfft3_plan p, const R *c, int ng) {
+    int st = ensure_pgrid(p, ng);
+    if (st == NFFT3_OK) st = ensure_fscratch(p, ng);
+    if (st != NFFT3_OK) return st;
+    const void *tw[3] = {p->tw[0], p->tw[1], p->tw[2]};
+    const cudaError_t e = launch_fused_series<R>(
+        (const typename Cplx<R>::T *)c, p->N, p->n, (const R *)p->D[0], (const R *)p->D[1],
+        (const R *)p->D[2], tw, p->fscratch, p->pgrid, p->m, pad_shift(p, ng), ng, p->stream);
+    p->launches += 3;
+    return cuda_status(e);
+}
+
+// Fused evaluation of ng grids: the transform is timed as the fft stage
+// (deconv and split stages are empty), then the gather.
+template <typename R> int fused_eval(nfft3_plan p, const R *c, R *f, R *grad, int ng, int rec) {
+    using C = typename Cplx<R>::T;
+    rec_mark(p, rec, 1);
+    const int st = fused_transform<R>(p, c, ng);
+    if (st != NFFT3_OK) return st;
+    rec_mark(p, rec, 2);
+    rec_mark(p, rec, 3);
+    const cudaError_t e = gather_padded<R>(p, ng, (C *)f, (C *)grad);
+    rec_mark(p, rec, 4);
+    return finish(p, cuda_status(e));
+}
+
 template <typename R> int eval_impl(nfft3_plan p, const R *c, R *f) {
     using C = typename Cplx<R>::T;
     constexpr int prec = sizeof(R) == 8 ? 64 : 32;
@@ -634,6 +706,7 @@ template <typename R> int eval_impl(nfft3_plan p, const R *c, R *f) {
     C *G = (C *)p->grid;
     p->stored_ng = 0;
     const int rec = rec_begin(p, kRecEval);
+    if (p->fused) return fused_eval<R>(p, c, f, nullptr, 1, rec);
     cudaError_t e = launch_deconv_scatter<R>((const C *)c, p->N[0], p->N[1], p->N[2],
                                              (const R *)p->D[0], (const R *)p->D[1],
                                              (const R *)p->D[2], G, g, 0, p->stream);
@@ -685,6 +758,10 @@ template <typename R> int eval_grad_impl(nfft3_plan p, const R *c, R *f, R *grad
     if (!p->points_ok) return NFFT3_ERR_NO_POINTS;
     if (p->M > 0 && (!c || !grad)) return NFFT3_ERR_ARG;
     if (p->M == 0) return NFFT3_OK;
+    if (p->fused) {
+        p->stored_ng = 0;
+        return fused_eval<R>(p, c, f, grad, 4, rec_begin(p, kRecGrad));
+    }
     int st = ensure_grad_grids<R>(p);
     if (st != NFFT3_OK) return st;
     const Grid3 g{p->n[0], p->n[1], p->n[2]};
@@ -713,6 +790,13 @@ template <typename R> int precompute_impl(nfft3_plan p, const R *c, int with_gra
     constexpr int prec = sizeof(R) == 8 ? 64 : 32;
     if (!p || p->prec != prec || !c || (p->gather_mode != 0 && p->gather_mode != 3)) return NFFT3_ERR_ARG;
     const int ng = with_grad ? 4 : 1;
+    if (p->fused) {
+        p->stored_ng = 0;
+        const int st = fused_transform<R>(p, c, ng);
+        if (st != NFFT3_OK) return st;
+        p->stored_ng = ng;
+        return finish(p, NFFT3_OK);
+    }
     int st = ng == 4 ? ensure_grad_grids<R>(p) : NFFT3_OK;
     if (st == NFFT3_OK) st = ensure_pgrid(p, ng);
     if (st != NFFT3_OK) return st;

@@ -41,6 +41,13 @@ struct nfft3_plan_s {
     // pruned transform (default; GBNFFT_FFT=full uses fft1/fft4): batched 2D
     // FFTs over the planes l1 with |k1| < N1/2, then 1D FFTs along l1
     int fft_pruned;
+    // fused forward transform (power-of-two n; default for the padded-grid
+    // gathers; GBNFFT_FFT=cufft or full selects cuFFT): twiddle tables
+    // w_{n_d}^i (double-float float4 or float2) and the two line-pass buffers
+    int fused;
+    void *tw[3];
+    void *fscratch;
+    int fscratch_ng;
     cufftHandle fft2d;        // n2 x n3, batch N1/2 planes
     cufftHandle fft1d;        // length n1, stride n2 n3, batch n2 n3
     // points

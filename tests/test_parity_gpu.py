@@ -279,6 +279,47 @@ def test_gather_variants_agree(m, monkeypatch):
                 assert rel_l2(g, gc) <= 5e-6, mode
 
 
+@pytest.mark.parametrize("N", [(16, 32, 8), (8, 1024, 8), (64, 64, 64)])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_fused_transform_matches_cufft_and_cpu(N, prec, monkeypatch):
+    """Power-of-two grids take the fused transform (deconvolution, radix-8
+    Stockham line passes in shared memory -- double-float for the FP64 family --
+    and the padded output) by default; GBNFFT_FFT=cufft takes cuFFT plus the
+    separate deconvolution and padding kernels.  Both must match the CPU NFFT
+    for eval, eval_grad and stored evaluations, and in the FP32 family also
+    with the tile-staged gather (centre-shifted padded layout).  n covers line
+    lengths 16 .. 2048 (radix-8 passes followed by a radix-2 or -4 pass)."""
+    from paper_1605_01244_gb300 import Plan
+    c = wl.gaussian_coeffs(N, 1e9, seed=70)
+    x = wl.mixed_points(1500, 0.05, seed=71)
+    m = 6 if prec == "f64" else 3
+    fc, gc = nfft_cpu.forward_grad(c, x, tuple(2 * v for v in N), m)
+    tol_f, tol_g = (2e-13, 3e-13) if prec == "f64" else (2e-6, 5e-6)
+    err = max_rel if prec == "f64" else rel_l2
+    modes = [("fused", None), ("cufft", "cufft")] + ([("fused-tma", "tma")] if prec == "f32" else [])
+    for name, env in modes:
+        monkeypatch.delenv("GBNFFT_FFT", raising=False)
+        monkeypatch.delenv("GBNFFT_GATHER", raising=False)
+        if name == "cufft":
+            monkeypatch.setenv("GBNFFT_FFT", "cufft")
+        if name == "fused-tma":
+            monkeypatch.setenv("GBNFFT_GATHER", "tma")
+        plan = Plan(N, len(x), m=m, sigma=2.0, precision=prec)
+        assert plan.n == tuple(2 * v for v in N)
+        plan.set_points(to_dev(x))
+        cd = to_dev(c, CD[prec])
+        f = to_np(plan.eval(cd)).astype(np.complex128)
+        fg, g = plan.eval_grad(cd)
+        assert err(f, fc) <= tol_f, name
+        assert err(to_np(fg).astype(np.complex128), fc) <= tol_f, name
+        assert err(to_np(g).astype(np.complex128), gc) <= tol_g, name
+        plan.precompute(cd, with_grad=True)
+        fs, gs = plan.eval_grad_stored()
+        assert err(to_np(gs).astype(np.complex128), gc) <= tol_g, name
+        plan.precompute(cd)
+        assert err(to_np(plan.eval_stored()).astype(np.complex128), fc) <= tol_f, name
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_precompute_then_stored_evaluations(prec):
     """One transform of c, then value and gradient at several point sets
