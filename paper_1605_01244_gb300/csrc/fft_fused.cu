@@ -169,27 +169,36 @@ template <class A> __device__ __forceinline__ void dft8(typename A::C (&x)[8]) {
 
 template <class A> __device__ __forceinline__ int pidx(int i) { return i + (i >> A::kPadShift); }
 
-// One Stockham pass of radix R = 2^LOGR over a line x of length L = 2^logL
+// One Stockham pass of radix R = 2^LOGR over a line x of length L = 2^LOGL
 // (element i at pidx(i)), by the line's T = L/8 threads, each taking 8/R
 // butterflies: butterfly j reads x[j + r L/R], applies w_{Ns R}^{r (j mod Ns)}
 // (w_n = exp(2 pi i / n), table tw[i] = w_L^i), and writes
-// x'[(j / Ns) Ns R + j mod Ns + r Ns].  In place: all reads, a barrier, all writes.
-template <class A, int LOGR>
-__device__ __forceinline__ void stockham_pass(typename A::S *x, const typename A::S *tw, int logL, int logNs,
-                                              int u, int T) {
+// x'[(j / Ns) Ns R + j mod Ns + r Ns], Ns = 2^LOGNS.  In place: all reads, a
+// barrier, all writes.  Sizes are compile-time, so strides and pads fold.
+template <class A, int LOGL, int LOGNS, int LOGR>
+__device__ __forceinline__ void stockham_pass(typename A::S *x, const typename A::S *tw, int u) {
     using C = typename A::C;
     constexpr int R = 1 << LOGR, PER = 8 / R;
-    const int nb = 1 << (logL - LOGR);
-    const int Ns = 1 << logNs;
+    constexpr int T = 1 << (LOGL - 3);
+    constexpr int NB = 1 << (LOGL - LOGR);
+    constexpr int NS = 1 << LOGNS;
+    constexpr int TWS = LOGL - LOGNS - LOGR;   // twiddle index shift
+    constexpr int PS = A::kPadShift;
     C v[8];
 #pragma unroll
     for (int b = 0; b < PER; ++b) {
         const int j = u + b * T;
-        const int k = j & (Ns - 1);
+        const int k = j & (NS - 1);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            C t = A::ld(x[pidx<A>(j + r * nb)]);
-            if (r > 0 && k > 0) t = A::mul(t, tw[(r * k) << (logL - logNs - LOGR)]);
+            int idx;
+            if constexpr ((NB & ((1 << PS) - 1)) == 0)
+                idx = pidx<A>(j) + r * (NB + (NB >> PS));
+            else
+                idx = pidx<A>(j + r * NB);
+            C t = A::ld(x[idx]);
+            if constexpr (LOGNS > 0)
+                if (r > 0) t = A::mul(t, tw[(r * k) << TWS]);
             v[b * R + r] = t;
         }
     }
@@ -206,25 +215,40 @@ __device__ __forceinline__ void stockham_pass(typename A::S *x, const typename A
 #pragma unroll
     for (int b = 0; b < PER; ++b) {
         const int j = u + b * T;
-        const int d = ((j >> logNs) << (logNs + LOGR)) + (j & (Ns - 1));
+        const int d = ((j >> LOGNS) << (LOGNS + LOGR)) + (j & (NS - 1));
 #pragma unroll
-        for (int r = 0; r < R; ++r) x[pidx<A>(d + r * Ns)] = A::st(v[b * R + r]);
+        for (int r = 0; r < R; ++r) {
+            int idx;
+            if constexpr ((NS & ((1 << PS) - 1)) == 0)
+                idx = pidx<A>(d) + r * (NS + (NS >> PS));
+            else
+                idx = pidx<A>(d + r * NS);
+            x[idx] = A::st(v[b * R + r]);
+        }
     }
     __syncthreads();
 }
 
+template <class A, int LOGL, int LOGNS>
+__device__ __forceinline__ void stockham_from(typename A::S *x, const typename A::S *tw, int u) {
+    if constexpr (LOGL - LOGNS >= 3) {
+        stockham_pass<A, LOGL, LOGNS, 3>(x, tw, u);
+        stockham_from<A, LOGL, LOGNS + 3>(x, tw, u);
+    } else if constexpr (LOGL - LOGNS == 2) {
+        stockham_pass<A, LOGL, LOGNS, 2>(x, tw, u);
+    } else if constexpr (LOGL - LOGNS == 1) {
+        stockham_pass<A, LOGL, LOGNS, 1>(x, tw, u);
+    }
+}
+
 // In-place DFT of the block's lines in shared memory: line `line` of length
-// L = 2^logL starts at sm + line * LS, T = L/8 threads per line, radix-8
+// L = 2^LOGL starts at sm + line * LS, T = L/8 threads per line, radix-8
 // passes then one radix-4 or radix-2 pass for the remaining factor.
-template <class A>
-__device__ void line_dft(typename A::S *sm, const typename A::S *__restrict__ tw, int logL, int LS) {
-    const int T = 1 << (logL - 3);
+template <class A, int LOGL>
+__device__ __forceinline__ void line_dft(typename A::S *sm, const typename A::S *__restrict__ tw, int LS) {
+    constexpr int T = 1 << (LOGL - 3);
     const int line = threadIdx.x / T, u = threadIdx.x - line * T;
-    typename A::S *x = sm + (int64_t)line * LS;
-    int logNs = 0;
-    for (; logL - logNs >= 3; logNs += 3) stockham_pass<A, 3>(x, tw, logL, logNs, u, T);
-    if (logL - logNs == 2) stockham_pass<A, 2>(x, tw, logL, logNs, u, T);
-    else if (logL - logNs == 1) stockham_pass<A, 1>(x, tw, logL, logNs, u, T);
+    stockham_from<A, LOGL, 0>(sm + line * LS, tw, u);
 }
 
 template <class A> __device__ __forceinline__ void load_twiddles(typename A::S *dst, const typename A::S *src, int L) {
@@ -269,17 +293,17 @@ struct FusedArgs {
 
 // Pass 1: rows along l3 for the in-band (k1, k2); input c deconvolved.
 // A[q][i1 N2 + i2][l3].
-template <class A, typename R>
+template <class A, typename R, int LOGL>
 __global__ void __launch_bounds__(kLineThreads) fused_rows_kernel(
     const typename Cplx<R>::T *__restrict__ c, const R *__restrict__ D1, const R *__restrict__ D2,
     const R *__restrict__ D3, const typename A::S *__restrict__ tw3, typename A::S *__restrict__ out,
     FusedArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using S = typename A::S;
-    const int L = a.n3, LPB = kLineElems / L;
-    const int LS = L + (L >> A::kPadShift) + 1;
+    constexpr int L = 1 << LOGL, LPB = kLineElems / L;
+    constexpr int LS = L + (L >> A::kPadShift) + 1;
     S *sm = reinterpret_cast<S *>(smem_raw);
-    S *tws = sm + (int64_t)LPB * LS;
+    S *tws = sm + LPB * LS;
     const int q = blockIdx.y;
     const int64_t nrows = (int64_t)a.N1 * a.N2;
     const int64_t row0 = (int64_t)blockIdx.x * LPB;
@@ -295,32 +319,32 @@ __global__ void __launch_bounds__(kLineThreads) fused_rows_kernel(
         // frequency k_q of the gradient grid q (unused for q = 0)
         const int kq = q == 1 ? i1 - a.N1 / 2 : q == 2 ? i2 - a.N2 / 2 : i3 - a.N3 / 2;
         const R d = D1[i1] * D2[i2] * D3[i3];
-        sm[(int64_t)line * LS + pidx<A>(band_pos(i3, a.N3, a.n3))] =
+        sm[line * LS + pidx<A>(band_pos(i3, a.N3, a.n3))] =
             A::st(series_value(A{}, c[row * a.N3 + i3], d, q, kq));
     }
     __syncthreads();
-    line_dft<A>(sm, tws, a.logn3, LS);
+    line_dft<A, LOGL>(sm, tws, LS);
     S *o = out + (int64_t)q * nrows * L;
     for (int e = threadIdx.x; e < LPB * L; e += blockDim.x) {
         const int line = e / L, l3 = e - line * L;
         const int64_t row = row0 + line;
-        if (row < nrows) o[row * L + l3] = sm[(int64_t)line * LS + pidx<A>(l3)];
+        if (row < nrows) o[row * L + l3] = sm[line * LS + pidx<A>(l3)];
     }
 }
 
 // Pass 2: lines along l2 for each (k1, l3).  in A[q][i1 N2 + i2][l3],
 // out B[q][i1][l2][l3].  A block takes LPB consecutive l3 of one i1.
-template <class A>
+template <class A, int LOGL>
 __global__ void __launch_bounds__(kLineThreads) fused_cols_kernel(const typename A::S *__restrict__ in,
                                                                   const typename A::S *__restrict__ tw2,
                                                                   typename A::S *__restrict__ out,
                                                                   FusedArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using S = typename A::S;
-    const int L = a.n2, LPB = kLineElems / L;
-    const int LS = L + (L >> A::kPadShift) + 1;
+    constexpr int L = 1 << LOGL, LPB = kLineElems / L;
+    constexpr int LS = L + (L >> A::kPadShift) + 1;
     S *sm = reinterpret_cast<S *>(smem_raw);
-    S *tws = sm + (int64_t)LPB * LS;
+    S *tws = sm + LPB * LS;
     const int q = blockIdx.y;
     const int nblk3 = (a.n3 + LPB - 1) / LPB;
     const int i1 = blockIdx.x / nblk3;
@@ -333,30 +357,30 @@ __global__ void __launch_bounds__(kLineThreads) fused_cols_kernel(const typename
     for (int e = threadIdx.x; e < LPB * a.N2; e += blockDim.x) {
         const int i2 = e / LPB, line = e - i2 * LPB;
         if (line < nl)
-            sm[(int64_t)line * LS + pidx<A>(band_pos(i2, a.N2, a.n2))] = src[(int64_t)i2 * a.n3 + l30 + line];
+            sm[line * LS + pidx<A>(band_pos(i2, a.N2, a.n2))] = src[(int64_t)i2 * a.n3 + l30 + line];
     }
     __syncthreads();
-    line_dft<A>(sm, tws, a.logn2, LS);
+    line_dft<A, LOGL>(sm, tws, LS);
     S *dst = out + ((int64_t)q * a.N1 + i1) * a.n2 * a.n3;
     for (int e = threadIdx.x; e < LPB * L; e += blockDim.x) {
         const int l2 = e / LPB, line = e - l2 * LPB;
-        if (line < nl) dst[(int64_t)l2 * a.n3 + l30 + line] = sm[(int64_t)line * LS + pidx<A>(l2)];
+        if (line < nl) dst[(int64_t)l2 * a.n3 + l30 + line] = sm[line * LS + pidx<A>(l2)];
     }
 }
 
 // Pass 3: lines along l1 for each (l2, l3); in B[q][i1][l2][l3]; out the
 // padded grid P[q][p1][p2][p3], p = l + shift + t n in [0, n + 2m).
-template <class A>
+template <class A, int LOGL>
 __global__ void __launch_bounds__(kLineThreads) fused_out_kernel(const typename A::S *__restrict__ in,
                                                                  const typename A::S *__restrict__ tw1,
                                                                  typename A::S *__restrict__ P,
                                                                  FusedArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using S = typename A::S;
-    const int L = a.n1, LPB = kLineElems / L;
-    const int LS = L + (L >> A::kPadShift) + 1;
+    constexpr int L = 1 << LOGL, LPB = kLineElems / L;
+    constexpr int LS = L + (L >> A::kPadShift) + 1;
     S *sm = reinterpret_cast<S *>(smem_raw);
-    S *tws = sm + (int64_t)LPB * LS;
+    S *tws = sm + LPB * LS;
     const int q = blockIdx.y;
     const int nblk3 = (a.n3 + LPB - 1) / LPB;
     const int l2 = blockIdx.x / nblk3;
@@ -369,18 +393,18 @@ __global__ void __launch_bounds__(kLineThreads) fused_out_kernel(const typename 
     for (int e = threadIdx.x; e < LPB * a.N1; e += blockDim.x) {
         const int i1 = e / LPB, line = e - i1 * LPB;
         if (line < nl)
-            sm[(int64_t)line * LS + pidx<A>(band_pos(i1, a.N1, a.n1))] =
+            sm[line * LS + pidx<A>(band_pos(i1, a.N1, a.n1))] =
                 src[(int64_t)i1 * a.n2 * a.n3 + line];
     }
     __syncthreads();
-    line_dft<A>(sm, tws, a.logn1, LS);
+    line_dft<A, LOGL>(sm, tws, LS);
     const int m2 = 2 * a.m;
     const int pn1 = a.n1 + m2, pn2 = a.n2 + m2, pn3 = a.n3 + m2;
     S *dstq = P + (int64_t)q * pn1 * pn2 * pn3;
     for (int e = threadIdx.x; e < LPB * L; e += blockDim.x) {
         const int l1 = e / LPB, line = e - l1 * LPB;
         if (line >= nl) continue;
-        const S v = sm[(int64_t)line * LS + pidx<A>(l1)];
+        const S v = sm[line * LS + pidx<A>(l1)];
         const int l3 = l30 + line;
 #pragma unroll
         for (int t1 = -1; t1 <= 1; ++t1) {
@@ -414,6 +438,81 @@ size_t line_smem(int L) {
     return sizeof(typename A::S) * ((size_t)LPB * LS + L);
 }
 
+template <class A, typename R, int LOGL>
+cudaError_t launch_rows(const typename Cplx<R>::T *c, const R *D1, const R *D2, const R *D3,
+                        const typename A::S *tw, typename A::S *out, const FusedArgs &a, cudaStream_t st) {
+    const size_t sm = line_smem<A>(1 << LOGL);
+    cudaError_t e = cudaFuncSetAttribute(fused_rows_kernel<A, R, LOGL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int64_t rows = (int64_t)a.N1 * a.N2, lpb = kLineElems >> LOGL;
+    dim3 g((unsigned)((rows + lpb - 1) / lpb), (unsigned)a.ng);
+    fused_rows_kernel<A, R, LOGL><<<g, kLineThreads, sm, st>>>(c, D1, D2, D3, tw, out, a);
+    return cudaGetLastError();
+}
+
+template <class A, int LOGL>
+cudaError_t launch_cols(const typename A::S *in, const typename A::S *tw, typename A::S *out,
+                        const FusedArgs &a, cudaStream_t st) {
+    const size_t sm = line_smem<A>(1 << LOGL);
+    cudaError_t e =
+        cudaFuncSetAttribute(fused_cols_kernel<A, LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int lpb = kLineElems >> LOGL;
+    dim3 g((unsigned)(a.N1 * ((a.n3 + lpb - 1) / lpb)), (unsigned)a.ng);
+    fused_cols_kernel<A, LOGL><<<g, kLineThreads, sm, st>>>(in, tw, out, a);
+    return cudaGetLastError();
+}
+
+template <class A, int LOGL>
+cudaError_t launch_out(const typename A::S *in, const typename A::S *tw, typename A::S *P,
+                       const FusedArgs &a, cudaStream_t st) {
+    const size_t sm = line_smem<A>(1 << LOGL);
+    cudaError_t e =
+        cudaFuncSetAttribute(fused_out_kernel<A, LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int lpb = kLineElems >> LOGL;
+    dim3 g((unsigned)(a.n2 * ((a.n3 + lpb - 1) / lpb)), (unsigned)a.ng);
+    fused_out_kernel<A, LOGL><<<g, kLineThreads, sm, st>>>(in, tw, P, a);
+    return cudaGetLastError();
+}
+
+// Line lengths 2^4 .. 2^11.
+#define GBNFFT_LOGL_SWITCH(logl, CALL)          \
+    switch (logl) {                            \
+        case 4: return CALL(4);                \
+        case 5: return CALL(5);                \
+        case 6: return CALL(6);                \
+        case 7: return CALL(7);                \
+        case 8: return CALL(8);                \
+        case 9: return CALL(9);                \
+        case 10: return CALL(10);              \
+        case 11: return CALL(11);              \
+        default: return cudaErrorInvalidValue; \
+    }
+
+template <class A, typename R>
+cudaError_t run_rows(const typename Cplx<R>::T *c, const R *D1, const R *D2, const R *D3,
+                     const typename A::S *tw, typename A::S *out, const FusedArgs &a, cudaStream_t st) {
+#define GBNFFT_CALL(L) launch_rows<A, R, L>(c, D1, D2, D3, tw, out, a, st)
+    GBNFFT_LOGL_SWITCH(a.logn3, GBNFFT_CALL)
+#undef GBNFFT_CALL
+}
+template <class A>
+cudaError_t run_cols(const typename A::S *in, const typename A::S *tw, typename A::S *out, const FusedArgs &a,
+                     cudaStream_t st) {
+#define GBNFFT_CALL(L) launch_cols<A, L>(in, tw, out, a, st)
+    GBNFFT_LOGL_SWITCH(a.logn2, GBNFFT_CALL)
+#undef GBNFFT_CALL
+}
+template <class A>
+cudaError_t run_out(const typename A::S *in, const typename A::S *tw, typename A::S *P, const FusedArgs &a,
+                    cudaStream_t st) {
+#define GBNFFT_CALL(L) launch_out<A, L>(in, tw, P, a, st)
+    GBNFFT_LOGL_SWITCH(a.logn1, GBNFFT_CALL)
+#undef GBNFFT_CALL
+}
+
 template <class A, typename R>
 cudaError_t run_fused(const typename Cplx<R>::T *c, const R *D1, const R *D2, const R *D3,
                       const void *const tw[3], void *scratch, void *P, const FusedArgs &a,
@@ -421,28 +520,10 @@ cudaError_t run_fused(const typename Cplx<R>::T *c, const R *D1, const R *D2, co
     using S = typename A::S;
     S *Abuf = (S *)scratch;
     S *Bbuf = Abuf + (int64_t)a.ng * a.N1 * a.N2 * a.n3;
-    const size_t sm1 = line_smem<A>(a.n3), sm2 = line_smem<A>(a.n2), sm3 = line_smem<A>(a.n1);
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(fused_rows_kernel<A, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sm1)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(fused_cols_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sm2)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(fused_out_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sm3)) != cudaSuccess)
-        return e;
-    const int64_t rows = (int64_t)a.N1 * a.N2;
-    const int lpb3 = kLineElems / a.n3, lpb2 = kLineElems / a.n2, lpb1 = kLineElems / a.n1;
-    dim3 g1((unsigned)((rows + lpb3 - 1) / lpb3), (unsigned)a.ng);
-    fused_rows_kernel<A, R><<<g1, kLineThreads, sm1, st>>>(c, D1, D2, D3, (const S *)tw[2], Abuf, a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    dim3 g2((unsigned)(a.N1 * ((a.n3 + lpb2 - 1) / lpb2)), (unsigned)a.ng);
-    fused_cols_kernel<A><<<g2, kLineThreads, sm2, st>>>(Abuf, (const S *)tw[1], Bbuf, a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    dim3 g3((unsigned)(a.n2 * ((a.n3 + lpb1 - 1) / lpb1)), (unsigned)a.ng);
-    fused_out_kernel<A><<<g3, kLineThreads, sm3, st>>>(Bbuf, (const S *)tw[0], (S *)P, a);
-    return cudaGetLastError();
+    cudaError_t e = run_rows<A, R>(c, D1, D2, D3, (const S *)tw[2], Abuf, a, st);
+    if (e == cudaSuccess) e = run_cols<A>(Abuf, (const S *)tw[1], Bbuf, a, st);
+    if (e == cudaSuccess) e = run_out<A>(Bbuf, (const S *)tw[0], (S *)P, a, st);
+    return e;
 }
 
 }  // namespace

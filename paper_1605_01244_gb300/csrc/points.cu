@@ -16,25 +16,30 @@ struct Reduced {
     double s;
 };
 
-__device__ __forceinline__ Reduced reduce_coord(double x, int n, int m, int *status) {
-    if (!isfinite(x)) {
+// nd = (double)n and alpha = m + 1/2 are passed in (hoisted by the caller);
+// the finiteness and range tests work on the bits, so the FP64 pipe (the
+// bound of this kernel on GB300) only does the arithmetic of the reduction.
+__device__ __forceinline__ Reduced reduce_coord(double x, int n, double nd, double alpha, int *status) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    if ((bits & 0x7FF0000000000000ull) == 0x7FF0000000000000ull) {
         atomicOr(status, 1);
         x = 0.0;
+        bits = 0;
     }
     // explicit round-to-nearest steps: no contraction into FMAs, so that the
     // stencil choice at exact half-integer u is reproducible.  Coordinates
-    // already in [-1/2, 1/2) (|x| < 1/2, or x = -1/2; tested on the bits,
-    // without FP64 arithmetic) skip the wrap, whose result they equal.
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    // already in [-1/2, 1/2) (|x| < 1/2, or x = -1/2) skip the wrap, whose
+    // result they equal.
     const unsigned long long mag = bits & 0x7FFFFFFFFFFFFFFFull;
     const bool in_range = mag < 0x3FE0000000000000ull || bits == 0xBFE0000000000000ull;
     const double xw = in_range ? x : __dsub_rn(x, floor(__dadd_rn(x, 0.5)));
-    const double u = __dmul_rn((double)n, __dadd_rn(xw, 0.5));
-    const double v = __dsub_rn(u, (double)m + 0.5);
+    const double u = __dmul_rn(nd, __dadd_rn(xw, 0.5));
+    const double v = __dsub_rn(u, alpha);
     const double l0 = ceil(v);
     Reduced r;
     r.s = __dsub_rn(l0, v);
-    if (r.s >= 1.0) r.s = 0.0;  // cannot happen for finite v; keeps s in [0, 1) regardless
+    // s >= 1 cannot happen for finite v; the bit test keeps s in [0, 1) regardless
+    if (__double_as_longlong(r.s) >= 0x3FF0000000000000ll) r.s = 0.0;
     // xw lies in [-1/2, 1/2], so u in [0, n] and l0 in [-m, n - m]: one
     // add wraps it unless n < m (small grids loop a few times)
     int li = __double2int_rn(l0);
@@ -57,11 +62,13 @@ __device__ __forceinline__ int tile_coord(int l0, int m, int n) {
 template <typename R>
 __global__ void points_count_kernel(const double *__restrict__ x, PointsBuild pb,
                                     int4 *__restrict__ key_tmp, R *__restrict__ s_tmp) {
+    const double alpha = (double)pb.m + 0.5;
+    const double nd1 = (double)pb.g.n1, nd2 = (double)pb.g.n2, nd3 = (double)pb.g.n3;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < pb.M;
          j += (int64_t)gridDim.x * blockDim.x) {
-        const Reduced r1 = reduce_coord(x[3 * j + 0], pb.g.n1, pb.m, pb.status);
-        const Reduced r2 = reduce_coord(x[3 * j + 1], pb.g.n2, pb.m, pb.status);
-        const Reduced r3 = reduce_coord(x[3 * j + 2], pb.g.n3, pb.m, pb.status);
+        const Reduced r1 = reduce_coord(x[3 * j + 0], pb.g.n1, nd1, alpha, pb.status);
+        const Reduced r2 = reduce_coord(x[3 * j + 1], pb.g.n2, nd2, alpha, pb.status);
+        const Reduced r3 = reduce_coord(x[3 * j + 2], pb.g.n3, nd3, alpha, pb.status);
         const int t1 = tile_coord(r1.l0, pb.m, pb.g.n1);
         const int t2 = tile_coord(r2.l0, pb.m, pb.g.n2);
         const int t3 = tile_coord(r3.l0, pb.m, pb.g.n3);
