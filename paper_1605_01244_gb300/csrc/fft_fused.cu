@@ -280,6 +280,19 @@ __device__ __forceinline__ ArithF32::C series_value(ArithF32, float2 c, float d,
     return ArithF32::C{re, im};
 }
 
+// padded ghost copy of primary position p (or -1), for 2m <= n
+__device__ __forceinline__ int ghost_of(int p, int n, int m2) { return p < m2 ? p + n : (p >= n ? p - n : -1); }
+
+// exact unsigned division by a runtime divisor d >= 1 for 32-bit dividends:
+// q = (umulhi(M, x) + x) >> s with s = ceil(log2 d), M = floor(2^32 (2^s - d) / d) + 1
+struct FastDiv {
+    unsigned M;
+    int s;
+    __device__ __forceinline__ unsigned div(unsigned x) const {
+        return (unsigned)(((unsigned long long)__umulhi(M, x) + x) >> s);
+    }
+};
+
 __device__ __forceinline__ int band_pos(int i, int N, int n) {   // k = i - N/2 -> l = k mod n
     const int k = i - N / 2;
     return k < 0 ? k + n : k;
@@ -289,7 +302,16 @@ struct FusedArgs {
     int N1, N2, N3, n1, n2, n3;
     int logn1, logn2, logn3;
     int m, shift, ng;
+    FastDiv divN2, divN3;
 };
+
+FastDiv make_fastdiv(unsigned d) {
+    FastDiv f;
+    f.s = 0;
+    while ((1ull << f.s) < d) ++f.s;
+    f.M = (unsigned)((((1ull << f.s) - d) << 32) / d + 1);
+    return f;
+}
 
 // Pass 1: rows along l3 for the in-band (k1, k2); input c deconvolved.
 // A[q][i1 N2 + i2][l3].
@@ -312,10 +334,10 @@ __global__ void __launch_bounds__(kLineThreads) fused_rows_kernel(
     for (int i = threadIdx.x; i < LPB * LS; i += blockDim.x) sm[i] = A::st(A::zero());
     __syncthreads();
     for (int e = threadIdx.x; e < LPB * a.N3; e += blockDim.x) {
-        const int line = e / a.N3, i3 = e - line * a.N3;
+        const int line = (int)a.divN3.div((unsigned)e), i3 = e - line * a.N3;
         const int64_t row = row0 + line;
         if (row >= nrows) continue;
-        const int i1 = (int)(row / a.N2), i2 = (int)(row - (int64_t)i1 * a.N2);
+        const int i1 = (int)a.divN2.div((unsigned)row), i2 = (int)(row - (int64_t)i1 * a.N2);
         // frequency k_q of the gradient grid q (unused for q = 0)
         const int kq = q == 1 ? i1 - a.N1 / 2 : q == 2 ? i2 - a.N2 / 2 : i3 - a.N3 / 2;
         const R d = D1[i1] * D2[i2] * D3[i3];
@@ -399,27 +421,34 @@ __global__ void __launch_bounds__(kLineThreads) fused_out_kernel(const typename 
     __syncthreads();
     line_dft<A, LOGL>(sm, tws, LS);
     const int m2 = 2 * a.m;
-    const int pn1 = a.n1 + m2, pn2 = a.n2 + m2, pn3 = a.n3 + m2;
-    S *dstq = P + (int64_t)q * pn1 * pn2 * pn3;
+    const int pn2 = a.n2 + m2, pn3 = a.n3 + m2;
+    const int64_t plane = (int64_t)pn2 * pn3;
+    S *dstq = P + (int64_t)q * (a.n1 + m2) * plane;
+    // every l has its primary position p = l + shift in [0, n + 2m) and at most
+    // one ghost copy (2m <= n): p + n if p < 2m, p - n if p >= n
+    const int p2 = l2 + a.shift, g2 = ghost_of(p2, a.n2, m2);
     for (int e = threadIdx.x; e < LPB * L; e += blockDim.x) {
         const int l1 = e / LPB, line = e - l1 * LPB;
         if (line >= nl) continue;
         const S v = sm[line * LS + pidx<A>(l1)];
-        const int l3 = l30 + line;
-#pragma unroll
-        for (int t1 = -1; t1 <= 1; ++t1) {
-            const int p1 = l1 + a.shift + t1 * a.n1;
-            if (p1 < 0 || p1 >= pn1) continue;
-#pragma unroll
-            for (int t2 = -1; t2 <= 1; ++t2) {
-                const int p2 = l2 + a.shift + t2 * a.n2;
-                if (p2 < 0 || p2 >= pn2) continue;
-                S *rowp = dstq + ((int64_t)p1 * pn2 + p2) * pn3;
-#pragma unroll
-                for (int t3 = -1; t3 <= 1; ++t3) {
-                    const int p3 = l3 + a.shift + t3 * a.n3;
-                    if (p3 >= 0 && p3 < pn3) rowp[p3] = v;
-                }
+        const int p1 = l1 + a.shift, g1 = ghost_of(p1, a.n1, m2);
+        const int p3 = l30 + line + a.shift, g3 = ghost_of(p3, a.n3, m2);
+        S *r = dstq + (int64_t)p1 * plane + (int64_t)p2 * pn3;
+        r[p3] = v;
+        if (g3 >= 0) r[g3] = v;
+        if (g2 >= 0) {
+            S *rg = dstq + (int64_t)p1 * plane + (int64_t)g2 * pn3;
+            rg[p3] = v;
+            if (g3 >= 0) rg[g3] = v;
+        }
+        if (g1 >= 0) {
+            S *r1 = dstq + (int64_t)g1 * plane + (int64_t)p2 * pn3;
+            r1[p3] = v;
+            if (g3 >= 0) r1[g3] = v;
+            if (g2 >= 0) {
+                S *rg = dstq + (int64_t)g1 * plane + (int64_t)g2 * pn3;
+                rg[p3] = v;
+                if (g3 >= 0) rg[g3] = v;
             }
         }
     }
@@ -556,6 +585,8 @@ cudaError_t launch_fused_series(const typename Cplx<R>::T *c, const int N[3], co
     a.m = m;
     a.shift = shift;
     a.ng = ng;
+    a.divN2 = make_fastdiv((unsigned)N[1]);
+    a.divN3 = make_fastdiv((unsigned)N[2]);
     if constexpr (sizeof(R) == 8)
         return run_fused<ArithDF, R>(c, D1, D2, D3, tw, scratch, P, a, st);
     else
