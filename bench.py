@@ -141,6 +141,12 @@ def gather_bytes(M: int, n: int, real_bytes: int) -> int:
     return n ** 3 * cplx + M * (3 * 4 + 3 * real_bytes + cplx)
 
 
+# DRAM bytes (read + write) of one gather launch at the default workload,
+# from ncu's dram__bytes_read.sum + dram__bytes_write.sum on the same kernels
+# at N = 128^3, M = 1.25e6 (both units 1/8 of the default), scaled by 8;
+# profiles/gather_col_128cubed_1.25e6pts_full.md has the capture.
+GATHER_TRAFFIC_BYTES = {"gather_col_df_kernel": 3.2739e9, "gather_col_f32_kernel": 1.5241e9}
+
 # FP32 instructions of one FP64-accurate (double-float) multiply-add: exact
 # product (1 mul + 3 fma), two-sum of the high parts (6 add/sub), 2 adds into
 # the low part.
@@ -252,11 +258,13 @@ def run_ours(args, rank, world, local):
         t_alu = flops / (apk[alu_key] * 1e12)
         t_hbm = byts / (peaks["hbm_gbs"] * 1e9)
         kname = "gather_col_df_kernel" if fam == "f64" else "gather_col_f32_kernel"
+        default_size = N == N_EDGE and M == M_POINTS
+        traffic = GATHER_TRAFFIC_BYTES[kname] if default_size else None
         if t_alu >= t_hbm:
             pk = apk[alu_key]
             ach = flops / (g_ms * 1e-3) / 1e12
             roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                    "traffic": None, "kernel": kname, "flops_per_launch": flops,
+                    "traffic": traffic, "kernel": kname, "flops_per_launch": flops,
                     "peak_source": "derived (unit counts x clock)"}
             if fam == "f64":
                 roof["note"] = ("FP64-equivalent flops; the window sums run in double-float on the FP32 "
@@ -266,8 +274,13 @@ def run_ours(args, rank, world, local):
             pk = peaks["hbm_gbs"]
             ach = byts / (g_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
-                    "traffic": None, "kernel": kname, "bytes_per_launch": byts,
+                    "traffic": traffic, "kernel": kname, "bytes_per_launch": byts,
                     "peak_source": peak_src}
+            w = 2 * m + 1
+            l1_floor_ms = w * w * M / (152 * 2.070e9) * 1e3
+            roof["note"] = ("the kernel is bound by L1 data-pipe wavefronts (about one per stencil row of "
+                            "%d values): floor %d x %d rows x M / (152 SMs x 2.07 GHz) = %.2f ms, achieved "
+                            "%.0f %% of it" % (w, w, w, l1_floor_ms, 100 * l1_floor_ms / g_ms))
         results[fam] = {
             "m": m, "ms_per_step": ms, "ms_eval_only": ms_eval, "e2e_ms": e2e_ms,
             "stages_ms": stages, "launches_per_step": launches.value / args.steps,

@@ -228,7 +228,7 @@ int nfft3_timing_read(nfft3_plan p, double *ms, int64_t *calls, int64_t *launche
  * J J^T (det <= 1e-30 (|Re grad|^2 + |Im grad|^2)^2), 3 step longer than
  * max_step (torus units).  resid[j] receives |psi| at the evaluated x.
  * The paper finds cores by thresholding rho = |psi|^2 on refined point sets
- * (Sec. 4, sftubeeval3); this step refines candidates onto the zero set.
+ * (Sec. 4.3, sftubeeval3); this step refines candidates onto the zero set.
  */
 int nfft3_newton_step(int prec, int64_t M, double *x, const void *f, const void *grad,
                       int *status, double *resid, double tol, double max_step, void *stream);
@@ -252,7 +252,7 @@ int nfft3_dedupe(int64_t M, const double *x, const int *status, double radius, i
  * and out_dir = +-(normal direction 1..3) signed by the winding; *count
  * (device unsigned long long, zeroed by the call) receives the total number
  * found, which may exceed cap (then only cap are written).  The paper marks
- * low-density lattice nodes instead (Sec. 4: rho = |psi|^2 <= 0.0012).
+ * low-density lattice nodes instead (Sec. 5: rho = |psi|^2 <= 0.0012).
  */
 int nfft3_lattice_points(double *x, int R1, int R2, int R3, const double *lo, const double *h,
                          void *stream);

@@ -1,4 +1,4 @@
-"""Learned vortex-core proposals (SURVEY row a10).
+"""Learned vortex-core proposals.
 
 A small fully convolutional 3D network reads psi on the coarse native
 lattice of a local box -- channels (Re psi, Im psi, |psi|^2), scaled by the
@@ -15,7 +15,7 @@ the mean position of the refined core points in the cell.  At inference the
 proposed cells (sigmoid(logit) > tau) are refined at fine resolution only
 inside themselves (``refine_cells``): the plaquette test on their fine
 sub-lattices, aligned with the judge's lattice, followed by Newton.  This
-mirrors the paper's idea of refining only inside vortex tubes (Sec. 3.3,
+mirrors the paper's idea of refining only inside vortex tubes (Sec. 4.3,
 sftubeeval3), with the tube chosen by the network instead of by rho <= rhobar.
 """
 from __future__ import annotations

@@ -5,7 +5,7 @@
 // +-2 pi around it.  On a fine lattice, a core crosses the face (plaquette)
 // of four neighbouring nodes when the phase differences around the face,
 // each wrapped into (-pi, pi], sum to +-2 pi.  The paper instead marks
-// lattice nodes with rho = |psi|^2 below a level (Sec. 4: isosurfaces at
+// lattice nodes with rho = |psi|^2 below a level (Sec. 5: isosurfaces at
 // rho = 0.0012 on 321^3 and 281^3 grids); the winding test gives a
 // point per crossing that Newton refinement can start from.
 #include <cmath>

@@ -4,7 +4,7 @@
 // psi: R^3 -> C gives two real equations F = (Re psi, Im psi) in three
 // unknowns; with J = [Re grad psi; Im grad psi] (2 x 3) the minimum-norm
 // Gauss-Newton step is  dx = -J^T (J J^T)^{-1} F.  The paper locates cores by
-// thresholding rho = |psi|^2 on refined point sets (Sec. 4, sftubeeval3);
+// thresholding rho = |psi|^2 on refined point sets (Sec. 4.3, sftubeeval3);
 // this iteration refines such candidates to the zero set of the series.
 #include <cmath>
 

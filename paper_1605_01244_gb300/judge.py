@@ -1,4 +1,4 @@
-"""Dense local-grid judge of vortex cores (SURVEY row a11).
+"""Dense local-grid judge of vortex cores.
 
 psi is evaluated by the NFFT on a fine R1 x R2 x R3 lattice spanning a local
 box, every lattice face around which the phase of psi winds by +-2 pi is
@@ -6,7 +6,7 @@ reported (``nfft3_plaquette_crossings``), and the face centres are refined
 onto the zero set by the Newton locator and de-duplicated.  The result is the
 ground truth and the fallback for the learned proposals, and the referee of
 their miss rate.  (The paper renders isosurfaces of rho = |psi|^2 on fine
-rectilinear grids for the same purpose, Sec. 4.)
+rectilinear grids for the same purpose, Sec. 5.)
 """
 from __future__ import annotations
 

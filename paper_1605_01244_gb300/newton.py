@@ -1,11 +1,11 @@
-"""Vortex-core locator: Newton iteration onto the zeros of psi (SURVEY row a9).
+"""Vortex-core locator: Newton iteration onto the zeros of psi.
 
 Each iteration sets the current points on the plan, evaluates psi and its
 gradient with ``eval_grad`` and applies the minimum-norm Gauss-Newton step
 dx = -J^T (J J^T)^{-1} F (``nfft3_newton_step``, F = (Re psi, Im psi),
 J = [Re grad psi; Im grad psi]) to every point still active.  Converged
 points are then de-duplicated (``nfft3_dedupe``).  The paper thresholds
-rho = |psi|^2 on refined grids instead (Sec. 4, sftubeeval3).
+rho = |psi|^2 on refined grids instead (Sec. 4.3, sftubeeval3).
 
 Coordinates are torus coordinates (see ``mapping``); lengths are in torus
 units.

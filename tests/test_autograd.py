@@ -1,4 +1,4 @@
-"""Differentiation of the NFFT (SURVEY row a8).
+"""Differentiation of the NFFT.
 
 CPU: the backward formulas (dL/dc = A^H G, dL/dx = Re(conj(G) grad f)) are
 pinned by torch.autograd.gradcheck on an oracle-backed Function that uses

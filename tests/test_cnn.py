@@ -1,4 +1,4 @@
-"""Core-proposal CNN (SURVEY row a10).
+"""Core-proposal CNN.
 
 CPU: the numpy reference (oracle/cnn_ref.py) is pinned against torch's CPU
 conv3d (a library routine) and against finite differences of its own loss.

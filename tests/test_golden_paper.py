@@ -11,7 +11,7 @@ printed numbers take on values of order 100.
 
 The oracle's direct sum at (a sample of) the same grid must agree with numpy's
 inverse FFT to that level; any index, sign or ordering mistake gives O(1)
-differences.  The fast CPU NFFT at m = 8 (largest window of this build) must
+differences.  The fast CPU NFFT at m = 8 (the largest window compiled in) must
 come within the window-error bound of the same grid values.
 """
 import os

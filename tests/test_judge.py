@@ -1,4 +1,4 @@
-"""Dense-grid judge (SURVEY row a11): plaquette winding test and core refinement.
+"""Dense-grid judge: plaquette winding test and core refinement.
 
 Pins: a straight vortex psi = (x1 - p) + i (x2 - q) crosses exactly one
 face with normal 3 per lattice layer, at the cell holding (p, q), with

@@ -1,4 +1,4 @@
-"""Vortex-core Newton locator (SURVEY row a9).
+"""Vortex-core Newton locator.
 
 Pins: the two-vortex ansatz psi = exp(-|x|^2/18)((x1 - a) + i x2)((x1 + a) - i x3)/(1 + |x|^2)
 vanishes on the lines {x1 = a, x2 = 0} and {x1 = -a, x3 = 0}; with a on a
