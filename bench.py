@@ -235,6 +235,19 @@ def run_ours(args, rank, world, local):
         e1.record(s)
         barrier()
         ms_eval = e0.elapsed_time(e1) / args.steps
+        # gradient throughput (points set): i k-weighted series (four grids)
+        # and window derivative (one grid), a few calls each
+        grad_ms = {}
+        for name, fn in (("eval_grad", lambda: plan.eval_grad(c, want_f=True)),
+                         ("eval_grad_window", lambda: plan.eval_grad_window(c, want_f=True))):
+            fn()
+            barrier()
+            e0.record(s)
+            for _ in range(min(args.steps, 3)):
+                fn()
+            e1.record(s)
+            barrier()
+            grad_ms[name] = e0.elapsed_time(e1) / min(args.steps, 3)
         # accuracy on the fixed subsample (oracle on rank 0's host; computed later)
         idx = np.concatenate([wl.rng(99).choice(M // 2, SUBSAMPLE, replace=False),
                               M // 2 + wl.rng(98).choice(M - M // 2, SUBSAMPLE, replace=False)])
@@ -282,7 +295,7 @@ def run_ours(args, rank, world, local):
                             "%d values): floor %d x %d rows x M / (152 SMs x 2.07 GHz) = %.2f ms, achieved "
                             "%.0f %% of it" % (w, w, w, l1_floor_ms, 100 * l1_floor_ms / g_ms))
         results[fam] = {
-            "m": m, "ms_per_step": ms, "ms_eval_only": ms_eval, "e2e_ms": e2e_ms,
+            "m": m, "ms_per_step": ms, "ms_eval_only": ms_eval, "e2e_ms": e2e_ms, "grad_ms": grad_ms,
             "stages_ms": stages, "launches_per_step": launches.value / args.steps,
             "clocks": clocks, "roofline": roof, "f_sub": f_sub, "idx": idx,
             "h2d": M * 3 * 8 + N ** 3 * 2 * rb, "d2h": M * 2 * rb,
@@ -320,6 +333,7 @@ def run_ours(args, rank, world, local):
             "value": pts / (r["ms_per_step"] * 1e-3) / 1e6,
             "ms_per_step": r["ms_per_step"], "m": r["m"], "rel_l2_vs_oracle": r["rel_l2"],
             "eval_only_mpoints_s": pts / (r["ms_eval_only"] * 1e-3) / 1e6,
+            "gradient_mpoints_s": {k: pts / (v * 1e-3) / 1e6 for k, v in r["grad_ms"].items()},
             "stages_ms": r["stages_ms"], "roofline": r["roofline"],
             "fft_share": r["stages_ms"]["fft"] / max(sum(r["stages_ms"].values()), 1e-12),
             "e2e": {"value": pts / (r["e2e_ms"] * 1e-3) / 1e6, "unit": "Mpoints/s",
@@ -342,6 +356,7 @@ def run_ours(args, rank, world, local):
                    "parallelism": "points sharded, no collective" if world > 1 else "single GPU"},
         "rel_l2_vs_oracle": main["rel_l2_vs_oracle"],
         "eval_only_mpoints_s": main["eval_only_mpoints_s"],
+        "gradient_mpoints_s": main["gradient_mpoints_s"],
         "stages_ms": main["stages_ms"], "fft_share": main["fft_share"],
         "roofline": main["roofline"],
         "e2e": main["e2e"],

@@ -111,6 +111,24 @@ int nfft3d_eval_grad(nfft3_plan p, const double *c, double *f, double *grad);
 int nfft3f_eval_grad(nfft3_plan p, const float *c, float *f, float *grad);
 
 /*
+ * f and grad as nfft3*_eval_grad, by differentiating the window instead of
+ * the series: one oversampled transform of c, then
+ *   grad_d f_j = sum_l g_l n_d phi'(u_d - l_d) prod_{e != d} phi(u_e - l_e),
+ * the derivative of the window sum of eq. (fs)'s NFFT approximation
+ * (u = n (x + 1/2), torus units).  One grid and one transform instead of four;
+ * the approximation error of the gradient is about ten times that of
+ * nfft3*_eval_grad at the same m (one more m gives the same accuracy).
+ * Default and tma gather modes only (NFFT3_ERR_ARG otherwise).
+ * The _stored variant gathers from the grid of a preceding
+ * nfft3*_precompute(c, 0 or 1) (NFFT3_ERR_NO_COEFFS without one;
+ * NFFT3_ERR_ARG if that grid was stored in the tile-staged layout).
+ */
+int nfft3d_eval_grad_window(nfft3_plan p, const double *c, double *f, double *grad);
+int nfft3f_eval_grad_window(nfft3_plan p, const float *c, float *f, float *grad);
+int nfft3d_eval_grad_window_stored(nfft3_plan p, double *f, double *grad);
+int nfft3f_eval_grad_window_stored(nfft3_plan p, float *f, float *grad);
+
+/*
  * nfft3d_eval_grad without allocation.  The paper has no counterpart: this
  * is a service for callers that cannot call cudaMalloc when they evaluate --
  * a process whose device memory is already reserved by another allocator (a

@@ -51,6 +51,24 @@ def kb_phi(tau, m: int, b: float):
     return np.where((tau > -al) & (tau <= al), val, 0.0)
 
 
+def kb_dphi(tau, m: int, b: float):
+    """Derivative of ``kb_phi`` in tau inside the support:
+    phi'(tau) = -tau (b s cosh(b s) - sinh(b s)) / (pi s^3),  s = sqrt(alpha^2 - tau^2),
+    with the series (b s)^3/3 + (b s)^5/30 + (b s)^7/840 of the bracket for
+    small b s (its limit at the support ends is -tau b^3 / (3 pi))."""
+    al = m + 0.5
+    tau = np.asarray(tau, dtype=np.float64)
+    s = np.sqrt(np.maximum((al - tau) * (al + tau), 0.0))
+    z = b * s
+    small = z < 1e-2
+    zs = np.where(small, 1.0, z)
+    ss = np.where(small, 1.0, s)
+    exact = -tau * (zs * np.cosh(zs) - np.sinh(zs)) / (math.pi * ss ** 3)
+    series = -tau * b ** 3 * (1.0 / 3.0 + z ** 2 / 30.0 + z ** 4 / 840.0) / math.pi
+    val = np.where(small, series, exact)
+    return np.where((tau > -al) & (tau <= al), val, 0.0)
+
+
 def kb_Phi(k, n: int, m: int, b: float):
     """Fourier transform of ``kb_phi`` at nu = k/n: I0(alpha sqrt(b^2 - (2 pi k/n)^2))."""
     k = np.asarray(k, dtype=np.float64)
@@ -130,6 +148,42 @@ def forward_grad(c, x, n, m: int):
         cd = 2j * math.pi * kd * c
         grads.append(_gather(_oversampled_grid(cd, N, n, ks, dec), x, n, m, bs))
     return f, np.stack(grads, axis=1)
+
+
+def forward_grad_window(c, x, n, m: int):
+    """Gradient by differentiating the window instead of the series: one grid
+    (steps 1-2 of ``forward``), then for each dimension d the window sum of
+    step 3 with phi replaced by n_d phi' in dimension d, since
+    d/dx_d phi(u_d - l_d) = n_d phi'(u_d - l_d) with u_d = n_d (x_d + 1/2).
+    Returns (f, grad)."""
+    c = np.asarray(c, dtype=np.complex128)
+    N, n, ks, bs, dec = _setup(c.shape, n, m)
+    g = _oversampled_grid(c, N, n, ks, dec)
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    l0s, ws = _window_rows(x, n, m, bs)
+    xw = x - np.floor(x + 0.5)
+    a = np.arange(2 * m + 1)
+    dws = []
+    for d in range(3):
+        u = n[d] * (xw[:, d] + 0.5)
+        tau = u[:, None] - (l0s[d][:, None] + a[None, :])
+        dws.append(n[d] * kb_dphi(tau, m, bs[d]))
+    M = x.shape[0]
+    f = np.zeros(M, dtype=np.complex128)
+    grad = np.zeros((M, 3), dtype=np.complex128)
+    i3 = (l0s[2][:, None] + a[None, :]) % n[2]
+    for p in range(2 * m + 1):
+        i1 = (l0s[0] + p) % n[0]
+        for q in range(2 * m + 1):
+            i2 = (l0s[1] + q) % n[1]
+            rows = g[i1[:, None], i2[:, None], i3]
+            inner = np.sum(rows * ws[2], axis=1)
+            inner_d = np.sum(rows * dws[2], axis=1)
+            f += ws[0][:, p] * ws[1][:, q] * inner
+            grad[:, 0] += dws[0][:, p] * ws[1][:, q] * inner
+            grad[:, 1] += ws[0][:, p] * dws[1][:, q] * inner
+            grad[:, 2] += ws[0][:, p] * ws[1][:, q] * inner_d
+    return f, grad
 
 
 def adjoint(f, x, N, n, m: int):

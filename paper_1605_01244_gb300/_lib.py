@@ -47,6 +47,10 @@ SIGNATURES = {
     "nfft3f_eval_stored": (_I, [_P, _P]),
     "nfft3d_eval_grad_stored": (_I, [_P, _P, _P]),
     "nfft3f_eval_grad_stored": (_I, [_P, _P, _P]),
+    "nfft3d_eval_grad_window": (_I, [_P, _P, _P, _P]),
+    "nfft3f_eval_grad_window": (_I, [_P, _P, _P, _P]),
+    "nfft3d_eval_grad_window_stored": (_I, [_P, _P, _P]),
+    "nfft3f_eval_grad_window_stored": (_I, [_P, _P, _P]),
     "nfft3_set_num_points": (_I, [_P, _I64]),
     "nfft3d_eval_host": (_I, [_P, _P, _P, _P]),
     "nfft3f_eval_host": (_I, [_P, _P, _P, _P]),

@@ -1,0 +1,141 @@
+// Shared pieces of the column-parallel gathers (gather_col.cu, gather_wd.cu):
+// lane-group size, double-float arithmetic helpers and the per-lane tap
+// weight evaluators (value, and value + derivative for the window-derivative
+// gradient).
+#pragma once
+#include "internal.cuh"
+
+namespace gbnfft {
+namespace {
+
+template <int W> struct GroupSize {
+    static constexpr int value = W <= 2 ? 2 : W <= 4 ? 4 : W <= 8 ? 8 : W <= 16 ? 16 : 32;
+};
+
+// ---- double-float helpers (same arithmetic as gather_df.cu) ------------------
+__device__ __forceinline__ void df_mac(float &ah, float &al, float xh, float xl, float yh,
+                                       float yl) {
+    const float p = __fmul_rn(xh, yh);
+    float e = __fmaf_rn(xh, yh, -p);
+    e = __fmaf_rn(xh, yl, e);
+    e = __fmaf_rn(xl, yh, e);
+    const float s = __fadd_rn(ah, p);
+    const float bb = __fsub_rn(s, ah);
+    const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    al = __fadd_rn(al, __fadd_rn(err, e));
+    ah = s;
+}
+__device__ __forceinline__ void df_norm(float &ah, float &al) {
+    const float s = __fadd_rn(ah, al);
+    al = __fsub_rn(al, __fsub_rn(s, ah));
+    ah = s;
+}
+__device__ __forceinline__ void df_add(float &ah, float &al, float bh, float bl) {
+    const float s = __fadd_rn(ah, bh);
+    const float bb = __fsub_rn(s, ah);
+    const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    al = __fadd_rn(al, __fadd_rn(err, bl));
+    ah = s;
+}
+__device__ __forceinline__ void df_horner_step(float &vh, float &vl, float th, float tl, float ch,
+                                               float cl) {
+    const float p = __fmul_rn(vh, th);
+    float e = __fmaf_rn(vh, th, -p);
+    e = __fmaf_rn(vh, tl, e);
+    e = __fmaf_rn(vl, th, e);
+    const float s = __fadd_rn(p, ch);
+    const float bb = __fsub_rn(s, p);
+    float err = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(ch, bb));
+    err = __fadd_rn(err, __fadd_rn(e, cl));
+    vh = __fadd_rn(s, err);
+    vl = __fsub_rn(err, __fsub_rn(vh, s));
+}
+
+// Tap weights of the double-float gather, per lane (its tap) and dimension,
+// as float pairs.  WeightsDF: Horner in double-float on the FP32 pipe with the
+// hi/lo coefficient table.  WeightsFP64: Horner in FP64 on the FP64 pipe --
+// which the window sums leave idle, so it runs alongside them -- then an exact
+// integer split of each weight into hi + lo.
+template <int MM> struct WeightsDF {
+    using Table = PolyDF<MM>;
+    static constexpr int W = 2 * MM + 1, D = kPolyDegDF;
+    float ch[3][W][D + 1];
+    float cl[3][W][D + 1];
+    __device__ void load(const Table &P) {
+        for (int i = threadIdx.x; i < 3 * W * (D + 1); i += blockDim.x) {
+            (&ch[0][0][0])[i] = (&P.ch[0][0][0])[i];
+            (&cl[0][0][0])[i] = (&P.cl[0][0][0])[i];
+        }
+    }
+    __device__ __forceinline__ void eval(int d, int tap, double s, float &wh, float &wl) const {
+        const double t = 2.0 * s - 1.0;
+        const float th = __double2float_rn(t);
+        const float tl = __double2float_rn(t - (double)th);
+        float vh = ch[d][tap][D], vl = cl[d][tap][D];
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) df_horner_step(vh, vl, th, tl, ch[d][tap][k], cl[d][tap][k]);
+        wh = vh;
+        wl = vl;
+    }
+};
+template <int MM> struct WeightsFP64 {
+    using Table = Poly<double, MM>;
+    static constexpr int W = 2 * MM + 1, D = PolyDeg<double>::value;
+    double c[3][W][D + 1];
+    __device__ void load(const Table &P) {
+        for (int i = threadIdx.x; i < 3 * W * (D + 1); i += blockDim.x) (&c[0][0][0])[i] = (&P.c[0][0][0])[i];
+    }
+    __device__ __forceinline__ void eval(int d, int tap, double s, float &wh, float &wl) const {
+        const double t = 2.0 * s - 1.0;
+        double v = c[d][tap][D];
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) v = fma(v, t, c[d][tap][k]);
+        split_df(v, wh, wl);
+    }
+};
+
+// Value and derivative weights: P(t) and dP/dx = -2 n_d P'(t) (t = 2s - 1,
+// s decreases by n_d per unit of x), Horner for P and P' together.
+template <int MM> struct WeightsFP64D {
+    using Table = Poly<double, MM>;
+    static constexpr int W = 2 * MM + 1, D = PolyDeg<double>::value;
+    double c[3][W][D + 1];
+    __device__ void load(const Table &P) {
+        for (int i = threadIdx.x; i < 3 * W * (D + 1); i += blockDim.x) (&c[0][0][0])[i] = (&P.c[0][0][0])[i];
+    }
+    // value (hi, lo) and derivative (hi, lo) scaled by dxs = -2 n_d
+    __device__ __forceinline__ void eval(int d, int tap, double s, double dxs, float &wh, float &wl, float &dh,
+                                         float &dl) const {
+        const double t = 2.0 * s - 1.0;
+        double v = c[d][tap][D], dv = 0.0;
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) {
+            dv = fma(dv, t, v);
+            v = fma(v, t, c[d][tap][k]);
+        }
+        split_df(v, wh, wl);
+        split_df(dv * dxs, dh, dl);
+    }
+};
+template <int MM> struct WeightsF32D {
+    using Table = Poly<float, MM>;
+    static constexpr int W = 2 * MM + 1, D = PolyDeg<float>::value;
+    float c[3][W][D + 1];
+    __device__ void load(const Table &P) {
+        for (int i = threadIdx.x; i < 3 * W * (D + 1); i += blockDim.x) (&c[0][0][0])[i] = (&P.c[0][0][0])[i];
+    }
+    __device__ __forceinline__ void eval(int d, int tap, float s, float dxs, float &w, float &dw) const {
+        const float t = 2.f * s - 1.f;
+        float v = c[d][tap][D], dv = 0.f;
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) {
+            dv = fmaf(dv, t, v);
+            v = fmaf(v, t, c[d][tap][k]);
+        }
+        w = v;
+        dw = dv * dxs;
+    }
+};
+
+}  // namespace
+}  // namespace gbnfft

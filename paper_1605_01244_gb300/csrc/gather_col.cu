@@ -18,53 +18,10 @@
 //
 // Two arithmetic variants: FP32 (mixed family) and double-float on the FP32
 // pipe (FP64 family; see gather_df.cu for the arithmetic).
-#include "internal.cuh"
+#include "col_common.cuh"
 
 namespace gbnfft {
 namespace {
-
-template <int W> struct GroupSize {
-    static constexpr int value = W <= 2 ? 2 : W <= 4 ? 4 : W <= 8 ? 8 : W <= 16 ? 16 : 32;
-};
-
-// ---- double-float helpers (same arithmetic as gather_df.cu) ------------------
-__device__ __forceinline__ void df_mac(float &ah, float &al, float xh, float xl, float yh,
-                                       float yl) {
-    const float p = __fmul_rn(xh, yh);
-    float e = __fmaf_rn(xh, yh, -p);
-    e = __fmaf_rn(xh, yl, e);
-    e = __fmaf_rn(xl, yh, e);
-    const float s = __fadd_rn(ah, p);
-    const float bb = __fsub_rn(s, ah);
-    const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    al = __fadd_rn(al, __fadd_rn(err, e));
-    ah = s;
-}
-__device__ __forceinline__ void df_norm(float &ah, float &al) {
-    const float s = __fadd_rn(ah, al);
-    al = __fsub_rn(al, __fsub_rn(s, ah));
-    ah = s;
-}
-__device__ __forceinline__ void df_add(float &ah, float &al, float bh, float bl) {
-    const float s = __fadd_rn(ah, bh);
-    const float bb = __fsub_rn(s, ah);
-    const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
-    al = __fadd_rn(al, __fadd_rn(err, bl));
-    ah = s;
-}
-__device__ __forceinline__ void df_horner_step(float &vh, float &vl, float th, float tl, float ch,
-                                               float cl) {
-    const float p = __fmul_rn(vh, th);
-    float e = __fmaf_rn(vh, th, -p);
-    e = __fmaf_rn(vh, tl, e);
-    e = __fmaf_rn(vl, th, e);
-    const float s = __fadd_rn(p, ch);
-    const float bb = __fsub_rn(s, p);
-    float err = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(ch, bb));
-    err = __fadd_rn(err, __fadd_rn(e, cl));
-    vh = __fadd_rn(s, err);
-    vl = __fsub_rn(err, __fsub_rn(vh, s));
-}
 
 // ---- FP32 (mixed family) -----------------------------------------------------
 template <int MM, int NG>
@@ -167,21 +124,16 @@ __global__ void __launch_bounds__(256) gather_col_f32_kernel(const float2 *__res
 #define GBNFFT_DF_MINB 3   // resident 256-thread blocks per SM the value kernel is compiled for
 #endif
 
-template <int MM, int NG>
+template <int MM, int NG, class Wt>
 __global__ void __launch_bounds__(256, NG == 1 ? GBNFFT_DF_MINB : 2) gather_col_df_kernel(const float4 *__restrict__ G, Grid3 pg,
                                                             PointsView<double> pts,
-                                                            const __grid_constant__ PolyDF<MM> P,
+                                                            const __grid_constant__ typename Wt::Table P,
                                                             double2 *__restrict__ f,
                                                             double2 *__restrict__ grad) {
     constexpr int W = 2 * MM + 1;
     constexpr int GS = GroupSize<W>::value;
-    constexpr int D = kPolyDegDF;
-    __shared__ float ch[3][W][D + 1];
-    __shared__ float cl[3][W][D + 1];
-    for (int i = threadIdx.x; i < 3 * W * (D + 1); i += blockDim.x) {
-        (&ch[0][0][0])[i] = (&P.ch[0][0][0])[i];
-        (&cl[0][0][0])[i] = (&P.cl[0][0][0])[i];
-    }
+    __shared__ Wt wt;
+    wt.load(P);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -197,14 +149,8 @@ __global__ void __launch_bounds__(256, NG == 1 ? GBNFFT_DF_MINB : 2) gather_col_
         const double s[3] = {pts.s1[jj], pts.s2[jj], pts.s3[jj]};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const double t = 2.0 * s[d] - 1.0;
-            const float th = __double2float_rn(t);
-            const float tl = __double2float_rn(t - (double)th);
-            float vh = ch[d][tap][D], vl = cl[d][tap][D];
-#pragma unroll
-            for (int k = D - 1; k >= 0; --k) df_horner_step(vh, vl, th, tl, ch[d][tap][k], cl[d][tap][k]);
-            mwh[d] = sub < W ? vh : 0.f;
-            mwl[d] = sub < W ? vl : 0.f;
+            wt.eval(d, tap, s[d], mwh[d], mwl[d]);
+            if (sub >= W) mwh[d] = mwl[d] = 0.f;
         }
     }
     float w2h[W], w2l[W];
@@ -342,12 +288,17 @@ cudaError_t col_f32_dispatch(const float2 *G, Grid3 g, PointsView<float> pts,
 
 template <int MM, int NG>
 cudaError_t col_df_dispatch(const float4 *G, Grid3 g, PointsView<double> pts, const WinTableDF &w,
-                            double2 *f, double2 *grad, cudaStream_t st) {
+                            const WinTable<double> &w64, bool fp64_weights, double2 *f, double2 *grad,
+                            cudaStream_t st) {
     constexpr int GS = GroupSize<2 * MM + 1>::value;
     const int threads = 256;
     const int64_t blocks = (pts.M * GS + threads - 1) / threads;
-    gather_col_df_kernel<MM, NG><<<(unsigned)blocks, threads, 0, st>>>(
-        G, g, pts, make_poly_df<MM>(w), f, grad);
+    if (fp64_weights)
+        gather_col_df_kernel<MM, NG, WeightsFP64<MM>><<<(unsigned)blocks, threads, 0, st>>>(
+            G, g, pts, make_poly<double, MM>(w64), f, grad);
+    else
+        gather_col_df_kernel<MM, NG, WeightsDF<MM>><<<(unsigned)blocks, threads, 0, st>>>(
+            G, g, pts, make_poly_df<MM>(w), f, grad);
     return cudaGetLastError();
 }
 
@@ -370,17 +321,18 @@ cudaError_t col_f32_select(const float2 *G, Grid3 g, int m, PointsView<float> pt
 
 template <int NG>
 cudaError_t col_df_select(const float4 *G, Grid3 g, int m, PointsView<double> pts,
-                          const WinTableDF &w, double2 *f, double2 *grad, cudaStream_t st) {
+                          const WinTableDF &w, const WinTable<double> &w64, bool fp64_weights, double2 *f,
+                          double2 *grad, cudaStream_t st) {
     if (pts.M == 0) return cudaSuccess;
     switch (m) {
-        case 1: return col_df_dispatch<1, NG>(G, g, pts, w, f, grad, st);
-        case 2: return col_df_dispatch<2, NG>(G, g, pts, w, f, grad, st);
-        case 3: return col_df_dispatch<3, NG>(G, g, pts, w, f, grad, st);
-        case 4: return col_df_dispatch<4, NG>(G, g, pts, w, f, grad, st);
-        case 5: return col_df_dispatch<5, NG>(G, g, pts, w, f, grad, st);
-        case 6: return col_df_dispatch<6, NG>(G, g, pts, w, f, grad, st);
-        case 7: return col_df_dispatch<7, NG>(G, g, pts, w, f, grad, st);
-        case 8: return col_df_dispatch<8, NG>(G, g, pts, w, f, grad, st);
+        case 1: return col_df_dispatch<1, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
+        case 2: return col_df_dispatch<2, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
+        case 3: return col_df_dispatch<3, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
+        case 4: return col_df_dispatch<4, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
+        case 5: return col_df_dispatch<5, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
+        case 6: return col_df_dispatch<6, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
+        case 7: return col_df_dispatch<7, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
+        case 8: return col_df_dispatch<8, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -409,10 +361,10 @@ cudaError_t launch_gather_col_f32(const float2 *G, Grid3 g, int m, PointsView<fl
 }
 
 cudaError_t launch_gather_col_df(const float4 *G, Grid3 g, int m, PointsView<double> pts,
-                                 const WinTableDF &w, double2 *f, double2 *grad, int ng,
-                                 cudaStream_t st) {
-    return ng == 4 ? col_df_select<4>(G, g, m, pts, w, f, grad, st)
-                   : col_df_select<1>(G, g, m, pts, w, f, nullptr, st);
+                                 const WinTableDF &w, const WinTable<double> &w64, bool fp64_weights,
+                                 double2 *f, double2 *grad, int ng, cudaStream_t st) {
+    return ng == 4 ? col_df_select<4>(G, g, m, pts, w, w64, fp64_weights, f, grad, st)
+                   : col_df_select<1>(G, g, m, pts, w, w64, fp64_weights, f, nullptr, st);
 }
 
 }  // namespace gbnfft

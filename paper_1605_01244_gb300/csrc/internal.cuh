@@ -110,6 +110,16 @@ __device__ __forceinline__ void split_df(double v, float &hi, float &lo) {
     lo = sign ? -lf : lf;
 }
 
+// ---- window-derivative gradient gathers (gather_wd.cu) --------------------------
+// f and grad[3j + d] from one padded grid (origin layout): the window sum with
+// phi replaced by n_d phi' in dimension d.  n: oversampled sizes.
+cudaError_t launch_gather_wd_df(const float4 *G, Grid3 pg, int m, PointsView<double> pts,
+                                const WinTable<double> &w, const int n[3], double2 *f, double2 *grad,
+                                cudaStream_t st);
+cudaError_t launch_gather_wd_f32(const float2 *G, Grid3 pg, int m, PointsView<float> pts,
+                                 const WinTable<float> &w, const int n[3], float2 *f, float2 *grad,
+                                 cudaStream_t st);
+
 // ---- fused forward transform (fft_fused.cu) -----------------------------------
 // Deconvolve + inverse DFT of the oversampled grid + ghost-padded output
 // P[q][p] = g_q[(p - shift) mod n] for ng grids (q > 0: 2 pi i k_q c_k D), in
@@ -141,8 +151,8 @@ cudaError_t launch_gather_col_f32(const float2 *G, Grid3 g, int m, PointsView<fl
                                   const WinTable<float> &w, float2 *f, float2 *grad, int ng,
                                   cudaStream_t st);
 cudaError_t launch_gather_col_df(const float4 *G, Grid3 g, int m, PointsView<double> pts,
-                                 const WinTableDF &w, double2 *f, double2 *grad, int ng,
-                                 cudaStream_t st);
+                                 const WinTableDF &w, const WinTable<double> &w64, bool fp64_weights,
+                                 double2 *f, double2 *grad, int ng, cudaStream_t st);
 
 // ---- launchers implemented in kernels.cu (all enqueue on `st`) ------------
 

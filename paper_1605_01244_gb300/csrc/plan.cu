@@ -389,6 +389,8 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         // native = one thread per point in the family's own precision (FP64
         // on the FP64 pipe)
         const char *g = std::getenv("GBNFFT_GATHER");
+        const char *wv = std::getenv("GBNFFT_DF_WEIGHTS");
+        p->df_weights_fp64 = !(wv && !std::strcmp(wv, "df"));
         p->gather_mode = !g                           ? 3
                          : !std::strcmp(g, "thread") ? 1
                          : !std::strcmp(g, "native") ? 2
@@ -598,8 +600,9 @@ int ensure_pgrid(nfft3_plan p, int ng) {
 // grid, tma mode, tensor map and chunk list ready) needs the stencil centre as
 // origin (shift m); the column kernels read from the first node (shift 0).
 // The choice is recorded so that a stored grid is read the way it was written.
-int pad_shift(nfft3_plan p, int ng) {
-    const bool tile = ng == 1 && p->prec == 32 && p->gather_mode == 0 && p->tmap_ok && p->nchunks > 0;
+int pad_shift(nfft3_plan p, int ng, bool allow_tile = true) {
+    const bool tile = allow_tile && ng == 1 && p->prec == 32 && p->gather_mode == 0 && p->tmap_ok &&
+                      p->nchunks > 0;
     p->pgrid_shift = tile ? p->m : 0;
     return p->pgrid_shift;
 }
@@ -614,7 +617,7 @@ cudaError_t gather_padded(nfft3_plan p, int ng, typename Cplx<R>::T *f, typename
     p->launches += 1;
     if (prec == 64)
         return launch_gather_col_df((const float4 *)p->pgrid, pg, p->m, points_view<double>(p), p->wtdf,
-                                    (double2 *)f, (double2 *)grad, ng, p->stream);
+                                    p->wt64, p->df_weights_fp64, (double2 *)f, (double2 *)grad, ng, p->stream);
     if (ng == 1 && p->pgrid_shift != 0 && p->tmap_ok && p->nchunks > 0)
         return launch_gather_tma_f32(p->tmap, p->pb.chunks, p->nchunks, p->pb.nt2, p->pb.nt3, g, p->m,
                                      points_view<float>(p), p->wt32, (float2 *)f, p->pb.status, p->stream);
@@ -669,14 +672,14 @@ cudaError_t gather_stage(nfft3_plan p, typename Cplx<R>::T *G, int ng, typename 
 // Fused forward transform of c into the padded grid(s) (ng = 1 or 4): the
 // deconvolution, the three DFT line passes and the padded layout in three
 // launches; the column / tile-staged gathers read the result directly.
-template <typename R> int fused_transform(nfft3_plan p, const R *c, int ng) {
+template <typename R> int fused_transform(nfft3_plan p, const R *c, int ng, bool allow_tile = true) {
     int st = ensure_pgrid(p, ng);
     if (st == NFFT3_OK) st = ensure_fscratch(p, ng);
     if (st != NFFT3_OK) return st;
     const void *tw[3] = {p->tw[0], p->tw[1], p->tw[2]};
     const cudaError_t e = launch_fused_series<R>(
         (const typename Cplx<R>::T *)c, p->N, p->n, (const R *)p->D[0], (const R *)p->D[1],
-        (const R *)p->D[2], tw, p->fscratch, p->pgrid, p->m, pad_shift(p, ng), ng, p->stream);
+        (const R *)p->D[2], tw, p->fscratch, p->pgrid, p->m, pad_shift(p, ng, allow_tile), ng, p->stream);
     p->launches += 3;
     return cuda_status(e);
 }
@@ -836,6 +839,80 @@ template <typename R> int eval_stored_impl(nfft3_plan p, R *f, R *grad, int ng) 
     return finish(p, cuda_status(e));
 }
 
+// ---- window-derivative gradient ------------------------------------------------
+// One transform of c into the padded grid (origin layout), then the gather
+// that differentiates the window (gather_wd.cu).  Padded-grid gather modes
+// (default and tma) only.
+template <typename R> cudaError_t gather_wd(nfft3_plan p, R *f, R *grad) {
+    using C = typename Cplx<R>::T;
+    const Grid3 pg{p->n[0] + 2 * p->m, p->n[1] + 2 * p->m, p->n[2] + 2 * p->m};
+    p->launches += 1;
+    if constexpr (sizeof(R) == 8)
+        return launch_gather_wd_df((const float4 *)p->pgrid, pg, p->m, points_view<double>(p), p->wt64, p->n,
+                                   (C *)f, (C *)grad, p->stream);
+    else
+        return launch_gather_wd_f32((const float2 *)p->pgrid, pg, p->m, points_view<float>(p), p->wt32, p->n,
+                                    (C *)f, (C *)grad, p->stream);
+}
+
+// c -> padded grid (one grid, origin layout), by the fused transform or by
+// deconvolution + cuFFT + padding.
+template <typename R> int series_to_origin_pgrid(nfft3_plan p, const R *c) {
+    using C = typename Cplx<R>::T;
+    if (p->fused) return fused_transform<R>(p, c, 1, false);
+    int st = ensure_pgrid(p, 1);
+    if (st != NFFT3_OK) return st;
+    const Grid3 g{p->n[0], p->n[1], p->n[2]};
+    const Grid3 pg{g.n1 + 2 * p->m, g.n2 + 2 * p->m, g.n3 + 2 * p->m};
+    C *G = (C *)p->grid;
+    cudaError_t e = launch_deconv_scatter<R>((const C *)c, p->N[0], p->N[1], p->N[2], (const R *)p->D[0],
+                                             (const R *)p->D[1], (const R *)p->D[2], G, g, 0, p->stream);
+    if (e != cudaSuccess) return NFFT3_ERR_CUDA;
+    st = exec_grid_fft(p, G, sizeof(R) == 8 ? 64 : 32, CUFFT_INVERSE, 1);
+    if (st != NFFT3_OK) return st;
+    if constexpr (sizeof(R) == 8)
+        e = launch_pad_grid_df((const double2 *)G, g, (float4 *)p->pgrid, pg, 1, pad_shift(p, 1, false), p->stream);
+    else
+        e = launch_pad_grid_f32((const float2 *)G, g, (float2 *)p->pgrid, pg, 1, pad_shift(p, 1, false), p->stream);
+    p->launches += 2;
+    return cuda_status(e);
+}
+
+template <typename R> int eval_grad_window_impl(nfft3_plan p, const R *c, R *f, R *grad) {
+    constexpr int prec = sizeof(R) == 8 ? 64 : 32;
+    if (!p || p->prec != prec || (p->gather_mode != 0 && p->gather_mode != 3)) return NFFT3_ERR_ARG;
+    if (!p->points_ok) return NFFT3_ERR_NO_POINTS;
+    if (p->M > 0 && (!c || !grad)) return NFFT3_ERR_ARG;
+    if (p->M == 0) return NFFT3_OK;
+    p->stored_ng = 0;
+    const int rec = rec_begin(p, kRecGrad);
+    rec_mark(p, rec, 1);
+    const int st = series_to_origin_pgrid<R>(p, c);
+    if (st != NFFT3_OK) return st;
+    rec_mark(p, rec, 2);
+    rec_mark(p, rec, 3);
+    const cudaError_t e = gather_wd<R>(p, f, grad);
+    rec_mark(p, rec, 4);
+    return finish(p, cuda_status(e));
+}
+
+template <typename R> int eval_grad_window_stored_impl(nfft3_plan p, R *f, R *grad) {
+    constexpr int prec = sizeof(R) == 8 ? 64 : 32;
+    if (!p || p->prec != prec) return NFFT3_ERR_ARG;
+    if (p->stored_ng < 1) return NFFT3_ERR_NO_COEFFS;
+    if (p->pgrid_shift != 0) return NFFT3_ERR_ARG;   // stored in the tile-staged (centre) layout
+    if (!p->points_ok) return NFFT3_ERR_NO_POINTS;
+    if (p->M == 0) return NFFT3_OK;
+    if (!grad) return NFFT3_ERR_ARG;
+    const int rec = rec_begin(p, kRecGrad);
+    rec_mark(p, rec, 1);
+    rec_mark(p, rec, 2);
+    rec_mark(p, rec, 3);
+    const cudaError_t e = gather_wd<R>(p, f, grad);
+    rec_mark(p, rec, 4);
+    return finish(p, cuda_status(e));
+}
+
 template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
     using C = typename Cplx<R>::T;
     constexpr int prec = sizeof(R) == 8 ? 64 : 32;
@@ -934,6 +1011,19 @@ int nfft3d_eval_grad(nfft3_plan p, const double *c, double *f, double *grad) {
 }
 int nfft3f_eval_grad(nfft3_plan p, const float *c, float *f, float *grad) {
     return eval_grad_impl<float>(p, c, f, grad);
+}
+
+int nfft3d_eval_grad_window(nfft3_plan p, const double *c, double *f, double *grad) {
+    return eval_grad_window_impl<double>(p, c, f, grad);
+}
+int nfft3f_eval_grad_window(nfft3_plan p, const float *c, float *f, float *grad) {
+    return eval_grad_window_impl<float>(p, c, f, grad);
+}
+int nfft3d_eval_grad_window_stored(nfft3_plan p, double *f, double *grad) {
+    return eval_grad_window_stored_impl<double>(p, f, grad);
+}
+int nfft3f_eval_grad_window_stored(nfft3_plan p, float *f, float *grad) {
+    return eval_grad_window_stored_impl<float>(p, f, grad);
 }
 
 int nfft3d_precompute(nfft3_plan p, const double *c, int with_grad) {

@@ -23,6 +23,7 @@ struct nfft3_plan_s {
     gbnfft::WinTableDF wtdf;   // FP64 family: double-float copy for the FP32-pipe gather
     double window_err;
     double window_err_df;
+    int df_weights_fp64;       // GBNFFT_DF_WEIGHTS: FP64-pipe weights (default) or df ("df")
     int gather_mode;           // GBNFFT_GATHER: 0 col (default), 1 thread, 2 native (see plan.cu)
     // tables and grid
     void *D[3];               // deconvolution factors, real type of the family

@@ -145,6 +145,25 @@ class Plan:
         _lib.check(self.prefix + "_eval_grad_stored", self._fn("_eval_grad_stored")(self._h, _ptr(f), _ptr(g)))
         return f, g
 
+    def eval_grad_window(self, c: torch.Tensor, want_f: bool = True):
+        """f and grad (M x 3) by differentiating the window: one transform
+        instead of four; about ten times the i k-method's gradient error at
+        the same m."""
+        self._cuda(c, self.cdtype, self.N, "c")
+        f = torch.empty(self.M, dtype=self.cdtype, device=self.device) if want_f else None
+        g = torch.empty((self.M, 3), dtype=self.cdtype, device=self.device)
+        _lib.check(self.prefix + "_eval_grad_window",
+                   self._fn("_eval_grad_window")(self._h, _ptr(c), _ptr(f), _ptr(g)))
+        return f, g
+
+    def eval_grad_window_stored(self, want_f: bool = True):
+        """eval_grad_window from the grid of a preceding precompute."""
+        f = torch.empty(self.M, dtype=self.cdtype, device=self.device) if want_f else None
+        g = torch.empty((self.M, 3), dtype=self.cdtype, device=self.device)
+        _lib.check(self.prefix + "_eval_grad_window_stored",
+                   self._fn("_eval_grad_window_stored")(self._h, _ptr(f), _ptr(g)))
+        return f, g
+
     def set_num_points(self, M: int):
         """Use M points (at most the capacity given at creation); set_points must follow."""
         if M > self.capacity:

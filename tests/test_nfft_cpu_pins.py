@@ -121,3 +121,47 @@ def test_gradient_approximates_direct():
     assert np.linalg.norm(f - fd) / np.linalg.norm(fd) <= 3e-12
     for d in range(3):
         assert np.linalg.norm(g[:, d] - gd[:, d]) / np.linalg.norm(gd[:, d]) <= 1e-11
+
+
+def test_window_derivative_matches_difference_quotients():
+    """kb_dphi is the derivative of kb_phi: central differences (h = 1e-5,
+    error ~ h^2 phi''' / 6) inside the support, including close to the ends
+    where its small-argument series takes over."""
+    for m, b in ((3, math.pi * 1.5), (6, math.pi * 1.5), (4, math.pi * (2 - 1 / 1.25))):
+        al = m + 0.5
+        tau = np.concatenate([np.linspace(-al + 1e-3, al - 1e-3, 101), [al - 1e-6, -al + 2e-6, 0.0]])
+        h = 1e-7 if m == 6 else 1e-5
+        fd = (nfft_cpu.kb_phi(tau + h, m, b) - nfft_cpu.kb_phi(tau - h, m, b)) / (2 * h)
+        inside = (tau + h <= al) & (tau - h > -al)
+        got = nfft_cpu.kb_dphi(tau, m, b)
+        scale = np.max(np.abs(got))
+        assert np.max(np.abs(got[inside] - fd[inside])) <= 1e-6 * scale, m
+    # limit at the support end and zero at the centre
+    b = math.pi * 1.5
+    assert abs(nfft_cpu.kb_dphi(3.5, 3, b) - (-3.5 * b ** 3 / (3 * math.pi))) <= 1e-12 * b ** 3
+    assert nfft_cpu.kb_dphi(0.0, 3, b) == 0.0
+
+
+def test_window_derivative_gradient_converges_to_direct():
+    """The window-derivative gradient approximates the direct gradient and
+    converges geometrically in m (about one unit of m behind the i k-method);
+    its value output is the plain NFFT's."""
+    N = (12, 8, 10)
+    n = (24, 16, 20)
+    c = wl.gaussian_coeffs(N, 3.0, seed=8)
+    x = wl.uniform_points(150, seed=9)
+    fd, gd = oracle.forward_grad(c, x)
+    errs = []
+    for m in (3, 4, 5, 6, 7):
+        f, g = nfft_cpu.forward_grad_window(c, x, n, m)
+        assert np.array_equal(f, nfft_cpu.forward(c, x, n, m)) or \
+            np.max(np.abs(f - nfft_cpu.forward(c, x, n, m))) <= 1e-13 * np.max(np.abs(f))
+        errs.append(max(np.linalg.norm(g[:, d] - gd[:, d]) / np.linalg.norm(gd[:, d]) for d in range(3)))
+    assert errs[-1] <= 1e-11
+    rate = math.exp(-2 * math.pi * math.sqrt(1 - 1 / 2.0))
+    for e0, e1 in zip(errs[:-1], errs[1:]):
+        assert e1 <= 4 * rate * e0, errs
+    # a sign or scale mistake in the derivative weights would not converge
+    f6, g6 = nfft_cpu.forward_grad(c, x, n, 6)
+    _, w7 = nfft_cpu.forward_grad_window(c, x, n, 7)
+    assert np.linalg.norm(w7 - g6) / np.linalg.norm(g6) <= 1e-10

@@ -246,7 +246,8 @@ def test_window_polynomials_accuracy(prec, tol):
 def test_gather_variants_agree(m, monkeypatch):
     """Gather variants selected by GBNFFT_GATHER: default (column-parallel
     groups over the padded grid; double-float on the FP32 pipe for the FP64
-    family), tma (mixed-family values from TMA-staged shared-memory tiles),
+    family, tap weights by FP64 Horner, or by double-float Horner with
+    GBNFFT_DF_WEIGHTS=df), tma (mixed-family values from TMA-staged shared-memory tiles),
     thread (one thread per point) and native (FP64 family on the FP64 pipe).  Every variant must match the CPU NFFT, for eval and
     eval_grad: to rounding in FP64, to FP32 accuracy in the mixed family."""
     from paper_1605_01244_gb300 import Plan
@@ -254,10 +255,14 @@ def test_gather_variants_agree(m, monkeypatch):
     c = wl.gaussian_coeffs(N, 1e9, seed=30 + m)
     x = wl.mixed_points(900, 0.03, seed=31)
     ref = None
-    for prec, modes in (("f64", ("default", "thread", "native")), ("f32", ("default", "tma", "thread"))):
+    for prec, modes in (("f64", ("default", "df-weights", "thread", "native")), ("f32", ("default", "tma", "thread"))):
         for mode in modes:
+            monkeypatch.delenv("GBNFFT_DF_WEIGHTS", raising=False)
             if mode == "default":
                 monkeypatch.delenv("GBNFFT_GATHER", raising=False)
+            elif mode == "df-weights":
+                monkeypatch.delenv("GBNFFT_GATHER", raising=False)
+                monkeypatch.setenv("GBNFFT_DF_WEIGHTS", "df")
             else:
                 monkeypatch.setenv("GBNFFT_GATHER", mode)
             plan = Plan(N, len(x), m=m, precision=prec)
@@ -318,6 +323,45 @@ def test_fused_transform_matches_cufft_and_cpu(N, prec, monkeypatch):
         assert err(to_np(gs).astype(np.complex128), gc) <= tol_g, name
         plan.precompute(cd)
         assert err(to_np(plan.eval_stored()).astype(np.complex128), fc) <= tol_f, name
+
+
+@pytest.mark.parametrize("N,sigma", [((16, 16, 16), 2.0), ((12, 16, 10), 2.0), ((10, 14, 18), 1.5)])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_window_derivative_gradient(N, sigma, prec, monkeypatch):
+    """eval_grad_window (one transform, derivative of the window) against the
+    CPU restatement of the same method (element-wise) and against the direct
+    sum's gradient (at m + 1 it meets the i k-method's tolerance at m);
+    power-of-two grids take the fused transform, the others cuFFT; the
+    stored variant and the value output agree with eval."""
+    from paper_1605_01244_gb300 import Plan
+    monkeypatch.delenv("GBNFFT_GATHER", raising=False)
+    c = wl.gaussian_coeffs(N, 3.0, seed=60)
+    x = wl.mixed_points(800, 0.05, seed=61)
+    fd, gd = oracle.forward_grad(c, x)
+    # the method's error falls by about exp(-2 pi sqrt(1 - 1/sigma)) per unit of m
+    tols = {2.0: ((6, 2e-10), (7, 1e-11)), 1.5: ((6, 2e-9), (7, 1e-10))}[sigma]
+    for m, tol_d in tols if prec == "f64" else ((4, 5e-6), (5, 5e-6)):
+        plan = Plan(N, len(x), m=m, sigma=sigma, precision=prec)
+        plan.set_points(to_dev(x))
+        cd = to_dev(c, CD[prec])
+        f, g = plan.eval_grad_window(cd)
+        f = to_np(f).astype(np.complex128)
+        g = to_np(g).astype(np.complex128)
+        fw, gw = nfft_cpu.forward_grad_window(c, x, plan.n, m)
+        if prec == "f64":
+            assert max_rel(g, gw) <= 1e-12, m
+            assert max_rel(f, fw) <= 1e-13, m
+        else:
+            assert rel_l2(g, gw) <= 2e-6, m
+        for d in range(3):
+            assert rel_l2(g[:, d], gd[:, d]) <= tol_d, (m, d)
+        fe = to_np(plan.eval(cd)).astype(np.complex128)
+        assert max_rel(f, fe) <= (1e-14 if prec == "f64" else 1e-6)
+        plan.precompute(cd)
+        fs, gs = plan.eval_grad_window_stored()
+        assert max_rel(to_np(gs).astype(np.complex128), g) <= (1e-14 if prec == "f64" else 1e-6)
+        _, g2 = plan.eval_grad_window(cd, want_f=False)
+        assert max_rel(to_np(g2).astype(np.complex128), g) <= (1e-14 if prec == "f64" else 1e-6)
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
