@@ -279,6 +279,24 @@ int nfft3_plaquette_crossings(int prec, const void *psi, int R1, int R2, int R3,
                               unsigned long long *count, void *stream);
 
 /*
+ * One refinement step of the vortex-tube evaluation (Sec. 4.3, sftubeeval3):
+ * of the M points x (device, M x 3 doubles) with values psi (device, M
+ * complex; double2 for prec 64, float2 for prec 32), keep those with
+ * rho = |psi|^2 <= rhobar and write, for the r-th kept point xi (in input
+ * order), the 27 points xi + (a h1/3, b h2/3, c h3/3), a, b, c in {-1, 0, 1}
+ * (c fastest) to out[27 r .. 27 r + 26] (device, cap x 3 doubles; h: host
+ * array of the current step sizes).  *kept (host) receives the number of kept
+ * points; the call synchronises the stream to read it.  Returns
+ * NFFT3_ERR_TOO_LARGE if 27 * kept > cap (then only the first cap points are
+ * written).  workspace: device memory of nfft3_tube_workspace_bytes(M)
+ * bytes.  Deterministic (a scan, no atomics).
+ */
+size_t nfft3_tube_workspace_bytes(int64_t M);
+int nfft3_tube_refine(int prec, const double *x, const void *psi, int64_t M, double rhobar, const double *h,
+                      double *out, int64_t cap, int64_t *kept, void *workspace, size_t ws_bytes,
+                      void *stream);
+
+/*
  * Kernels of the core-proposal CNN (no counterpart in the paper: a learned
  * proposal stage in front of the NFFT + Newton refinement).  All pointers
  * are device pointers; activations and weights are BF16 (bit pattern

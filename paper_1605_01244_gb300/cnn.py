@@ -236,7 +236,7 @@ def refine_cells(c: torch.Tensor, cells: torch.Tensor, box: Box, precision: str 
     """Core points found inside the given coarse cells: psi on each cell's
     (r+1)^3 fine sub-lattice (aligned with the judge's lattice), the plaquette
     test, Newton.  Returns converged points (K, 3).  With a plan whose
-    gradient grids were precomputed for c, no FFT runs here."""
+    grid was precomputed for c, no FFT runs here."""
     K = cells.shape[0]
     if K == 0:
         return torch.zeros((0, 3), dtype=torch.float64, device=c.device)
@@ -245,7 +245,7 @@ def refine_cells(c: torch.Tensor, cells: torch.Tensor, box: Box, precision: str 
     if plan is None:
         plan = judge.make_plan(c, K * n1 ** 3, precision)
     if not precomputed:
-        plan.precompute(c, with_grad=True)
+        plan.precompute(c)
     per = max(1, plan.capacity // n1 ** 3)    # cells per batch that fit the plan
     loc = torch.arange(n1, device=c.device, dtype=torch.float64) * box.h_fine
     g1, g2, g3 = torch.meshgrid(loc, loc, loc, indexing="ij")

@@ -136,14 +136,14 @@ def evaluate(model, snap, box, tau, rho_bar, plan, precision="f64"):
     c = snap["c"]
 
     def learned():
-        plan.precompute(c, with_grad=True)
+        plan.precompute(c)
         feat = cnn.coarse_features(c, box, precision, plan=plan, precomputed=True)
         prob, _ = model.predict(feat[None])
         cells = cnn.proposals(prob[0], tau)
         return cells, cnn.refine_cells(c, cells, box, precision, plan=plan, precomputed=True)
 
     def rho_path():
-        plan.precompute(c, with_grad=True)
+        plan.precompute(c)
         feat = cnn.coarse_features(c, box, precision, plan=plan, precomputed=True)
         cells = cnn.rho_proposals(feat, rho_bar)
         return cells, cnn.refine_cells(c, cells, box, precision, plan=plan, precomputed=True)

@@ -219,6 +219,8 @@ cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R 
 cudaError_t launch_chunks(PointsBuild &pb, cudaStream_t st);
 
 size_t scan_tmp_ints(int64_t n);
+// Exclusive scan of n ints on the stream; tmp must hold scan_tmp_ints(n) ints.
+cudaError_t exclusive_scan(const int *in, int *out, int64_t n, int *tmp, cudaStream_t st);
 int scan_launches(int64_t n);   // kernels exclusive_scan enqueues for n entries
 
 }  // namespace gbnfft

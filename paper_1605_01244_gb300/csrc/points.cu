@@ -158,25 +158,6 @@ __global__ void scan_add_kernel(int *__restrict__ out, int64_t n, const int *__r
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Exclusive scan of n ints; tmp must hold scan_tmp_ints(n) ints.
-cudaError_t exclusive_scan(const int *in, int *out, int64_t n, int *tmp, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    const int64_t nb = ceil_div(n, kScanChunk);
-    if (nb == 1) {
-        scan_chunk_kernel<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
-        return cudaGetLastError();
-    }
-    int *bsum = tmp;
-    int *boff = tmp + nb;
-    scan_chunk_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, bsum);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = exclusive_scan(bsum, boff, nb, tmp + 2 * nb, st);
-    if (e != cudaSuccess) return e;
-    scan_add_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(out, n, boff);
-    return cudaGetLastError();
-}
-
 __global__ void chunk_count_kernel(PointsBuild pb) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= pb.ntile;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -207,6 +188,25 @@ int point_blocks(int64_t M) {
 }
 
 }  // namespace
+
+// Exclusive scan of n ints; tmp must hold scan_tmp_ints(n) ints.
+cudaError_t exclusive_scan(const int *in, int *out, int64_t n, int *tmp, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t nb = ceil_div(n, kScanChunk);
+    if (nb == 1) {
+        scan_chunk_kernel<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
+        return cudaGetLastError();
+    }
+    int *bsum = tmp;
+    int *boff = tmp + nb;
+    scan_chunk_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, bsum);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = exclusive_scan(bsum, boff, nb, tmp + 2 * nb, st);
+    if (e != cudaSuccess) return e;
+    scan_add_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(out, n, boff);
+    return cudaGetLastError();
+}
 
 size_t scan_tmp_ints(int64_t n) {
     size_t tot = 0;

@@ -89,11 +89,11 @@ def dense_cores(c: torch.Tensor, R, lo, hi, precision: str = "f64", merge_radius
     """Core points: crossings refined by Newton, de-duplicated.  Returns (points, crossings).
 
     One plan serves the lattice evaluation and the Newton iterations; the
-    series is transformed once (value and gradient grids)."""
+    series is transformed once (one grid: Newton differentiates the window)."""
     R = tuple(int(r) for r in R)
     if plan is None:
         plan = make_plan(c, R[0] * R[1] * R[2], precision)
-    plan.precompute(c, with_grad=True)
+    plan.precompute(c)
     cr = dense_crossings(c, R, lo, hi, precision, plan=plan, precomputed=True)
     if cr.points.shape[0] == 0:
         return cr.points, cr

@@ -36,12 +36,17 @@ def _p(t):
 
 
 def locate(plan: Plan, c: torch.Tensor, seeds: torch.Tensor, tol: float | None = None,
-           max_iter: int = 30, max_step: float | None = None, precomputed: bool = False) -> NewtonResult:
+           max_iter: int = 30, max_step: float | None = None, precomputed: bool = False,
+           gradient: str = "window") -> NewtonResult:
     """Newton from ``seeds`` (M x 3 float64 CUDA tensor; the plan's capacity must be >= M).
 
-    The series is deconvolved and transformed once (``precompute`` with the
-    gradient grids; skipped when ``precomputed``), then every iteration is a
-    set_points + stored gather of psi and grad psi + the step kernel.
+    The series is deconvolved and transformed once (``precompute``; skipped
+    when ``precomputed``), then every iteration is a set_points + stored
+    gather of psi and grad psi + the step kernel.  gradient="window" takes the
+    Jacobian from the derivative of the window (one stored grid); "series"
+    from the i k-weighted series (four stored grids, ``precompute`` with
+    with_grad).  The converged points are zeros of psi itself, so the
+    Jacobian's approximation error only affects the iteration count.
     tol: |psi| below which a point is converged (default 1e-10 for FP64 plans,
     1e-5 for mixed).  max_step: largest accepted step (default two coarse
     cells, 2 / max N_d).
@@ -53,8 +58,10 @@ def locate(plan: Plan, c: torch.Tensor, seeds: torch.Tensor, tol: float | None =
     M = seeds.shape[0]
     if plan.M != M:
         plan.set_num_points(M)
+    if gradient not in ("window", "series"):
+        raise ValueError("gradient must be 'window' or 'series'")
     if not precomputed:
-        plan.precompute(c, with_grad=True)
+        plan.precompute(c, with_grad=gradient == "series")
     x = seeds.detach().to(torch.float64).clone().contiguous()
     status = torch.zeros(M, dtype=torch.int32, device=x.device)
     resid = torch.full((M,), float("inf"), dtype=torch.float64, device=x.device)
@@ -62,7 +69,7 @@ def locate(plan: Plan, c: torch.Tensor, seeds: torch.Tensor, tol: float | None =
     it = 0
     for it in range(1, max_iter + 1):
         plan.set_points(x)
-        f, g = plan.eval_grad_stored()
+        f, g = plan.eval_grad_window_stored() if gradient == "window" else plan.eval_grad_stored()
         _lib.call("nfft3_newton_step", prec, M, _p(x), _p(f), _p(g), _p(status), _p(resid),
                   float(tol), float(max_step), ctypes.c_void_p(plan.stream.cuda_stream))
         if not bool((status == ACTIVE).any()):

@@ -75,8 +75,9 @@ def test_oracle_newton_lands_on_the_analytic_lines():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("gradient", ["window", "series"])
 @pytest.mark.parametrize("prec,tol,dist", [("f64", 1e-10, 1e-9), ("f32", 1e-5, 1e-5)])
-def test_cuda_newton_finds_the_cores(prec, tol, dist):
+def test_cuda_newton_finds_the_cores(prec, tol, dist, gradient):
     from paper_1605_01244_gb300 import Plan
     from paper_1605_01244_gb300.newton import CONVERGED, dedupe, locate
     N = 64
@@ -84,7 +85,8 @@ def test_cuda_newton_finds_the_cores(prec, tol, dist):
     seeds = seeds_near_lines(4096, 0.004, seed=71)
     plan = Plan((N, N, N), len(seeds), m=0, eps=1e-12 if prec == "f64" else 1e-6, precision=prec)
     cd = torch.complex128 if prec == "f64" else torch.complex64
-    res = locate(plan, torch.from_numpy(c).to(cd).cuda(), torch.from_numpy(seeds).cuda(), tol=tol)
+    res = locate(plan, torch.from_numpy(c).to(cd).cuda(), torch.from_numpy(seeds).cuda(), tol=tol,
+                 gradient=gradient)
     x = res.x.cpu().numpy()
     st = res.status.cpu().numpy()
     ok = st == CONVERGED
@@ -111,10 +113,11 @@ def test_cuda_newton_matches_oracle_iteration():
     c = wl.gpe_coeffs((N, N, N), L, A)
     seeds = seeds_near_lines(24, 0.003, seed=72)
     plan = Plan((N, N, N), len(seeds), m=7, precision="f64")
-    res = locate(plan, torch.from_numpy(c).cuda(), torch.from_numpy(seeds).cuda(), tol=1e-10,
-                 max_step=2.0 / N)
     xo, so = oracle_newton(c, seeds, 1e-10, 30, 2.0 / N)
-    st = res.status.cpu().numpy()
-    both = (st == 1) & (so == 1)
-    assert both.mean() >= 0.9
-    assert np.max(np.abs(res.x.cpu().numpy()[both] - xo[both])) <= 1e-9
+    for gradient in ("series", "window"):
+        res = locate(plan, torch.from_numpy(c).cuda(), torch.from_numpy(seeds).cuda(), tol=1e-10,
+                     max_step=2.0 / N, gradient=gradient)
+        st = res.status.cpu().numpy()
+        both = (st == 1) & (so == 1)
+        assert both.mean() >= 0.9, gradient
+        assert np.max(np.abs(res.x.cpu().numpy()[both] - xo[both])) <= 1e-9, gradient
