@@ -279,6 +279,24 @@ int nfft3_plaquette_crossings(int prec, const void *psi, int R1, int R2, int R3,
                               unsigned long long *count, void *stream);
 
 /*
+ * Evaluation on a rectilinear grid (the paper's igridftn / ndcovlt, Sec. 2.1):
+ *   f[(i1 M2 + i2) M3 + i3] = sum_k c_k exp(+2 pi i (k1 y1[i1] + k2 y2[i2] + k3 y3[i3]))
+ * for the grid y1 x y2 x y3 (device arrays of M1, M2, M3 torus coordinates),
+ * computed exactly (no window approximation) as three dense complex
+ * contractions, one dimension at a time (cuBLAS Z/CGEMM).  c as in eval,
+ * f: M1 M2 M3 complex (device, overwritten).  workspace: device memory of
+ * nfft3_grid_eval_workspace_bytes bytes (the three exponential matrices and
+ * two partial contractions: M1 N1 + M2 N2 + M3 N3 + N1 N2 M3 + N1 M2 M3
+ * complex).  Asynchronous on the stream.  N1 N2 and M2 M3 must stay below
+ * 2^31 (NFFT3_ERR_TOO_LARGE).
+ */
+size_t nfft3_grid_eval_workspace_bytes(int prec, int N1, int N2, int N3, int M1, int M2, int M3);
+int nfft3d_grid_eval(const double *c, int N1, int N2, int N3, const double *y1, int M1, const double *y2, int M2,
+                     const double *y3, int M3, double *f, void *workspace, size_t ws_bytes, void *stream);
+int nfft3f_grid_eval(const float *c, int N1, int N2, int N3, const double *y1, int M1, const double *y2, int M2,
+                     const double *y3, int M3, float *f, void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * One refinement step of the vortex-tube evaluation (Sec. 4.3, sftubeeval3):
  * of the M points x (device, M x 3 doubles) with values psi (device, M
  * complex; double2 for prec 64, float2 for prec 32), keep those with

@@ -76,6 +76,9 @@ SIGNATURES = {
                       ctypes.c_float, _I, _P]),
     "nfft3_lattice_points": (_I, [_P, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "nfft3_tube_workspace_bytes": (ctypes.c_size_t, [_I64]),
+    "nfft3_grid_eval_workspace_bytes": (ctypes.c_size_t, [_I, _I, _I, _I, _I, _I, _I]),
+    "nfft3d_grid_eval": (_I, [_P, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _P, ctypes.c_size_t, _P]),
+    "nfft3f_grid_eval": (_I, [_P, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _P, ctypes.c_size_t, _P]),
     "nfft3_tube_refine": (_I, [_I, _P, _P, _I64, _D, ctypes.POINTER(_D), _P, _I64, ctypes.POINTER(_I64), _P,
                                ctypes.c_size_t, _P]),
     "nfft3_plaquette_crossings": (_I, [_I, _P, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), _P,

@@ -67,11 +67,27 @@ def make_plan(c: torch.Tensor, capacity: int, precision: str = "f64", eps: float
     return Plan(c.shape, capacity, m=0, eps=eps, precision=precision)
 
 
+def lattice_axes(R, lo, hi, device="cuda"):
+    """The three coordinate axes of ``lattice(R, lo, hi)`` (same values)."""
+    R = tuple(int(r) for r in R)
+    h = [(float(b) - float(a)) / max(r - 1, 1) for a, b, r in zip(lo, hi, R)]
+    return [float(lo[d]) + torch.arange(R[d], dtype=torch.float64, device=device) * h[d] for d in range(3)]
+
+
 def dense_crossings(c: torch.Tensor, R, lo, hi, precision: str = "f64", plan: Plan | None = None,
-                    precomputed: bool = False) -> Crossings:
-    """Evaluate the series c on the lattice and run the plaquette test."""
+                    precomputed: bool = False, method: str = "nfft") -> Crossings:
+    """Evaluate the series c on the lattice and run the plaquette test.
+    method="nfft": the NFFT at the lattice points; "grid": the exact
+    rectilinear-grid evaluation (three dense contractions, ``grid.grid_eval``)."""
     R = tuple(int(r) for r in R)
     M = R[0] * R[1] * R[2]
+    if method == "grid":
+        from .grid import grid_eval
+        cc = c if precision == "f64" else c.to(torch.complex64)
+        psi = grid_eval(cc, *lattice_axes(R, lo, hi, c.device)).reshape(-1)
+        return crossings_from_samples(psi, R, lo, hi)
+    if method != "nfft":
+        raise ValueError("method must be 'nfft' or 'grid'")
     if plan is None:
         plan = make_plan(c, M, precision)
     plan.set_num_points(M)
