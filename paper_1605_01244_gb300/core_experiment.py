@@ -10,7 +10,10 @@ For each held-out snapshot, three ways to find the cores are compared:
 * dense: the judge on the whole fine lattice (ground truth);
 * learned: CoreCNN proposals, refined only in the proposed cells;
 * rho: the no-network baseline, cells whose corner |psi|^2 is below a level
-  fixed on the training snapshots (the paper's rho <= rhobar tube test).
+  fixed on the training snapshots (the paper's rho <= rhobar tube test);
+* tube: the paper's own pipeline (Sec. 4.3, sftubeeval3): two refinements
+  of the coarse lattice inside rho <= rhobar, rhobar/9 (step h/3, h/9), the
+  points with rho <= rhobar/81 seeding Newton (``tube``).
 The report gives recall against the dense cores (a dense core point is
 recovered when a found point lies within 2 fine spacings), the number of
 refined cells, and CUDA-timed wall time of each path.
@@ -27,7 +30,7 @@ import time
 import numpy as np
 import torch
 
-from . import cnn, judge, workloads
+from . import cnn, judge, newton, tube, workloads
 
 
 # Offset of the lattices from the native grid nodes, in fine spacings per
@@ -128,6 +131,35 @@ def choose_rho(snaps, box, target_recall=1.0):
     return 2.0
 
 
+def tube_cores(c, box, rho_bar, plan, precision="f64"):
+    """Core points by the vortex-tube refinement: rho levels in units of the
+    snapshot's mean |psi|^2 on the coarse lattice (the features' scale):
+    rhobar, rhobar / 9 for the two refinements (rho ~ r^2 near a core and each
+    refinement divides the step by 3), then Newton from the final points with
+    rho <= rhobar / 81.  Returns (points, number of tube points, seeds)."""
+    R = (box.Dn,) * 3
+    plan.precompute(c)
+    x0 = judge.lattice(R, box.lo, box.hi, c.device)
+    psi0 = tube.evaluate_points(plan, x0)
+    s2 = float(torch.mean(psi0.abs() ** 2).item())
+    levels = [rho_bar * s2, rho_bar * s2 / 9.0]
+    x, rho = tube.tube_eval(c, levels, R, box.lo, box.hi, precision, plan=plan)
+    sel = rho <= rho_bar * s2 / 81.0
+    seeds, srho = x[sel], rho[sel]
+    n_tube = int(x.shape[0])
+    if seeds.shape[0] == 0:
+        return seeds, n_tube, 0
+    cap = min(plan.capacity, 32768)           # the lowest-density seeds if there are more
+    if seeds.shape[0] > cap:
+        seeds = seeds[torch.topk(srho, cap, largest=False).indices]
+    seeds = seeds.contiguous()
+    res = newton.locate(plan, c, seeds, precomputed=True)
+    conv = res.status == newton.CONVERGED
+    pts = res.x[conv]
+    keep = newton.dedupe(pts, res.status[conv], 0.5 * box.h_fine)
+    return pts[keep], n_tube, int(seeds.shape[0])
+
+
 def evaluate(model, snap, box, tau, rho_bar, plan, precision="f64"):
     """Both proposal paths from the coefficients: coarse features, proposals,
     one series transform (value + gradient grids), refinement in the proposed
@@ -148,13 +180,16 @@ def evaluate(model, snap, box, tau, rho_bar, plan, precision="f64"):
         cells = cnn.rho_proposals(feat, rho_bar)
         return cells, cnn.refine_cells(c, cells, box, precision, plan=plan, precomputed=True)
 
+    learned()                                   # warm-up: first-call set-up is not timed
     (cells_l, found_l), t_l = timed(learned)
     (cells_r, found_r), t_r = timed(rho_path)
+    (found_t, n_tube, n_seeds), t_t = timed(lambda: tube_cores(c, box, rho_bar, plan, precision))
     truth = snap["cores"]
     return {
         "a": snap["a"], "dense_points": int(truth.shape[0]), "t_dense_s": snap["t_dense"],
         "learned": {"cells": int(cells_l.shape[0]), "recall": judge.recall(found_l, truth, radius), "t_s": t_l},
         "rho": {"cells": int(cells_r.shape[0]), "recall": judge.recall(found_r, truth, radius), "t_s": t_r},
+        "tube": {"points": n_tube, "seeds": n_seeds, "recall": judge.recall(found_t, truth, radius), "t_s": t_t},
         "total_cells": (box.Dn - 1) ** 3,
     }
 

@@ -17,11 +17,15 @@
 // With ng = 4 the same passes also produce the gradient grids 2 pi i k_d g.
 #include "internal.cuh"
 
+#ifndef GBNFFT_F32_LINE_ELEMS
+#define GBNFFT_F32_LINE_ELEMS 4096   // FP32 passes: 512-thread blocks (2048 measured slower)
+#endif
+
 namespace gbnfft {
 namespace {
 
-constexpr int kLineThreads = 512;   // threads per block
-constexpr int kLineElems = 4096;    // line elements per block (lines x length)
+// Line elements per block (lines x length) are A::kElems; a block has
+// kElems / 8 threads (one radix-8 butterfly each per pass).
 
 // ---- double-float arithmetic (FP64-accurate on the FP32 pipe) ---------------
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -53,6 +57,7 @@ struct ArithDF {
     };
     using S = float4;
     static constexpr int kPadShift = 3;   // 16-byte elements: one pad per 8
+    static constexpr int kElems = 4096;   // 512 threads
     static __device__ __forceinline__ C ld(const S &s) { return C{s.x, s.y, s.z, s.w}; }
     static __device__ __forceinline__ S st(const C &c) { return make_float4(c.rh, c.rl, c.ih, c.il); }
     static __device__ __forceinline__ C zero() { return C{0.f, 0.f, 0.f, 0.f}; }
@@ -111,6 +116,7 @@ struct ArithF32 {
     };
     using S = float2;
     static constexpr int kPadShift = 4;   // 8-byte elements: one pad per 16
+    static constexpr int kElems = GBNFFT_F32_LINE_ELEMS;
     static __device__ __forceinline__ C ld(const S &s) { return C{s.x, s.y}; }
     static __device__ __forceinline__ S st(const C &c) { return make_float2(c.r, c.i); }
     static __device__ __forceinline__ C zero() { return C{0.f, 0.f}; }
@@ -316,13 +322,13 @@ FastDiv make_fastdiv(unsigned d) {
 // Pass 1: rows along l3 for the in-band (k1, k2); input c deconvolved.
 // A[q][i1 N2 + i2][l3].
 template <class A, typename R, int LOGL>
-__global__ void __launch_bounds__(kLineThreads) fused_rows_kernel(
+__global__ void __launch_bounds__(A::kElems / 8) fused_rows_kernel(
     const typename Cplx<R>::T *__restrict__ c, const R *__restrict__ D1, const R *__restrict__ D2,
     const R *__restrict__ D3, const typename A::S *__restrict__ tw3, typename A::S *__restrict__ out,
     FusedArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using S = typename A::S;
-    constexpr int L = 1 << LOGL, LPB = kLineElems / L;
+    constexpr int L = 1 << LOGL, LPB = A::kElems / L;
     constexpr int LS = L + (L >> A::kPadShift) + 1;
     S *sm = reinterpret_cast<S *>(smem_raw);
     S *tws = sm + LPB * LS;
@@ -357,13 +363,13 @@ __global__ void __launch_bounds__(kLineThreads) fused_rows_kernel(
 // Pass 2: lines along l2 for each (k1, l3).  in A[q][i1 N2 + i2][l3],
 // out B[q][i1][l2][l3].  A block takes LPB consecutive l3 of one i1.
 template <class A, int LOGL>
-__global__ void __launch_bounds__(kLineThreads) fused_cols_kernel(const typename A::S *__restrict__ in,
+__global__ void __launch_bounds__(A::kElems / 8) fused_cols_kernel(const typename A::S *__restrict__ in,
                                                                   const typename A::S *__restrict__ tw2,
                                                                   typename A::S *__restrict__ out,
                                                                   FusedArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using S = typename A::S;
-    constexpr int L = 1 << LOGL, LPB = kLineElems / L;
+    constexpr int L = 1 << LOGL, LPB = A::kElems / L;
     constexpr int LS = L + (L >> A::kPadShift) + 1;
     S *sm = reinterpret_cast<S *>(smem_raw);
     S *tws = sm + LPB * LS;
@@ -393,13 +399,13 @@ __global__ void __launch_bounds__(kLineThreads) fused_cols_kernel(const typename
 // Pass 3: lines along l1 for each (l2, l3); in B[q][i1][l2][l3]; out the
 // padded grid P[q][p1][p2][p3], p = l + shift + t n in [0, n + 2m).
 template <class A, int LOGL>
-__global__ void __launch_bounds__(kLineThreads) fused_out_kernel(const typename A::S *__restrict__ in,
+__global__ void __launch_bounds__(A::kElems / 8) fused_out_kernel(const typename A::S *__restrict__ in,
                                                                  const typename A::S *__restrict__ tw1,
                                                                  typename A::S *__restrict__ P,
                                                                  FusedArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using S = typename A::S;
-    constexpr int L = 1 << LOGL, LPB = kLineElems / L;
+    constexpr int L = 1 << LOGL, LPB = A::kElems / L;
     constexpr int LS = L + (L >> A::kPadShift) + 1;
     S *sm = reinterpret_cast<S *>(smem_raw);
     S *tws = sm + LPB * LS;
@@ -462,7 +468,7 @@ int ilog2(int v) {
 
 template <class A>
 size_t line_smem(int L) {
-    const int LPB = kLineElems / L;
+    const int LPB = A::kElems / L;
     const int LS = L + (L >> A::kPadShift) + 1;
     return sizeof(typename A::S) * ((size_t)LPB * LS + L);
 }
@@ -474,9 +480,9 @@ cudaError_t launch_rows(const typename Cplx<R>::T *c, const R *D1, const R *D2, 
     cudaError_t e = cudaFuncSetAttribute(fused_rows_kernel<A, R, LOGL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int64_t rows = (int64_t)a.N1 * a.N2, lpb = kLineElems >> LOGL;
+    const int64_t rows = (int64_t)a.N1 * a.N2, lpb = A::kElems >> LOGL;
     dim3 g((unsigned)((rows + lpb - 1) / lpb), (unsigned)a.ng);
-    fused_rows_kernel<A, R, LOGL><<<g, kLineThreads, sm, st>>>(c, D1, D2, D3, tw, out, a);
+    fused_rows_kernel<A, R, LOGL><<<g, A::kElems / 8, sm, st>>>(c, D1, D2, D3, tw, out, a);
     return cudaGetLastError();
 }
 
@@ -487,9 +493,9 @@ cudaError_t launch_cols(const typename A::S *in, const typename A::S *tw, typena
     cudaError_t e =
         cudaFuncSetAttribute(fused_cols_kernel<A, LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int lpb = kLineElems >> LOGL;
+    const int lpb = A::kElems >> LOGL;
     dim3 g((unsigned)(a.N1 * ((a.n3 + lpb - 1) / lpb)), (unsigned)a.ng);
-    fused_cols_kernel<A, LOGL><<<g, kLineThreads, sm, st>>>(in, tw, out, a);
+    fused_cols_kernel<A, LOGL><<<g, A::kElems / 8, sm, st>>>(in, tw, out, a);
     return cudaGetLastError();
 }
 
@@ -500,9 +506,9 @@ cudaError_t launch_out(const typename A::S *in, const typename A::S *tw, typenam
     cudaError_t e =
         cudaFuncSetAttribute(fused_out_kernel<A, LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int lpb = kLineElems >> LOGL;
+    const int lpb = A::kElems >> LOGL;
     dim3 g((unsigned)(a.n2 * ((a.n3 + lpb - 1) / lpb)), (unsigned)a.ng);
-    fused_out_kernel<A, LOGL><<<g, kLineThreads, sm, st>>>(in, tw, P, a);
+    fused_out_kernel<A, LOGL><<<g, A::kElems / 8, sm, st>>>(in, tw, P, a);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,8 @@
 //
 // Two arithmetic variants: FP32 (mixed family) and double-float on the FP32
 // pipe (FP64 family; see gather_df.cu for the arithmetic).
+#include <cstdlib>
+
 #include "col_common.cuh"
 
 namespace gbnfft {
@@ -116,6 +118,78 @@ __global__ void __launch_bounds__(256) gather_col_f32_kernel(const float2 *__res
             for (int d = 0; d < 3; ++d)
                 grad[3 * (int64_t)key.w + d] = make_float2(T[(d + 1) % NG][0], T[(d + 1) % NG][1]);
         }
+    }
+}
+
+// Same sum for grids whose three dimensions share one window table (equal
+// N_d and n_d, e.g. cubes), value only: the lane's tap polynomial (D + 1
+// floats) lives in registers for the whole kernel, and each warp walks
+// 32/GS consecutive sorted points per iteration (grid-stride, warp-uniform),
+// so no shared-memory table read is repeated per point.
+template <int MM>
+__global__ void __launch_bounds__(256) gather_col_f32_cube_kernel(const float2 *__restrict__ G, Grid3 pg,
+                                                                  PointsView<float> pts,
+                                                                  const __grid_constant__ Poly<float, MM> P,
+                                                                  float2 *__restrict__ f) {
+    constexpr int W = 2 * MM + 1;
+    constexpr int GS = GroupSize<W>::value;
+    constexpr int PPW = 32 / GS;
+    constexpr int D = PolyDeg<float>::value;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (GS - 1);
+    const int gbase = lane & ~(GS - 1);
+    const int tap = sub < W ? sub : 0;
+    float cf[D + 1];
+#pragma unroll
+    for (int k = 0; k <= D; ++k) cf[k] = P.c[0][tap][k];
+    const int64_t s1 = (int64_t)pg.n2 * pg.n3;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t jb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * PPW; jb < pts.M;
+         jb += nwarps * PPW) {
+        const int64_t j = jb + lane / GS;
+        const bool valid = j < pts.M;
+        const int64_t jj = valid ? j : jb;
+        const int4 key = pts.key[jj];
+        float myw[3];
+        {
+            const float s[3] = {pts.s1[jj], pts.s2[jj], pts.s3[jj]};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float t = 2.f * s[d] - 1.f;
+                float v = cf[D];
+#pragma unroll
+                for (int k = D - 1; k >= 0; --k) v = fmaf(v, t, cf[k]);
+                myw[d] = sub < W ? v : 0.f;
+            }
+        }
+        float w2[W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) w2[b] = __shfl_sync(0xffffffffu, myw[1], gbase + b);
+        const float2 *base = G + (int64_t)key.x * s1 + (int64_t)key.y * pg.n3 + key.z + tap;
+        float Tr = 0.f, Ti = 0.f;
+#pragma unroll 1
+        for (int a = 0; a < W; ++a) {
+            float Sr = 0.f, Si = 0.f;
+            const float2 *row = base;
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const float2 v = __ldg(row);
+                Sr = fmaf(w2[b], v.x, Sr);
+                Si = fmaf(w2[b], v.y, Si);
+                row += pg.n3;
+            }
+            const float w1 = __shfl_sync(0xffffffffu, myw[0], gbase + a);
+            Tr = fmaf(w1, Sr, Tr);
+            Ti = fmaf(w1, Si, Ti);
+            base += s1;
+        }
+        float re = myw[2] * Tr, im = myw[2] * Ti;
+#pragma unroll
+        for (int off = GS / 2; off > 0; off >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, off, GS);
+            im += __shfl_xor_sync(0xffffffffu, im, off, GS);
+        }
+        if (valid && sub == 0) f[key.w] = make_float2(re, im);
     }
 }
 
@@ -278,11 +352,29 @@ int pad_blocks(int64_t rows) {
 template <int MM, int NG>
 cudaError_t col_f32_dispatch(const float2 *G, Grid3 g, PointsView<float> pts,
                              const WinTable<float> &w, float2 *f, float2 *grad, cudaStream_t st) {
-    constexpr int GS = GroupSize<2 * MM + 1>::value;
+    constexpr int W = 2 * MM + 1;
+    constexpr int GS = GroupSize<W>::value;
     const int threads = 256;
-    const int64_t blocks = (pts.M * GS + threads - 1) / threads;
-    gather_col_f32_kernel<MM, NG><<<(unsigned)blocks, threads, 0, st>>>(
-        G, g, pts, make_poly<float, MM>(w), f, grad);
+    const int64_t want = (pts.M * GS + threads - 1) / threads;
+    bool shared_table = NG == 1 && !std::getenv("GBNFFT_F32_NO_CUBE");
+    for (int d = 1; d < 3 && shared_table; ++d)
+        for (int a = 0; a < W && shared_table; ++a)
+            for (int k = 0; k <= PolyDeg<float>::value; ++k)
+                if (w.coef[d][a][k] != w.coef[0][a][k]) shared_table = false;
+    if (shared_table) {
+        static int resident = 0;   // blocks per SM x SMs for this instantiation
+        if (resident == 0) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather_col_f32_cube_kernel<MM>, threads, 0);
+            resident = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+        }
+        const int64_t blocks = want < resident ? want : resident;
+        gather_col_f32_cube_kernel<MM><<<(unsigned)blocks, threads, 0, st>>>(G, g, pts, make_poly<float, MM>(w), f);
+        return cudaGetLastError();
+    }
+    gather_col_f32_kernel<MM, NG><<<(unsigned)want, threads, 0, st>>>(G, g, pts, make_poly<float, MM>(w), f, grad);
     return cudaGetLastError();
 }
 

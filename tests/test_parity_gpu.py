@@ -284,6 +284,30 @@ def test_gather_variants_agree(m, monkeypatch):
                 assert rel_l2(g, gc) <= 5e-6, mode
 
 
+@pytest.mark.parametrize("m", [2, 3, 5])
+def test_f32_shared_table_gather(m, monkeypatch):
+    """Cubic grids share one window table across dimensions; the FP32 value
+    gather then keeps the lane's tap polynomial in registers and walks points
+    grid-stride (gather_col_f32_cube_kernel).  It must match the per-point
+    table kernel (GBNFFT_F32_NO_CUBE=1) and the CPU NFFT, including a ragged
+    tail of points (M not a multiple of the points per warp)."""
+    from paper_1605_01244_gb300 import Plan
+    N = (16, 16, 16)
+    c = wl.gaussian_coeffs(N, 1e9, seed=90 + m)
+    x = wl.mixed_points(2003, 0.05, seed=91)
+    fc = nfft_cpu.forward(c, x, (32, 32, 32), m)
+    out = {}
+    for mode in ("cube", "table"):
+        monkeypatch.delenv("GBNFFT_F32_NO_CUBE", raising=False)
+        if mode == "table":
+            monkeypatch.setenv("GBNFFT_F32_NO_CUBE", "1")
+        plan = Plan(N, len(x), m=m, precision="f32")
+        plan.set_points(to_dev(x))
+        out[mode] = to_np(plan.eval(to_dev(c, torch.complex64))).astype(np.complex128)
+        assert rel_l2(out[mode], fc) <= 2e-6, mode
+    assert max_rel(out["cube"], out["table"]) <= 1e-6
+
+
 @pytest.mark.parametrize("N", [(16, 32, 8), (8, 1024, 8), (64, 64, 64)])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_fused_transform_matches_cufft_and_cpu(N, prec, monkeypatch):
