@@ -181,6 +181,17 @@ cudaError_t launch_deconv_gather(const typename Cplx<R>::T *H, Grid3 g, const R 
 
 // ---- launchers implemented in points.cu ------------------------------------
 
+// One reduced point before sorting: stencil origin and tile (key.w), offsets.
+template <typename R> struct alignas(16) PointRec {
+    int4 key;
+    R s[3];
+};
+// scratch bytes set_points needs for capacity M
+inline size_t points_scratch_bytes(int64_t M, int prec) {
+    return (prec == 64 ? sizeof(PointRec<double>) : sizeof(PointRec<float>)) * (size_t)(M + 1) +
+           sizeof(int) * (size_t)(M + 1);
+}
+
 struct PointsBuild {
     int m;
     Grid3 g;
@@ -192,7 +203,7 @@ struct PointsBuild {
     int *rank;              // M
     int *scan_tmp;          // scan partials
     int *status;            // device status word (bit 0: non-finite coordinate)
-    void *scratch;          // unsorted reduced points: M_cap int4 + 3 M_cap reals
+    void *scratch;          // unsorted reduced points: (M_cap + 1) PointRec + M_cap ints (inverse permutation)
     int64_t M_cap;
     // work list of the tile-staged gather: chunks of <= kChunk points of one tile
     int *chunk_count;       // ntile + 1 (chunks per tile; last entry 0)

@@ -482,7 +482,7 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * scan_tmp_ints(pb.ntile + 1)), pb.scan_tmp = (int *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int)), pb.status = (int *)v;
         pb.M_cap = M;
-        if (st == NFFT3_OK) st = dev_alloc(p, &pb.scratch, (sizeof(int4) + 3 * rs) * (M + 1));
+        if (st == NFFT3_OK) st = dev_alloc(p, &pb.scratch, points_scratch_bytes(M, prec));
         pb.chunk_cap = pb.ntile + M / kChunk + 1;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1)), pb.chunk_count = (int *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1)), pb.chunk_start = (int *)v;
@@ -558,7 +558,7 @@ int set_points_impl(nfft3_plan p, const double *x, int prec) {
         e = launch_points<float>(x, p->pb, p->key, (float *)p->s[0], (float *)p->s[1],
                                  (float *)p->s[2], p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
-    p->launches += p->M > 0 ? 2 + scan_launches(p->pb.ntile + 1) : scan_launches(p->pb.ntile + 1);
+    p->launches += p->M > 0 ? 3 + scan_launches(p->pb.ntile + 1) : scan_launches(p->pb.ntile + 1);
     if (launch_chunks(p->pb, p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
     p->launches += 2 + scan_launches(p->pb.ntile + 1);
     rec_mark(p, rec, 1);

@@ -56,12 +56,12 @@ __device__ __forceinline__ int tile_coord(int l0, int m, int n) {
     return c / kTile;
 }
 
-// Pass 1: reduce every point once (FP64), store the result unsorted in the
-// scratch arrays (key with the point's tile in .w, offsets), and count the
+// Pass 1: reduce every point once (FP64), store the result unsorted as one
+// aligned record per point (stencil origin, tile, offsets), and count the
 // points per tile; the returned count is the point's rank within its tile.
 template <typename R>
 __global__ void points_count_kernel(const double *__restrict__ x, PointsBuild pb,
-                                    int4 *__restrict__ key_tmp, R *__restrict__ s_tmp) {
+                                    PointRec<R> *__restrict__ rec) {
     const double alpha = (double)pb.m + 0.5;
     const double nd1 = (double)pb.g.n1, nd2 = (double)pb.g.n2, nd3 = (double)pb.g.n3;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < pb.M;
@@ -74,26 +74,38 @@ __global__ void points_count_kernel(const double *__restrict__ x, PointsBuild pb
         const int t3 = tile_coord(r3.l0, pb.m, pb.g.n3);
         const int64_t t = ((int64_t)t1 * pb.nt2 + t2) * pb.nt3 + t3;
         pb.rank[j] = atomicAdd(&pb.tile_count[t], 1);
-        key_tmp[j] = make_int4(r1.l0, r2.l0, r3.l0, (int)t);
-        s_tmp[3 * j + 0] = (R)r1.s;
-        s_tmp[3 * j + 1] = (R)r2.s;
-        s_tmp[3 * j + 2] = (R)r3.s;
+        PointRec<R> o;
+        o.key = make_int4(r1.l0, r2.l0, r3.l0, (int)t);
+        o.s[0] = (R)r1.s;
+        o.s[1] = (R)r2.s;
+        o.s[2] = (R)r3.s;
+        rec[j] = o;
     }
 }
 
-// Pass 2: move every point to tile_start[tile] + rank.
+// Pass 2a: the inverse permutation, perm[tile_start[tile] + rank] = j (one
+// 4-byte store per point at its sorted position).
 template <typename R>
-__global__ void points_scatter_kernel(PointsBuild pb, const int4 *__restrict__ key_tmp,
-                                      const R *__restrict__ s_tmp, int4 *__restrict__ key,
-                                      R *__restrict__ s1, R *__restrict__ s2, R *__restrict__ s3) {
+__global__ void points_perm_kernel(PointsBuild pb, const PointRec<R> *__restrict__ rec, int *__restrict__ perm) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < pb.M;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int4 k = key_tmp[j];
-        const int64_t pos = (int64_t)pb.tile_start[k.w] + pb.rank[j];
-        key[pos] = make_int4(k.x, k.y, k.z, (int)j);
-        s1[pos] = s_tmp[3 * j + 0];
-        s2[pos] = s_tmp[3 * j + 1];
-        s3[pos] = s_tmp[3 * j + 2];
+         j += (int64_t)gridDim.x * blockDim.x)
+        perm[(int64_t)pb.tile_start[rec[j].key.w] + pb.rank[j]] = (int)j;
+}
+
+// Pass 2b: write the sorted arrays in order: position p takes record perm[p]
+// (one aligned record read per point, all stores contiguous).
+template <typename R>
+__global__ void points_gather_kernel(PointsBuild pb, const PointRec<R> *__restrict__ rec,
+                                     const int *__restrict__ perm, int4 *__restrict__ key, R *__restrict__ s1,
+                                     R *__restrict__ s2, R *__restrict__ s3) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < pb.M;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int j = perm[p];
+        const PointRec<R> r = rec[j];
+        key[p] = make_int4(r.key.x, r.key.y, r.key.z, j);
+        s1[p] = r.s[0];
+        s2[p] = r.s[1];
+        s3[p] = r.s[2];
     }
 }
 
@@ -232,16 +244,18 @@ cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R 
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(pb.status, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    int4 *key_tmp = (int4 *)pb.scratch;
-    R *s_tmp = (R *)((char *)pb.scratch + sizeof(int4) * pb.M_cap);
+    PointRec<R> *rec = (PointRec<R> *)pb.scratch;
+    int *perm = (int *)((char *)pb.scratch + sizeof(PointRec<R>) * (pb.M_cap + 1));
     if (pb.M > 0) {
-        points_count_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(x, pb, key_tmp, s_tmp);
+        points_count_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(x, pb, rec);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     e = exclusive_scan(pb.tile_count, pb.tile_start, pb.ntile + 1, pb.scan_tmp, st);
     if (e != cudaSuccess) return e;
     if (pb.M > 0) {
-        points_scatter_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(pb, key_tmp, s_tmp, key, s1, s2, s3);
+        points_perm_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(pb, rec, perm);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        points_gather_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(pb, rec, perm, key, s1, s2, s3);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
