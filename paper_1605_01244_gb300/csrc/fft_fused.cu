@@ -182,7 +182,7 @@ template <class A> __device__ __forceinline__ int pidx(int i) { return i + (i >>
 // x'[(j / Ns) Ns R + j mod Ns + r Ns], Ns = 2^LOGNS.  In place: all reads, a
 // barrier, all writes.  Sizes are compile-time, so strides and pads fold.
 template <class A, int LOGL, int LOGNS, int LOGR>
-__device__ __forceinline__ void stockham_pass(typename A::S *x, const typename A::S *tw, int u) {
+__device__ __forceinline__ void stockham_pass(typename A::S *x, const typename A::S *tw, int u, int bh) {
     using C = typename A::C;
     constexpr int R = 1 << LOGR, PER = 8 / R;
     constexpr int T = 1 << (LOGL - 3);
@@ -202,9 +202,16 @@ __device__ __forceinline__ void stockham_pass(typename A::S *x, const typename A
                 idx = pidx<A>(j) + r * (NB + (NB >> PS));
             else
                 idx = pidx<A>(j + r * NB);
-            C t = A::ld(x[idx]);
-            if constexpr (LOGNS > 0)
+            C t;
+            if constexpr (LOGNS == 0) {
+                // first pass: only the band l < bh or l >= L - bh holds input;
+                // the rest of the line buffer is never written and reads as zero
+                const int l = j + r * NB;
+                t = (l < bh || l >= (1 << LOGL) - bh) ? A::ld(x[idx]) : A::zero();
+            } else {
+                t = A::ld(x[idx]);
                 if (r > 0) t = A::mul(t, tw[(r * k) << TWS]);
+            }
             v[b * R + r] = t;
         }
     }
@@ -236,14 +243,14 @@ __device__ __forceinline__ void stockham_pass(typename A::S *x, const typename A
 }
 
 template <class A, int LOGL, int LOGNS>
-__device__ __forceinline__ void stockham_from(typename A::S *x, const typename A::S *tw, int u) {
+__device__ __forceinline__ void stockham_from(typename A::S *x, const typename A::S *tw, int u, int bh) {
     if constexpr (LOGL - LOGNS >= 3) {
-        stockham_pass<A, LOGL, LOGNS, 3>(x, tw, u);
-        stockham_from<A, LOGL, LOGNS + 3>(x, tw, u);
+        stockham_pass<A, LOGL, LOGNS, 3>(x, tw, u, bh);
+        stockham_from<A, LOGL, LOGNS + 3>(x, tw, u, bh);
     } else if constexpr (LOGL - LOGNS == 2) {
-        stockham_pass<A, LOGL, LOGNS, 2>(x, tw, u);
+        stockham_pass<A, LOGL, LOGNS, 2>(x, tw, u, bh);
     } else if constexpr (LOGL - LOGNS == 1) {
-        stockham_pass<A, LOGL, LOGNS, 1>(x, tw, u);
+        stockham_pass<A, LOGL, LOGNS, 1>(x, tw, u, bh);
     }
 }
 
@@ -251,10 +258,11 @@ __device__ __forceinline__ void stockham_from(typename A::S *x, const typename A
 // L = 2^LOGL starts at sm + line * LS, T = L/8 threads per line, radix-8
 // passes then one radix-4 or radix-2 pass for the remaining factor.
 template <class A, int LOGL>
-__device__ __forceinline__ void line_dft(typename A::S *sm, const typename A::S *__restrict__ tw, int LS) {
+__device__ __forceinline__ void line_dft(typename A::S *sm, const typename A::S *__restrict__ tw, int LS,
+                                         int bh) {
     constexpr int T = 1 << (LOGL - 3);
     const int line = threadIdx.x / T, u = threadIdx.x - line * T;
-    stockham_from<A, LOGL, 0>(sm + line * LS, tw, u);
+    stockham_from<A, LOGL, 0>(sm + line * LS, tw, u, bh);
 }
 
 template <class A> __device__ __forceinline__ void load_twiddles(typename A::S *dst, const typename A::S *src, int L) {
@@ -336,9 +344,8 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_rows_kernel(
     const int64_t nrows = (int64_t)a.N1 * a.N2;
     const int64_t row0 = (int64_t)blockIdx.x * LPB;
     load_twiddles<A>(tws, tw3, L);
-    // zero the lines, then place the N3 deconvolved coefficients of each row
-    for (int i = threadIdx.x; i < LPB * LS; i += blockDim.x) sm[i] = A::st(A::zero());
-    __syncthreads();
+    // the N3 deconvolved coefficients of each row, at their band positions
+    // (the first pass reads the rest of the line as zero)
     for (int e = threadIdx.x; e < LPB * a.N3; e += blockDim.x) {
         const int line = (int)a.divN3.div((unsigned)e), i3 = e - line * a.N3;
         const int64_t row = row0 + line;
@@ -351,7 +358,7 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_rows_kernel(
             A::st(series_value(A{}, c[row * a.N3 + i3], d, q, kq));
     }
     __syncthreads();
-    line_dft<A, LOGL>(sm, tws, LS);
+    line_dft<A, LOGL>(sm, tws, LS, a.N3 / 2);
     S *o = out + (int64_t)q * nrows * L;
     for (int e = threadIdx.x; e < LPB * L; e += blockDim.x) {
         const int line = e / L, l3 = e - line * L;
@@ -379,8 +386,6 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_cols_kernel(const typenam
     const int l30 = (blockIdx.x - i1 * nblk3) * LPB;
     const int nl = a.n3 - l30 < LPB ? a.n3 - l30 : LPB;
     load_twiddles<A>(tws, tw2, L);
-    for (int i = threadIdx.x; i < LPB * LS; i += blockDim.x) sm[i] = A::st(A::zero());
-    __syncthreads();
     const S *src = in + ((int64_t)q * a.N1 + i1) * a.N2 * a.n3;
     for (int e = threadIdx.x; e < LPB * a.N2; e += blockDim.x) {
         const int i2 = e / LPB, line = e - i2 * LPB;
@@ -388,7 +393,7 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_cols_kernel(const typenam
             sm[line * LS + pidx<A>(band_pos(i2, a.N2, a.n2))] = src[(int64_t)i2 * a.n3 + l30 + line];
     }
     __syncthreads();
-    line_dft<A, LOGL>(sm, tws, LS);
+    line_dft<A, LOGL>(sm, tws, LS, a.N2 / 2);
     S *dst = out + ((int64_t)q * a.N1 + i1) * a.n2 * a.n3;
     for (int e = threadIdx.x; e < LPB * L; e += blockDim.x) {
         const int l2 = e / LPB, line = e - l2 * LPB;
@@ -415,8 +420,6 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_out_kernel(const typename
     const int l30 = (blockIdx.x - l2 * nblk3) * LPB;
     const int nl = a.n3 - l30 < LPB ? a.n3 - l30 : LPB;
     load_twiddles<A>(tws, tw1, L);
-    for (int i = threadIdx.x; i < LPB * LS; i += blockDim.x) sm[i] = A::st(A::zero());
-    __syncthreads();
     const S *src = in + (int64_t)q * a.N1 * a.n2 * a.n3 + (int64_t)l2 * a.n3 + l30;
     for (int e = threadIdx.x; e < LPB * a.N1; e += blockDim.x) {
         const int i1 = e / LPB, line = e - i1 * LPB;
@@ -425,7 +428,7 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_out_kernel(const typename
                 src[(int64_t)i1 * a.n2 * a.n3 + line];
     }
     __syncthreads();
-    line_dft<A, LOGL>(sm, tws, LS);
+    line_dft<A, LOGL>(sm, tws, LS, a.N1 / 2);
     const int m2 = 2 * a.m;
     const int pn2 = a.n2 + m2, pn3 = a.n3 + m2;
     const int64_t plane = (int64_t)pn2 * pn3;
