@@ -198,8 +198,15 @@ struct PointsBuild {
     int nt1, nt2, nt3;      // tiles per dimension
     int64_t ntile;
     int64_t M;
-    int *tile_count;        // ntile + 1 (last entry stays 0)
-    int *tile_start;        // ntile + 1
+    // sort keys: tile x nsub + the stencil centre's (x, y) cell inside the
+    // tile (nsub = 64, mixed family), so points reading the same grid rows are
+    // neighbours in the sorted order; nsub = 1 (tile only) for the FP64 family
+    // or when ntile x 64 would be too large
+    int nsub;
+    int64_t nkey;           // ntile * nsub
+    int *key_count;         // nkey + 1 (last entry stays 0)
+    int *key_start;         // nkey + 1 (exclusive scan)
+    int *tile_start;        // ntile + 1: key_start[t * nsub]
     int *rank;              // M
     int *scan_tmp;          // scan partials
     int *status;            // device status word (bit 0: non-finite coordinate)

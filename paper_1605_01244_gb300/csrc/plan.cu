@@ -319,7 +319,8 @@ void release(nfft3_plan p) {
     void *k = p->key;
     dev_free(k);
     void *v;
-    v = p->pb.tile_count; dev_free(v);
+    v = p->pb.key_count; dev_free(v);
+    v = p->pb.key_start; dev_free(v);
     v = p->pb.tile_start; dev_free(v);
     v = p->pb.rank; dev_free(v);
     v = p->pb.scan_tmp; dev_free(v);
@@ -475,11 +476,16 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         pb.ntile = (int64_t)pb.nt1 * pb.nt2 * pb.nt3;
         pb.M = M;
         void *v;
-        st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1));
-        pb.tile_count = (int *)v;
+        // the finer key pays off where the gather is bound by L1 row reads (the
+        // mixed family); the double-float gather is ALU-bound and keeps tile order
+        pb.nsub = prec == 32 && pb.ntile * kTile * kTile <= ((int64_t)1 << 27) ? kTile * kTile : 1;
+        pb.nkey = pb.ntile * pb.nsub;
+        st = dev_alloc(p, &v, sizeof(int) * (pb.nkey + 1));
+        pb.key_count = (int *)v;
+        if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.nkey + 1)), pb.key_start = (int *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1)), pb.tile_start = (int *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (M + 1)), pb.rank = (int *)v;
-        if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * scan_tmp_ints(pb.ntile + 1)), pb.scan_tmp = (int *)v;
+        if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * scan_tmp_ints(pb.nkey + 1)), pb.scan_tmp = (int *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int)), pb.status = (int *)v;
         pb.M_cap = M;
         if (st == NFFT3_OK) st = dev_alloc(p, &pb.scratch, points_scratch_bytes(M, prec));
@@ -558,7 +564,7 @@ int set_points_impl(nfft3_plan p, const double *x, int prec) {
         e = launch_points<float>(x, p->pb, p->key, (float *)p->s[0], (float *)p->s[1],
                                  (float *)p->s[2], p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
-    p->launches += p->M > 0 ? 3 + scan_launches(p->pb.ntile + 1) : scan_launches(p->pb.ntile + 1);
+    p->launches += (p->M > 0 ? 4 : 1) + scan_launches(p->pb.nkey + 1);
     if (launch_chunks(p->pb, p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
     p->launches += 2 + scan_launches(p->pb.ntile + 1);
     rec_mark(p, rec, 1);

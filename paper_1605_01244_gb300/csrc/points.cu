@@ -49,11 +49,11 @@ __device__ __forceinline__ Reduced reduce_coord(double x, int n, double nd, doub
     return r;
 }
 
-// tile of a stencil: the tile holding its centre node l0 + m (mod n)
-__device__ __forceinline__ int tile_coord(int l0, int m, int n) {
+// centre node l0 + m (mod n) of a stencil; its tile is centre / kTile
+__device__ __forceinline__ int centre_node(int l0, int m, int n) {
     int c = l0 + m;
     while (c >= n) c -= n;
-    return c / kTile;
+    return c;
 }
 
 // Pass 1: reduce every point once (FP64), store the result unsorted as one
@@ -69,13 +69,15 @@ __global__ void points_count_kernel(const double *__restrict__ x, PointsBuild pb
         const Reduced r1 = reduce_coord(x[3 * j + 0], pb.g.n1, nd1, alpha, pb.status);
         const Reduced r2 = reduce_coord(x[3 * j + 1], pb.g.n2, nd2, alpha, pb.status);
         const Reduced r3 = reduce_coord(x[3 * j + 2], pb.g.n3, nd3, alpha, pb.status);
-        const int t1 = tile_coord(r1.l0, pb.m, pb.g.n1);
-        const int t2 = tile_coord(r2.l0, pb.m, pb.g.n2);
-        const int t3 = tile_coord(r3.l0, pb.m, pb.g.n3);
-        const int64_t t = ((int64_t)t1 * pb.nt2 + t2) * pb.nt3 + t3;
-        pb.rank[j] = atomicAdd(&pb.tile_count[t], 1);
+        const int c1 = centre_node(r1.l0, pb.m, pb.g.n1);
+        const int c2 = centre_node(r2.l0, pb.m, pb.g.n2);
+        const int c3 = centre_node(r3.l0, pb.m, pb.g.n3);
+        const int64_t t = ((int64_t)(c1 / kTile) * pb.nt2 + c2 / kTile) * pb.nt3 + c3 / kTile;
+        const int sub = pb.nsub == 1 ? 0 : (c1 % kTile) * kTile + c2 % kTile;
+        const int64_t k = t * pb.nsub + sub;
+        pb.rank[j] = atomicAdd(&pb.key_count[k], 1);
         PointRec<R> o;
-        o.key = make_int4(r1.l0, r2.l0, r3.l0, (int)t);
+        o.key = make_int4(r1.l0, r2.l0, r3.l0, (int)k);
         o.s[0] = (R)r1.s;
         o.s[1] = (R)r2.s;
         o.s[2] = (R)r3.s;
@@ -89,7 +91,7 @@ template <typename R>
 __global__ void points_perm_kernel(PointsBuild pb, const PointRec<R> *__restrict__ rec, int *__restrict__ perm) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < pb.M;
          j += (int64_t)gridDim.x * blockDim.x)
-        perm[(int64_t)pb.tile_start[rec[j].key.w] + pb.rank[j]] = (int)j;
+        perm[(int64_t)pb.key_start[rec[j].key.w] + pb.rank[j]] = (int)j;
 }
 
 // Pass 2b: write the sorted arrays in order: position p takes record perm[p]
@@ -107,6 +109,12 @@ __global__ void points_gather_kernel(PointsBuild pb, const PointRec<R> *__restri
         s2[p] = r.s[1];
         s3[p] = r.s[2];
     }
+}
+
+__global__ void tile_start_kernel(PointsBuild pb) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= pb.ntile;
+         t += (int64_t)gridDim.x * blockDim.x)
+        pb.tile_start[t] = pb.key_start[t * pb.nsub];
 }
 
 // ---- exclusive scan (three phases, recursive over block sums) -------------
@@ -239,8 +247,8 @@ int scan_launches(int64_t n) {
 template <typename R>
 cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R *s2, R *s3,
                           cudaStream_t st) {
-    // tile_count has ntile + 1 entries; the extra zero makes tile_start[ntile] = M.
-    cudaError_t e = cudaMemsetAsync(pb.tile_count, 0, sizeof(int) * (pb.ntile + 1), st);
+    // key_count has nkey + 1 entries; the extra zero makes key_start[nkey] = M.
+    cudaError_t e = cudaMemsetAsync(pb.key_count, 0, sizeof(int) * (pb.nkey + 1), st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(pb.status, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -250,8 +258,10 @@ cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R 
         points_count_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(x, pb, rec);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    e = exclusive_scan(pb.tile_count, pb.tile_start, pb.ntile + 1, pb.scan_tmp, st);
+    e = exclusive_scan(pb.key_count, pb.key_start, pb.nkey + 1, pb.scan_tmp, st);
     if (e != cudaSuccess) return e;
+    tile_start_kernel<<<point_blocks(pb.ntile + 1), 256, 0, st>>>(pb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (pb.M > 0) {
         points_perm_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(pb, rec, perm);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
