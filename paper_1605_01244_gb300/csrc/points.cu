@@ -16,6 +16,29 @@ struct Reduced {
     double s;
 };
 
+// The value of an integral double v with |v| < 2^31, from its bits (no FP64
+// conversion instruction).
+__device__ __forceinline__ int int_of_integral(double v) {
+    const long long b = __double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;   // |v| = 1.f * 2^e, or v = +-0
+    if (e < 0) return 0;
+    const unsigned long long mant = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int mag = (int)(mant >> (52 - (e < 30 ? e : 30)));
+    return b < 0 ? -mag : mag;
+}
+
+// Offset s in [0, 1) as the family's real type: FP64 unchanged; FP32 by
+// truncating the significand from the bits (at most one unit in the last
+// place below round-to-nearest, no FP64 conversion instruction).
+template <typename R> __device__ __forceinline__ R offset_as(double s);
+template <> __device__ __forceinline__ double offset_as<double>(double s) { return s; }
+template <> __device__ __forceinline__ float offset_as<float>(double s) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+    const int e = (int)(b >> 52) - 1023;   // s >= 0
+    if (e < -126) return 0.f;
+    return __int_as_float(((e + 127) << 23) | (int)((b >> 29) & 0x7FFFFF));
+}
+
 // nd = (double)n and alpha = m + 1/2 are passed in (hoisted by the caller);
 // the finiteness and range tests work on the bits, so the FP64 pipe (the
 // bound of this kernel on GB300) only does the arithmetic of the reduction.
@@ -42,7 +65,7 @@ __device__ __forceinline__ Reduced reduce_coord(double x, int n, double nd, doub
     if (__double_as_longlong(r.s) >= 0x3FF0000000000000ll) r.s = 0.0;
     // xw lies in [-1/2, 1/2], so u in [0, n] and l0 in [-m, n - m]: one
     // add wraps it unless n < m (small grids loop a few times)
-    int li = __double2int_rn(l0);
+    int li = int_of_integral(l0);
     while (li < 0) li += n;
     while (li >= n) li -= n;
     r.l0 = li;
@@ -78,9 +101,9 @@ __global__ void points_count_kernel(const double *__restrict__ x, PointsBuild pb
         pb.rank[j] = atomicAdd(&pb.key_count[k], 1);
         PointRec<R> o;
         o.key = make_int4(r1.l0, r2.l0, r3.l0, (int)k);
-        o.s[0] = (R)r1.s;
-        o.s[1] = (R)r2.s;
-        o.s[2] = (R)r3.s;
+        o.s[0] = offset_as<R>(r1.s);
+        o.s[1] = offset_as<R>(r2.s);
+        o.s[2] = offset_as<R>(r3.s);
         rec[j] = o;
     }
 }
