@@ -279,6 +279,25 @@ int nfft3_plaquette_crossings(int prec, const void *psi, int R1, int R2, int R3,
                               unsigned long long *count, void *stream);
 
 /*
+ * One- and two-dimensional NFFT (the paper's infft and infft2, Appendix B),
+ * FP64, one call:  f_j = sum_k c_k exp(+2 pi i k.x_j), k_d in [-N_d/2, N_d/2),
+ * with the 3D path's window (Kaiser-Bessel, half-width m + 1/2 grid cells,
+ * sigma = n_d / N_d, n_d the smallest even 7-smooth integer >= sigma N_d):
+ * deconvolve + zero-pad, cuFFT inverse transform, window sum.
+ *   dim: 1 or 2;  N: host array of dim sizes (even, >= 2);  m in 1..8;
+ *   sigma in [1.25, 8] (<= 0: 2);  x: device, M x dim doubles (any finite
+ *   values; periodic);  c: device, N1 (x N2) complex doubles, centred order,
+ *   row-major;  f: device, M complex doubles (overwritten).
+ *   workspace: device memory of nfft_lowdim_workspace_bytes bytes.
+ * Synchronises the stream (the non-finite-coordinate check is read back:
+ * NFFT3_ERR_POINTS).  Returns NFFT3_ERR_ARG for invalid sizes (0 bytes from
+ * the workspace query).
+ */
+size_t nfft_lowdim_workspace_bytes(int dim, const int *N, int m, double sigma);
+int nfft_lowdim_eval(int dim, const int *N, int64_t M, int m, double sigma, const double *x, const double *c,
+                     double *f, void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * Evaluation on a rectilinear grid (the paper's igridftn / ndcovlt, Sec. 2.1):
  *   f[(i1 M2 + i2) M3 + i3] = sum_k c_k exp(+2 pi i (k1 y1[i1] + k2 y2[i2] + k3 y3[i3]))
  * for the grid y1 x y2 x y3 (device arrays of M1, M2, M3 torus coordinates),

@@ -204,3 +204,55 @@ def adjoint(f, x, N, n, m: int):
     Hk = np.fft.fftn(H)  # unnormalised e^{-} transform
     D = dec[0][:, None, None] * dec[1][None, :, None] * dec[2][None, None, :]
     return Hk[np.ix_(ks[0] % n[0], ks[1] % n[1], ks[2] % n[2])] * D
+
+
+# ---- one- and two-dimensional series (the paper's infft / infft2) ----------
+
+def direct_lowdim(c, x):
+    """Direct sum f_j = sum_k c_k exp(2 pi i k.x_j) for a 1D or 2D c, with
+    the phase k.x reduced in extended precision (np.longdouble) before the
+    exponential."""
+    c = np.asarray(c, dtype=np.complex128)
+    dim = c.ndim
+    x = np.asarray(x, dtype=np.float64).reshape(-1, dim)
+    tabs = []
+    for d in range(dim):
+        k = (np.arange(c.shape[d]) - c.shape[d] // 2).astype(np.longdouble)
+        ph = x[:, d].astype(np.longdouble)[:, None] * k[None, :]
+        r = (ph - np.rint(ph)).astype(np.float64)
+        tabs.append(np.exp(2j * np.pi * r))
+    if dim == 1:
+        return tabs[0] @ c
+    return np.einsum("ja,ab,jb->j", tabs[0], c, tabs[1])
+
+
+def forward_lowdim(c, x, n, m: int):
+    """The NFFT approximation (steps 1-3 of ``forward``) in 1 or 2 dimensions."""
+    c = np.asarray(c, dtype=np.complex128)
+    dim = c.ndim
+    N = c.shape
+    n = tuple(int(v) for v in n)[:dim]
+    x = np.asarray(x, dtype=np.float64).reshape(-1, dim)
+    ks = [np.arange(Nd) - Nd // 2 for Nd in N]
+    bs = [kb_b(nd, Nd) for nd, Nd in zip(n, N)]
+    dec = [((-1.0) ** np.abs(k)) / kb_Phi(k, nd, m, b) for k, nd, b in zip(ks, n, bs)]
+    G = np.zeros(n, dtype=np.complex128)
+    D = dec[0] if dim == 1 else dec[0][:, None] * dec[1][None, :]
+    G[np.ix_(*[k % nd for k, nd in zip(ks, n)])] = c * D
+    g = np.fft.ifftn(G) * np.prod(n)
+    xw = x - np.floor(x + 0.5)
+    al = m + 0.5
+    a = np.arange(2 * m + 1)
+    idx, ws = [], []
+    for d in range(dim):
+        u = n[d] * (xw[:, d] + 0.5)
+        l0 = np.ceil(u - al)
+        idx.append(((l0[:, None] + a[None, :]).astype(np.int64)) % n[d])
+        ws.append(kb_phi(u[:, None] - (l0[:, None] + a[None, :]), m, bs[d]))
+    if dim == 1:
+        return np.sum(g[idx[0]] * ws[0], axis=1)
+    f = np.zeros(x.shape[0], dtype=np.complex128)
+    for p in range(2 * m + 1):
+        f += ws[0][:, p] * np.sum(g[idx[0][:, p:p + 1], idx[1]] * ws[1], axis=1)
+    return f
+

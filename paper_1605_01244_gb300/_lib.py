@@ -77,6 +77,8 @@ SIGNATURES = {
     "nfft3_lattice_points": (_I, [_P, _I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "nfft3_tube_workspace_bytes": (ctypes.c_size_t, [_I64]),
     "nfft3_grid_eval_workspace_bytes": (ctypes.c_size_t, [_I, _I, _I, _I, _I, _I, _I]),
+    "nfft_lowdim_workspace_bytes": (ctypes.c_size_t, [_I, _P, _I, _D]),
+    "nfft_lowdim_eval": (_I, [_I, _P, _I64, _I, _D, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "nfft3d_grid_eval": (_I, [_P, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _P, ctypes.c_size_t, _P]),
     "nfft3f_grid_eval": (_I, [_P, _I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _P, ctypes.c_size_t, _P]),
     "nfft3_tube_refine": (_I, [_I, _P, _P, _I64, _D, ctypes.POINTER(_D), _P, _I64, ctypes.POINTER(_I64), _P,
