@@ -332,6 +332,11 @@ void release(nfft3_plan p) {
     v = p->x_dev; dev_free(v);
     dev_free(p->c_dev);
     dev_free(p->f_dev);
+    if (p->aux_stream) {
+        cudaEventDestroy(p->aux_ev[0]);
+        cudaEventDestroy(p->aux_ev[1]);
+        cudaStreamDestroy(p->aux_stream);
+    }
     if (p->fft1) cufftDestroy(p->fft1);
     if (p->have_fft4) cufftDestroy(p->fft4);
     if (p->fft2d) cufftDestroy(p->fft2d);
@@ -954,10 +959,21 @@ template <typename R> int eval_host_impl(nfft3_plan p, const double *x_host, con
     int st = NFFT3_OK;
     if (!p->x_dev) {
         void *v = nullptr;
-        st = dev_alloc(p, &v, sizeof(double) * 3 * (p->M + 1));
+        st = dev_alloc(p, &v, sizeof(double) * 3 * (p->M_cap + 1));
         p->x_dev = (double *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &p->c_dev, 2 * sizeof(R) * NN);
-        if (st == NFFT3_OK) st = dev_alloc(p, &p->f_dev, 2 * sizeof(R) * (p->M + 1));
+        if (st == NFFT3_OK) st = dev_alloc(p, &p->f_dev, 2 * sizeof(R) * (p->M_cap + 1));
+        if (st == NFFT3_OK && !p->aux_stream) {
+            if (cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking) != cudaSuccess) {
+                p->aux_stream = nullptr;
+                st = NFFT3_ERR_CUDA;
+            } else if (cudaEventCreateWithFlags(&p->aux_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&p->aux_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+                cudaStreamDestroy(p->aux_stream);
+                p->aux_stream = nullptr;
+                st = NFFT3_ERR_CUDA;
+            }
+        }
         if (st != NFFT3_OK) {
             void *x = p->x_dev;
             dev_free(x);
@@ -967,15 +983,24 @@ template <typename R> int eval_host_impl(nfft3_plan p, const double *x_host, con
             return st;
         }
     }
+    // c on the auxiliary stream (after all earlier work of the plan's stream),
+    // x and set_points on the plan's stream; eval waits for c
+    if (cudaEventRecord(p->aux_ev[0], p->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(p->aux_stream, p->aux_ev[0], 0) != cudaSuccess ||
+        cudaMemcpyAsync(p->c_dev, c_host, 2 * sizeof(R) * NN, cudaMemcpyHostToDevice, p->aux_stream) !=
+            cudaSuccess ||
+        cudaEventRecord(p->aux_ev[1], p->aux_stream) != cudaSuccess)
+        return NFFT3_ERR_CUDA;
     if (p->M > 0 &&
         cudaMemcpyAsync(p->x_dev, x_host, sizeof(double) * 3 * p->M, cudaMemcpyHostToDevice,
                         p->stream) != cudaSuccess)
         return NFFT3_ERR_CUDA;
-    if (cudaMemcpyAsync(p->c_dev, c_host, 2 * sizeof(R) * NN, cudaMemcpyHostToDevice, p->stream) !=
-        cudaSuccess)
-        return NFFT3_ERR_CUDA;
     st = set_points_impl(p, p->x_dev, prec);
-    if (st != NFFT3_OK) return st;
+    if (st != NFFT3_OK) {
+        cudaStreamSynchronize(p->aux_stream);
+        return st;
+    }
+    if (cudaStreamWaitEvent(p->stream, p->aux_ev[1], 0) != cudaSuccess) return NFFT3_ERR_CUDA;
     st = eval_impl<R>(p, (const R *)p->c_dev, (R *)p->f_dev);
     if (st < 0) return st;
     if (p->M > 0 &&

@@ -56,10 +56,13 @@ struct nfft3_plan_s {
     int4 *key;
     void *s[3];
     gbnfft::PointsBuild pb;
-    // host-buffer staging (allocated on first _host call)
+    // host-buffer staging (allocated on first _host call); the coefficient
+    // copy runs on aux_stream, overlapping the copy of x and set_points
     double *x_dev;
     void *c_dev;
     void *f_dev;
+    cudaStream_t aux_stream;
+    cudaEvent_t aux_ev[2];
     // stage timing (CUDA events on the plan's stream), enabled by nfft3_timing_enable
     int timing;
     int nrec;
