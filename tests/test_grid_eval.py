@@ -71,3 +71,19 @@ def test_empty_and_box_lattice_against_nfft():
         pa = a.points.cpu().numpy()
         pb = b.points.cpu().numpy()
         assert np.array_equal(np.sort(pa, axis=0), np.sort(pb, axis=0))
+
+
+def test_two_dimensional_grid_as_unit_third_dimension():
+    """The paper's igridft2 (a 2D series on a rectilinear grid): the same
+    contractions with N3 = M3 = 1 (y3 = 0) against the 2D direct sum."""
+    from oracle import nfft_cpu
+    from paper_1605_01244_gb300.grid import grid_eval
+    g = wl.rng(55)
+    c2 = g.standard_normal((12, 10)) + 1j * g.standard_normal((12, 10))
+    y1 = np.sort(g.uniform(-0.5, 0.5, 9))
+    y2 = np.sort(g.uniform(-0.5, 0.5, 13))
+    f = grid_eval(torch.from_numpy(c2[:, :, None]).cuda(), torch.from_numpy(y1).cuda(), torch.from_numpy(y2).cuda(),
+                  torch.zeros(1, dtype=torch.float64, device="cuda")).cpu().numpy()[:, :, 0]
+    pts = np.stack(np.meshgrid(y1, y2, indexing="ij"), -1).reshape(-1, 2)
+    ref = nfft_cpu.direct_lowdim(c2, pts).reshape(9, 13)
+    assert np.max(np.abs(f - ref)) <= 1e-13 * np.max(np.abs(ref))

@@ -205,6 +205,16 @@ def test_host_path_matches_device_path(prec):
     plan.set_points(xh.cuda())
     fdev = plan.eval(ch.cuda()).cpu()
     assert torch.equal(fh, fdev)
+    # staging is sized for the capacity: a smaller first call, then the full count
+    plan2 = Plan(c.shape, len(x), m=5, precision=prec)
+    plan2.set_num_points(100)
+    f_small = torch.empty(100, dtype=CD[prec])
+    plan2.eval_host(xh[:100].contiguous(), ch, f_small)
+    assert torch.equal(f_small, fdev[:100]) or max_rel(f_small.numpy(), fdev[:100].numpy()) <= 1e-15
+    plan2.set_num_points(len(x))
+    f_full = torch.empty(len(x), dtype=CD[prec])
+    plan2.eval_host(xh, ch, f_full)
+    assert torch.equal(f_full, fdev)
 
 
 @pytest.mark.parametrize("prec,m,tol", [("f64", 6, 1e-12), ("f32", 3, 1e-6)])
