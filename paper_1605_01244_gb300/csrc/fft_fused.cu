@@ -18,7 +18,7 @@
 #include "internal.cuh"
 
 #ifndef GBNFFT_F32_LINE_ELEMS
-#define GBNFFT_F32_LINE_ELEMS 4096   // FP32 passes: 512-thread blocks (2048 measured slower)
+#define GBNFFT_F32_LINE_ELEMS 4096   // FP32 passes: 512-thread blocks (2048 and 8192 measured slower)
 #endif
 
 namespace gbnfft {
