@@ -163,6 +163,13 @@ def alu_peaks():
             "df_tflops": lanes_hz * 2 / DF_MAC_INSTRUCTIONS / 1e12}
 
 
+def workload_config(N: int, M: int) -> dict:
+    """The workload both arms run (the reference arm on a bounded sample)."""
+    return {"workload": "precision sweep: N=%d^3 gaussian(40) coefficients, M=%d points (half uniform, "
+                        "half gaussian std 0.02), sigma=2" % (N, M),
+            "N": N, "M_per_gpu": M, "sigma": 2.0, "m_fp64": M_FP64, "m_mixed": M_MIXED}
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_1605_01244_gb300 import build, sharding, workloads as wl
@@ -350,11 +357,10 @@ def run_ours(args, rank, world, local):
         "value": main["value"], "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "precision sweep: N=%d^3 gaussian(40) coefficients, M=%d points (half uniform, "
-                               "half gaussian std 0.02), sigma=2" % (N, M),
-                   "N": N, "M_per_gpu": M, "sigma": 2.0, "m_fp64": M_FP64, "m_mixed": M_MIXED,
-                   "step": "set_points + eval", "l2": "inputs larger than L2 (grid %.2f GB FP64), no flush" % ((2 * N) ** 3 * 16 / 1e9),
-                   "parallelism": "points sharded, no collective" if world > 1 else "single GPU"},
+        "config": dict(workload_config(N, M), **{
+            "step": "set_points + eval",
+            "l2": "inputs larger than L2 (grid %.2f GB FP64), no flush" % ((2 * N) ** 3 * 16 / 1e9),
+            "parallelism": "points sharded, no collective" if world > 1 else "single GPU"}),
         "rel_l2_vs_oracle": main["rel_l2_vs_oracle"],
         "eval_only_mpoints_s": main["eval_only_mpoints_s"],
         "gradient_mpoints_s": main["gradient_mpoints_s"],
@@ -378,7 +384,8 @@ def run_reference(args, rank, world, local):
     from paper_1605_01244_gb300 import workloads as wl
     N = args.n
     c_np = wl.gaussian_coeffs((N, N, N), 40.0, seed=0)
-    x_np = wl.mixed_points(args.points, 0.02, seed=100)
+    from paper_1605_01244_gb300 import sharding
+    x_np = wl.mixed_points(args.points, 0.02, seed=sharding.point_seed(0))
     S = 2048  # points per step: ~2.5 s of direct summation at N = 256^3 on 16 Arm cores
     rng = wl.rng(5)
     times = []
@@ -397,9 +404,9 @@ def run_reference(args, rank, world, local):
         "value": val, "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "precision sweep: N=%d^3 gaussian(40) coefficients, M=%d points (half uniform, "
-                               "half gaussian std 0.02), sigma=2" % (N, args.points), "N": N,
-                   "step": "FP64 direct sum (the oracle) over %d sampled points" % S},
+        "config": dict(workload_config(N, args.points), **{
+            "step": "FP64 direct sum (the oracle) over %d sampled points of the workload" % S,
+            "parallelism": "host cores"}),
         "cpu_baseline": {"value": val, "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
                          "sample": "%d random points of the workload per step" % S},
         "e2e": {"value": val, "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
