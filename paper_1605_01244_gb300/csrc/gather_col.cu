@@ -198,6 +198,95 @@ __global__ void __launch_bounds__(256) gather_col_f32_cube_kernel(const float2 *
 #define GBNFFT_DF_MINB 3   // resident 256-thread blocks per SM the value kernel is compiled for
 #endif
 
+// Value gather with the W^2 taps of each stencil plane spread over all GS
+// lanes of the group ("slots"): lane l owns taps s = l + GS t, (b, c) =
+// (s / W, s mod W), t < NSLOT = ceil(W^2 / GS), instead of one column each.
+// For W = 13 (m = 6) that fills 169 of 176 lane slots (96 %) instead of
+// 13 of 16 columns (81 %); for W = 11 or 17 the gain is larger.  Each slot's
+// weight w2[b] w3[c] is formed once per point; per plane a lane adds its
+// slots' products and the plane weight w1[a] multiplies the lane sum; the
+// group reduces the lane sums at the end.  Double-float throughout.
+template <int MM>
+__global__ void __launch_bounds__(256, GBNFFT_DF_MINB) gather_slot_df_kernel(
+    const float4 *__restrict__ G, Grid3 pg, PointsView<double> pts,
+    const __grid_constant__ typename WeightsFP64<MM>::Table P, double2 *__restrict__ f) {
+    constexpr int W = 2 * MM + 1;
+    constexpr int GS = GroupSize<W>::value;
+    constexpr int NSLOT = (W * W + GS - 1) / GS;
+    __shared__ WeightsFP64<MM> wt;
+    wt.load(P);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (GS - 1);
+    const int gbase = lane & ~(GS - 1);
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / GS;
+    const bool valid = j < pts.M;
+    const int64_t jj = valid ? j : 0;
+    const int4 key = pts.M > 0 ? pts.key[jj] : make_int4(0, 0, 0, 0);
+    const int tap = sub < W ? sub : 0;
+    float wh[3], wl[3];
+    {
+        const double s[3] = {pts.s1[jj], pts.s2[jj], pts.s3[jj]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            wt.eval(d, tap, s[d], wh[d], wl[d]);
+            if (sub >= W) wh[d] = wl[d] = 0.f;
+        }
+    }
+    // slot offsets within a plane and slot weights w2[b] w3[c]
+    int off[NSLOT];
+    float w23h[NSLOT], w23l[NSLOT];
+#pragma unroll
+    for (int t = 0; t < NSLOT; ++t) {
+        const int sidx = sub + GS * t;
+        const bool in = sidx < W * W;
+        const int b = in ? sidx / W : 0, c = in ? sidx - (sidx / W) * W : 0;
+        const float bh = __shfl_sync(0xffffffffu, wh[1], gbase + b);
+        const float bl = __shfl_sync(0xffffffffu, wl[1], gbase + b);
+        const float ch = __shfl_sync(0xffffffffu, wh[2], gbase + c);
+        const float cl = __shfl_sync(0xffffffffu, wl[2], gbase + c);
+        float ph = 0.f, pl = 0.f;
+        df_mac(ph, pl, bh, bl, ch, cl);
+        df_norm(ph, pl);
+        w23h[t] = in ? ph : 0.f;
+        w23l[t] = in ? pl : 0.f;
+        off[t] = b * pg.n3 + c;
+    }
+    const int64_t s1 = (int64_t)pg.n2 * pg.n3;
+    const float4 *base = G + (int64_t)key.x * s1 + (int64_t)key.y * pg.n3 + key.z;
+    float T[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int a = 0; a < W; ++a) {
+        float S[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < NSLOT; ++t) {
+            const float4 v = __ldg(base + off[t]);
+            df_mac(S[0], S[1], v.x, v.y, w23h[t], w23l[t]);
+            df_mac(S[2], S[3], v.z, v.w, w23h[t], w23l[t]);
+        }
+        const float w1h = __shfl_sync(0xffffffffu, wh[0], gbase + a);
+        const float w1l = __shfl_sync(0xffffffffu, wl[0], gbase + a);
+        df_norm(S[0], S[1]);
+        df_norm(S[2], S[3]);
+        df_mac(T[0], T[1], S[0], S[1], w1h, w1l);
+        df_mac(T[2], T[3], S[2], S[3], w1h, w1l);
+        base += s1;
+    }
+    df_norm(T[0], T[1]);
+    df_norm(T[2], T[3]);
+#pragma unroll
+    for (int o = GS / 2; o > 0; o >>= 1) {
+        const float orh = __shfl_xor_sync(0xffffffffu, T[0], o, GS);
+        const float orl = __shfl_xor_sync(0xffffffffu, T[1], o, GS);
+        const float oih = __shfl_xor_sync(0xffffffffu, T[2], o, GS);
+        const float oil = __shfl_xor_sync(0xffffffffu, T[3], o, GS);
+        df_add(T[0], T[1], orh, orl);
+        df_add(T[2], T[3], oih, oil);
+    }
+    if (valid && sub == 0) f[key.w] = make_double2((double)T[0] + (double)T[1], (double)T[2] + (double)T[3]);
+}
+
 template <int MM, int NG, class Wt>
 __global__ void __launch_bounds__(256, NG == 1 ? GBNFFT_DF_MINB : 2) gather_col_df_kernel(const float4 *__restrict__ G, Grid3 pg,
                                                             PointsView<double> pts,
@@ -385,7 +474,9 @@ cudaError_t col_df_dispatch(const float4 *G, Grid3 g, PointsView<double> pts, co
     constexpr int GS = GroupSize<2 * MM + 1>::value;
     const int threads = 256;
     const int64_t blocks = (pts.M * GS + threads - 1) / threads;
-    if (fp64_weights)
+    if (NG == 1 && fp64_weights && !std::getenv("GBNFFT_DF_COLUMNS"))
+        gather_slot_df_kernel<MM><<<(unsigned)blocks, threads, 0, st>>>(G, g, pts, make_poly<double, MM>(w64), f);
+    else if (fp64_weights)
         gather_col_df_kernel<MM, NG, WeightsFP64<MM>><<<(unsigned)blocks, threads, 0, st>>>(
             G, g, pts, make_poly<double, MM>(w64), f, grad);
     else

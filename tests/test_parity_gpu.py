@@ -140,9 +140,10 @@ def test_gradient_against_oracle():
         assert rel_l2(f, fd) <= tol_f, prec
         for d in range(3):
             assert rel_l2(g[:, d], gd[:, d]) <= tol_g, (prec, d)
-        # the value from eval_grad agrees with eval (batched vs single FFT may round differently)
+        # the value from eval_grad agrees with eval (the value gather and the
+        # four-grid gather sum the taps in different orders)
         fe = to_np(plan.eval(to_dev(c, CD[prec]))).astype(np.complex128)
-        assert max_rel(f, fe) <= (1e-14 if prec == "f64" else 1e-6)
+        assert max_rel(f, fe) <= (5e-14 if prec == "f64" else 1e-6)
     # f may be omitted
     plan = Plan(N, len(x), m=6)
     plan.set_points(to_dev(x))
@@ -254,10 +255,11 @@ def test_window_polynomials_accuracy(prec, tol):
 
 @pytest.mark.parametrize("m", [2, 3, 6, 8])
 def test_gather_variants_agree(m, monkeypatch):
-    """Gather variants selected by GBNFFT_GATHER: default (column-parallel
-    groups over the padded grid; double-float on the FP32 pipe for the FP64
-    family, tap weights by FP64 Horner, or by double-float Horner with
-    GBNFFT_DF_WEIGHTS=df), tma (mixed-family values from TMA-staged shared-memory tiles),
+    """Gather variants selected by GBNFFT_GATHER: default (lane groups over the
+    padded grid; for the FP64 family double-float on the FP32 pipe, the value
+    gather spreading each plane's taps over all lanes -- GBNFFT_DF_COLUMNS=1
+    keeps one column per lane -- and tap weights by FP64 Horner, or by
+    double-float Horner with GBNFFT_DF_WEIGHTS=df), tma (mixed-family values from TMA-staged shared-memory tiles),
     thread (one thread per point) and native (FP64 family on the FP64 pipe).  Every variant must match the CPU NFFT, for eval and
     eval_grad: to rounding in FP64, to FP32 accuracy in the mixed family."""
     from paper_1605_01244_gb300 import Plan
@@ -265,14 +267,19 @@ def test_gather_variants_agree(m, monkeypatch):
     c = wl.gaussian_coeffs(N, 1e9, seed=30 + m)
     x = wl.mixed_points(900, 0.03, seed=31)
     ref = None
-    for prec, modes in (("f64", ("default", "df-weights", "thread", "native")), ("f32", ("default", "tma", "thread"))):
+    for prec, modes in (("f64", ("default", "df-columns", "df-weights", "thread", "native")),
+                        ("f32", ("default", "tma", "thread"))):
         for mode in modes:
             monkeypatch.delenv("GBNFFT_DF_WEIGHTS", raising=False)
+            monkeypatch.delenv("GBNFFT_DF_COLUMNS", raising=False)
             if mode == "default":
                 monkeypatch.delenv("GBNFFT_GATHER", raising=False)
             elif mode == "df-weights":
                 monkeypatch.delenv("GBNFFT_GATHER", raising=False)
                 monkeypatch.setenv("GBNFFT_DF_WEIGHTS", "df")
+            elif mode == "df-columns":
+                monkeypatch.delenv("GBNFFT_GATHER", raising=False)
+                monkeypatch.setenv("GBNFFT_DF_COLUMNS", "1")
             else:
                 monkeypatch.setenv("GBNFFT_GATHER", mode)
             plan = Plan(N, len(x), m=m, precision=prec)
@@ -390,7 +397,7 @@ def test_window_derivative_gradient(N, sigma, prec, monkeypatch):
         for d in range(3):
             assert rel_l2(g[:, d], gd[:, d]) <= tol_d, (m, d)
         fe = to_np(plan.eval(cd)).astype(np.complex128)
-        assert max_rel(f, fe) <= (1e-14 if prec == "f64" else 1e-6)
+        assert max_rel(f, fe) <= (5e-14 if prec == "f64" else 1e-6)   # different tap order
         plan.precompute(cd)
         fs, gs = plan.eval_grad_window_stored()
         assert max_rel(to_np(gs).astype(np.complex128), g) <= (1e-14 if prec == "f64" else 1e-6)
