@@ -194,6 +194,9 @@ __global__ void __launch_bounds__(256) gather_col_f32_cube_kernel(const float2 *
 }
 
 // ---- double-float (FP64 family) ----------------------------------------------
+#ifndef GBNFFT_SLOT_MINB
+#define GBNFFT_SLOT_MINB 3   // resident 256-thread blocks per SM the slot kernel is compiled for (2: 38.4 ms vs 31.6)
+#endif
 #ifndef GBNFFT_DF_MINB
 #define GBNFFT_DF_MINB 3   // resident 256-thread blocks per SM the value kernel is compiled for
 #endif
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(256) gather_col_f32_cube_kernel(const float2 *
 // slots' products and the plane weight w1[a] multiplies the lane sum; the
 // group reduces the lane sums at the end.  Double-float throughout.
 template <int MM>
-__global__ void __launch_bounds__(256, GBNFFT_DF_MINB) gather_slot_df_kernel(
+__global__ void __launch_bounds__(256, GBNFFT_SLOT_MINB) gather_slot_df_kernel(
     const float4 *__restrict__ G, Grid3 pg, PointsView<double> pts,
     const __grid_constant__ typename WeightsFP64<MM>::Table P, double2 *__restrict__ f) {
     constexpr int W = 2 * MM + 1;
