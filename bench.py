@@ -145,7 +145,7 @@ def gather_bytes(M: int, n: int, real_bytes: int) -> int:
 # from ncu's dram__bytes_read.sum + dram__bytes_write.sum on the same kernels
 # at N = 128^3, M = 1.25e6 (both units 1/8 of the default), scaled by 8;
 # profiles/gather_col_128cubed_1.25e6pts_full.md has the capture.
-GATHER_TRAFFIC_BYTES = {"gather_col_f32_cube_kernel": 1.51e9}
+GATHER_TRAFFIC_BYTES = {"gather_slot_df_kernel": 3.258e9, "gather_col_f32_cube_kernel": 1.51e9}
 
 # FP32 instructions of one FP64-accurate (double-float) multiply-add: exact
 # product (1 mul + 3 fma), two-sum of the high parts (6 add/sub), 2 adds into
