@@ -90,13 +90,30 @@ int nfft3f_plan(nfft3_plan *out, int N1, int N2, int N3, int64_t M, int m,
 /*
  * Set the M points (device pointer x, M*3 doubles).  Each coordinate is
  * wrapped onto [-1/2, 1/2) (the series is periodic; paper Sec. 2.2.1 uses
- * mod(.,1)), reduced in FP64 to its first stencil node and a fractional
- * offset, and the points are bucketed by grid tile.  Synchronises the
+ * mod(.,1)), reduced with FP64 rounding to its first stencil node and a
+ * fractional offset (nfft3_reduce_coords), and the points are bucketed by grid tile.  Synchronises the
  * plan's stream (it reads back a status word).  NaN/Inf coordinates give
  * NFFT3_ERR_POINTS and leave the plan without points.
  */
 int nfft3d_set_points(nfft3_plan p, const double *x);
 int nfft3f_set_points(nfft3_plan p, const double *x);
+
+/*
+ * The per-coordinate reduction of set_points on its own, for inspection:
+ * for each of the M doubles x[j] (device) and an oversampled size n with
+ * cutoff m (1..8), the first stencil node l0[j] = ceil(u - m - 1/2) wrapped
+ * into [0, n), u = n (x_w + 1/2), x_w = x - floor(x + 1/2), and the offset
+ * s = l0 - (u - m - 1/2) in [0, 1) as the FP64 family stores it (s) and as
+ * the mixed family stores it (s32: the FP64 value's significand truncated to
+ * FP32).  Every step rounds like FP64 round-to-nearest arithmetic; for
+ * n = 2^L (8 <= n <= 2^30) all steps after x_w + 1/2 run on the integer
+ * pipe with the same results.  Any of l0, s, s32 may be NULL.  *status
+ * (device int) is zeroed and gets bit 0 if some x[j] is NaN or infinite
+ * (that coordinate is reduced as 0).  Asynchronous on the stream.
+ * Coordinate wrap: paper Sec. 2.2.1.
+ */
+int nfft3_reduce_coords(int n, int m, const double *x, int64_t M, int *l0, double *s, float *s32,
+                        int *status, void *stream);
 
 /* f = A c  (type-2 NFFT).  c: N1*N2*N3 complex, f: M complex (overwritten). */
 int nfft3d_eval(nfft3_plan p, const double *c, double *f);

@@ -65,6 +65,7 @@ SIGNATURES = {
     "nfft3_choose_m": (_I, [_D, _D]),
     "nfft3_timing_enable": (_I, [_P, _I]),
     "nfft3_timing_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64), ctypes.POINTER(_I64), _I]),
+    "nfft3_reduce_coords": (_I, [_I, _I, _P, _I64, _P, _P, _P, _P, _P]),
     "nfft3_fma_peak": (_I, [_I, _I, _P, ctypes.POINTER(_D)]),
     "nfft3_newton_step": (_I, [_I, _I64, _P, _P, _P, _P, _P, _D, _D, _P]),
     "nfft3_dedupe": (_I, [_I64, _P, _P, _D, _P, _P]),

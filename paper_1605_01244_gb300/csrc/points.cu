@@ -12,19 +12,22 @@ __device__ __forceinline__ int centre_node(int l0, int m, int n) {
     return c;
 }
 
-// Pass 1: reduce every point once (FP64), store the result unsorted as one
-// aligned record per point (stencil origin, tile, offsets), and count the
-// points per tile; the returned count is the point's rank within its tile.
+// Pass 1: reduce every point once (FP64 results, integer pipe for n = 2^L),
+// store the result unsorted as one aligned record per point (stencil origin,
+// tile, offsets), and count the points per tile; the returned count is the
+// point's rank within its tile.
 template <typename R>
 __global__ void points_count_kernel(const double *__restrict__ x, PointsBuild pb,
                                     PointRec<R> *__restrict__ rec) {
     const double alpha = (double)pb.m + 0.5;
     const double nd1 = (double)pb.g.n1, nd2 = (double)pb.g.n2, nd3 = (double)pb.g.n3;
+    const int L1 = log2_if_pow2(pb.g.n1), L2 = log2_if_pow2(pb.g.n2), L3 = log2_if_pow2(pb.g.n3);
+    const int width = 2 * pb.m + 1;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < pb.M;
          j += (int64_t)gridDim.x * blockDim.x) {
-        const Reduced r1 = reduce_coord(x[3 * j + 0], pb.g.n1, nd1, alpha, pb.status);
-        const Reduced r2 = reduce_coord(x[3 * j + 1], pb.g.n2, nd2, alpha, pb.status);
-        const Reduced r3 = reduce_coord(x[3 * j + 2], pb.g.n3, nd3, alpha, pb.status);
+        const Reduced r1 = reduce_coord(x[3 * j + 0], pb.g.n1, nd1, alpha, L1, width, pb.status);
+        const Reduced r2 = reduce_coord(x[3 * j + 1], pb.g.n2, nd2, alpha, L2, width, pb.status);
+        const Reduced r3 = reduce_coord(x[3 * j + 2], pb.g.n3, nd3, alpha, L3, width, pb.status);
         const int c1 = centre_node(r1.l0, pb.m, pb.g.n1);
         const int c2 = centre_node(r2.l0, pb.m, pb.g.n2);
         const int c3 = centre_node(r3.l0, pb.m, pb.g.n3);
@@ -244,3 +247,33 @@ template cudaError_t launch_points<float>(const double *, PointsBuild &, int4 *,
                                           float *, cudaStream_t);
 
 }  // namespace gbnfft
+
+namespace gbnfft {
+namespace {
+
+__global__ void reduce_coords_kernel(const double *__restrict__ x, int64_t M, int n, int m, int *__restrict__ l0,
+                                     double *__restrict__ s, float *__restrict__ s32, int *__restrict__ status) {
+    const double alpha = (double)m + 0.5, nd = (double)n;
+    const int L = log2_if_pow2(n);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x) {
+        const Reduced r = reduce_coord(x[j], n, nd, alpha, L, 2 * m + 1, status);
+        if (l0) l0[j] = r.l0;
+        if (s) s[j] = offset_as<double>(r.s);
+        if (s32) s32[j] = offset_as<float>(r.s);
+    }
+}
+
+}  // namespace
+}  // namespace gbnfft
+
+extern "C" int nfft3_reduce_coords(int n, int m, const double *x, int64_t M, int *l0, double *s, float *s32,
+                                   int *status, void *stream) {
+    using namespace gbnfft;
+    if (n < 2 || m < 1 || m > kMaxM || M < 0 || !status) return NFFT3_ERR_ARG;
+    if (M > 0 && !x) return NFFT3_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return NFFT3_ERR_CUDA;
+    if (M == 0) return NFFT3_OK;
+    reduce_coords_kernel<<<point_blocks(M), 256, 0, st>>>(x, M, n, m, l0, s, s32, status);
+    return cudaGetLastError() == cudaSuccess ? NFFT3_OK : NFFT3_ERR_CUDA;
+}

@@ -189,3 +189,22 @@ class Plan:
 def choose_m(eps: float, sigma: float = 2.0) -> int:
     """Cutoff m the library picks for a target relative error eps."""
     return int(_lib.lib().nfft3_choose_m(float(eps), float(sigma)))
+
+
+def reduce_coords(x: torch.Tensor, n: int, m: int):
+    """set_points' reduction of each coordinate in ``x`` (float64 CUDA
+    tensor, any shape) for an oversampled size n and cutoff m: the first
+    stencil node l0 (int32, in [0, n)), the offset s in [0, 1) as the FP64
+    family stores it (float64) and as the mixed family stores it (float32)."""
+    if x.dtype != torch.float64 or not x.is_cuda:
+        raise TypeError("x must be a float64 CUDA tensor")
+    xf = x.contiguous().reshape(-1)
+    l0 = torch.empty(xf.shape, dtype=torch.int32, device=x.device)
+    s = torch.empty(xf.shape, dtype=torch.float64, device=x.device)
+    s32 = torch.empty(xf.shape, dtype=torch.float32, device=x.device)
+    status = torch.empty(1, dtype=torch.int32, device=x.device)
+    _lib.call("nfft3_reduce_coords", int(n), int(m), _ptr(xf), xf.numel(), _ptr(l0), _ptr(s), _ptr(s32),
+              _ptr(status), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if int(status.item()) & 1:
+        raise _lib.NFFTError("nfft3_reduce_coords", _lib.NFFT3_ERR_POINTS)
+    return l0.reshape(x.shape), s.reshape(x.shape), s32.reshape(x.shape)
