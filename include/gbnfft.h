@@ -106,8 +106,8 @@ int nfft3f_set_points(nfft3_plan p, const double *x);
  * s = l0 - (u - m - 1/2) in [0, 1) as the FP64 family stores it (s) and as
  * the mixed family stores it (s32: the FP64 value's significand truncated to
  * FP32).  Every step rounds like FP64 round-to-nearest arithmetic; for
- * n = 2^L (8 <= n <= 2^30) all steps after x_w + 1/2 run on the integer
- * pipe with the same results.  Any of l0, s, s32 may be NULL.  *status
+ * n = 2^L (8 <= n <= 2^30) the steps after x_w + 1/2 run on the integer
+ * pipe with the same results, except next to x = -1/2.  Any of l0, s, s32 may be NULL.  *status
  * (device int) is zeroed and gets bit 0 if some x[j] is NaN or infinite
  * (that coordinate is reduced as 0).  Asynchronous on the stream.
  * Coordinate wrap: paper Sec. 2.2.1.

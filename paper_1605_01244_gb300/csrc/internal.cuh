@@ -181,7 +181,7 @@ cudaError_t launch_deconv_gather(const typename Cplx<R>::T *H, Grid3 g, const R 
 
 // ---- launchers implemented in points.cu ------------------------------------
 
-// One reduced point before sorting: stencil origin and tile (key.w), offsets.
+// One reduced point before sorting: stencil origin and original index (key.w), offsets.
 template <typename R> struct alignas(16) PointRec {
     int4 key;
     R s[3];
@@ -207,7 +207,7 @@ struct PointsBuild {
     int *key_count;         // nkey + 1 (last entry stays 0)
     int *key_start;         // nkey + 1 (exclusive scan)
     int *tile_start;        // ntile + 1: key_start[t * nsub]
-    int *rank;              // M
+    int2 *key_rank;         // M: (sort key, rank among the points of that key)
     int *scan_tmp;          // scan partials
     int *status;            // device status word (bit 0: non-finite coordinate)
     void *scratch;          // unsorted reduced points: (M_cap + 1) PointRec + M_cap ints (inverse permutation)

@@ -83,13 +83,12 @@ __device__ __forceinline__ double low_weight(double s, int tap, int m, double b)
 
 __global__ void low_gather_kernel(const double2 *__restrict__ G, LowArgs a, const double *__restrict__ x,
                                   int64_t M, double2 *__restrict__ f, int *__restrict__ status) {
-    const double alpha = a.m + 0.5;
     const int W = 2 * a.m + 1;
-    const int L1 = log2_if_pow2(a.n1), L2 = log2_if_pow2(a.n2);
+    const CoordParams cp1 = coord_params(a.n1, a.m), cp2 = coord_params(a.n2, a.m);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x) {
-        const Reduced r1 = reduce_coord(x[(int64_t)a.dim * j], a.n1, (double)a.n1, alpha, L1, W, status);
+        const Reduced r1 = reduce_coord(x[(int64_t)a.dim * j], cp1, status);
         Reduced r2{0, 0.0};
-        if (a.dim == 2) r2 = reduce_coord(x[2 * j + 1], a.n2, (double)a.n2, alpha, L2, W, status);
+        if (a.dim == 2) r2 = reduce_coord(x[2 * j + 1], cp2, status);
         double w2[kMaxTaps];
         if (a.dim == 2)
             for (int q = 0; q < W; ++q) w2[q] = low_weight(r2.s, q, a.m, a.b2);

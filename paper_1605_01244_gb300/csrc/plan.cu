@@ -322,7 +322,7 @@ void release(nfft3_plan p) {
     v = p->pb.key_count; dev_free(v);
     v = p->pb.key_start; dev_free(v);
     v = p->pb.tile_start; dev_free(v);
-    v = p->pb.rank; dev_free(v);
+    v = p->pb.key_rank; dev_free(v);
     v = p->pb.scan_tmp; dev_free(v);
     v = p->pb.status; dev_free(v);
     dev_free(p->pb.scratch);
@@ -480,16 +480,18 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         pb.nt3 = (p->n[2] + kTile - 1) / kTile;
         pb.ntile = (int64_t)pb.nt1 * pb.nt2 * pb.nt3;
         pb.M = M;
-        void *v;
+        void *v = nullptr;
         // the finer key pays off where the gather is bound by L1 row reads (the
         // mixed family); the double-float gather is ALU-bound and keeps tile order
         pb.nsub = prec == 32 && pb.ntile * kTile * kTile <= ((int64_t)1 << 27) ? kTile * kTile : 1;
         pb.nkey = pb.ntile * pb.nsub;
-        st = dev_alloc(p, &v, sizeof(int) * (pb.nkey + 1));
+        // sort keys and their offsets are int (a grid that large would not fit the device anyway)
+        if (pb.nkey >= ((int64_t)1 << 31) - 1) st = NFFT3_ERR_TOO_LARGE;
+        if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.nkey + 1));
         pb.key_count = (int *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.nkey + 1)), pb.key_start = (int *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1)), pb.tile_start = (int *)v;
-        if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (M + 1)), pb.rank = (int *)v;
+        if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int2) * (M + 1)), pb.key_rank = (int2 *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * scan_tmp_ints(pb.nkey + 1)), pb.scan_tmp = (int *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int)), pb.status = (int *)v;
         pb.M_cap = M;

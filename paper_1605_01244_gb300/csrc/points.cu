@@ -5,68 +5,125 @@
 namespace gbnfft {
 namespace {
 
-// centre node l0 + m (mod n) of a stencil; its tile is centre / kTile
+// centre node l0 + m (mod n) of a stencil (l0 in [0, n)); its tile is centre / kTile
 __device__ __forceinline__ int centre_node(int l0, int m, int n) {
     int c = l0 + m;
-    while (c >= n) c -= n;
+    c -= c >= n ? n : 0;
+    if (c >= n) c = wrap_index(c, n);   // n < m only
     return c;
 }
 
+// Points per thread per loop trip in the set_points passes: their loads are
+// issued together, so each thread keeps several HBM requests in flight.
+constexpr int kPtsILP = 4;
+
 // Pass 1: reduce every point once (FP64 results, integer pipe for n = 2^L),
 // store the result unsorted as one aligned record per point (stencil origin,
-// tile, offsets), and count the points per tile; the returned count is the
-// point's rank within its tile.
+// original index, offsets) plus its (key, rank) pair, where rank counts the
+// points of the key before it.
 template <typename R>
-__global__ void points_count_kernel(const double *__restrict__ x, PointsBuild pb,
-                                    PointRec<R> *__restrict__ rec) {
-    const double alpha = (double)pb.m + 0.5;
-    const double nd1 = (double)pb.g.n1, nd2 = (double)pb.g.n2, nd3 = (double)pb.g.n3;
-    const int L1 = log2_if_pow2(pb.g.n1), L2 = log2_if_pow2(pb.g.n2), L3 = log2_if_pow2(pb.g.n3);
-    const int width = 2 * pb.m + 1;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < pb.M;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const Reduced r1 = reduce_coord(x[3 * j + 0], pb.g.n1, nd1, alpha, L1, width, pb.status);
-        const Reduced r2 = reduce_coord(x[3 * j + 1], pb.g.n2, nd2, alpha, L2, width, pb.status);
-        const Reduced r3 = reduce_coord(x[3 * j + 2], pb.g.n3, nd3, alpha, L3, width, pb.status);
-        const int c1 = centre_node(r1.l0, pb.m, pb.g.n1);
-        const int c2 = centre_node(r2.l0, pb.m, pb.g.n2);
-        const int c3 = centre_node(r3.l0, pb.m, pb.g.n3);
-        const int64_t t = ((int64_t)(c1 / kTile) * pb.nt2 + c2 / kTile) * pb.nt3 + c3 / kTile;
-        const int sub = pb.nsub == 1 ? 0 : (c1 % kTile) * kTile + c2 % kTile;
-        const int64_t k = t * pb.nsub + sub;
-        pb.rank[j] = atomicAdd(&pb.key_count[k], 1);
-        PointRec<R> o;
-        o.key = make_int4(r1.l0, r2.l0, r3.l0, (int)k);
-        o.s[0] = offset_as<R>(r1.s);
-        o.s[1] = offset_as<R>(r2.s);
-        o.s[2] = offset_as<R>(r3.s);
-        rec[j] = o;
+__global__ void __launch_bounds__(256) points_count_kernel(const double *__restrict__ x, PointsBuild pb,
+                                                           PointRec<R> *__restrict__ rec) {
+    const CoordParams cp1 = coord_params(pb.g.n1, pb.m), cp2 = coord_params(pb.g.n2, pb.m),
+                      cp3 = coord_params(pb.g.n3, pb.m);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j0 < pb.M; j0 += kPtsILP * stride) {
+        double xs[kPtsILP][3];
+#pragma unroll
+        for (int q = 0; q < kPtsILP; ++q) {
+            const int64_t j = j0 + q * stride;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) xs[q][d] = j < pb.M ? __ldcs(x + 3 * j + d) : 0.0;
+        }
+        // phase 1: reduce, store the records, and issue one atomic per
+        // distinct key in the warp (clustered points share keys) for all
+        // points of the trip before any result is needed
+        int k[kPtsILP], base[kPtsILP];
+        unsigned peers[kPtsILP];
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int q = 0; q < kPtsILP; ++q) {
+            const int64_t j = j0 + q * stride;
+            peers[q] = 0;
+            base[q] = 0;
+            k[q] = 0;
+            if (j >= pb.M) continue;
+            const Reduced r1 = reduce_coord(xs[q][0], cp1, pb.status);
+            const Reduced r2 = reduce_coord(xs[q][1], cp2, pb.status);
+            const Reduced r3 = reduce_coord(xs[q][2], cp3, pb.status);
+            PointRec<R> o;
+            o.key = make_int4(r1.l0, r2.l0, r3.l0, (int)j);
+            o.s[0] = offset_as<R>(r1.s);
+            o.s[1] = offset_as<R>(r2.s);
+            o.s[2] = offset_as<R>(r3.s);
+            rec[j] = o;
+            const int c1 = centre_node(r1.l0, pb.m, pb.g.n1);
+            const int c2 = centre_node(r2.l0, pb.m, pb.g.n2);
+            const int c3 = centre_node(r3.l0, pb.m, pb.g.n3);
+            // nkey = ntile nsub < 2^31 (checked at plan creation)
+            const int t = ((c1 / kTile) * pb.nt2 + c2 / kTile) * pb.nt3 + c3 / kTile;
+            k[q] = pb.nsub == 1 ? t : t * pb.nsub + (c1 % kTile) * kTile + c2 % kTile;
+            peers[q] = __match_any_sync(__activemask(), k[q]);
+            if (lane == __ffs(peers[q]) - 1) base[q] = atomicAdd(&pb.key_count[k[q]], __popc(peers[q]));
+        }
+        // phase 2: each lane's rank is its leader's base plus its place among
+        // the lanes with the same key
+#pragma unroll
+        for (int q = 0; q < kPtsILP; ++q) {
+            const int64_t j = j0 + q * stride;
+            if (j >= pb.M) continue;
+            const int b = __shfl_sync(peers[q], base[q], __ffs(peers[q]) - 1);
+            pb.key_rank[j] = make_int2(k[q], b + __popc(peers[q] & ((1u << lane) - 1u)));
+        }
     }
 }
 
-// Pass 2a: the inverse permutation, perm[tile_start[tile] + rank] = j (one
+// Pass 2a: the inverse permutation, perm[key_start[key] + rank] = j (one
 // 4-byte store per point at its sorted position).
-template <typename R>
-__global__ void points_perm_kernel(PointsBuild pb, const PointRec<R> *__restrict__ rec, int *__restrict__ perm) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < pb.M;
-         j += (int64_t)gridDim.x * blockDim.x)
-        perm[(int64_t)pb.key_start[rec[j].key.w] + pb.rank[j]] = (int)j;
+__global__ void __launch_bounds__(256) points_perm_kernel(PointsBuild pb, int *__restrict__ perm) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j0 < pb.M; j0 += kPtsILP * stride) {
+        int2 kr[kPtsILP];
+#pragma unroll
+        for (int q = 0; q < kPtsILP; ++q) {
+            const int64_t j = j0 + q * stride;
+            kr[q] = j < pb.M ? pb.key_rank[j] : make_int2(0, 0);
+        }
+        int ks[kPtsILP];
+#pragma unroll
+        for (int q = 0; q < kPtsILP; ++q) ks[q] = j0 + q * stride < pb.M ? pb.key_start[kr[q].x] : 0;
+#pragma unroll
+        for (int q = 0; q < kPtsILP; ++q) {
+            const int64_t j = j0 + q * stride;
+            if (j < pb.M) perm[(int64_t)ks[q] + kr[q].y] = (int)j;
+        }
+    }
 }
 
 // Pass 2b: write the sorted arrays in order: position p takes record perm[p]
 // (one aligned record read per point, all stores contiguous).
 template <typename R>
-__global__ void points_gather_kernel(PointsBuild pb, const PointRec<R> *__restrict__ rec,
-                                     const int *__restrict__ perm, int4 *__restrict__ key, R *__restrict__ s1,
-                                     R *__restrict__ s2, R *__restrict__ s3) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < pb.M;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int j = perm[p];
-        const PointRec<R> r = rec[j];
-        key[p] = make_int4(r.key.x, r.key.y, r.key.z, j);
-        s1[p] = r.s[0];
-        s2[p] = r.s[1];
-        s3[p] = r.s[2];
+__global__ void __launch_bounds__(256) points_gather_kernel(PointsBuild pb, const PointRec<R> *__restrict__ rec,
+                                                            const int *__restrict__ perm, int4 *__restrict__ key,
+                                                            R *__restrict__ s1, R *__restrict__ s2,
+                                                            R *__restrict__ s3) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p0 < pb.M; p0 += kPtsILP * stride) {
+        int js[kPtsILP];
+#pragma unroll
+        for (int q = 0; q < kPtsILP; ++q) js[q] = p0 + q * stride < pb.M ? perm[p0 + q * stride] : 0;
+        PointRec<R> r[kPtsILP];
+#pragma unroll
+        for (int q = 0; q < kPtsILP; ++q) r[q] = rec[js[q]];
+#pragma unroll
+        for (int q = 0; q < kPtsILP; ++q) {
+            const int64_t p = p0 + q * stride;
+            if (p >= pb.M) break;
+            key[p] = r[q].key;
+            s1[p] = r[q].s[0];
+            s2[p] = r[q].s[1];
+            s3[p] = r[q].s[2];
+        }
     }
 }
 
@@ -222,7 +279,7 @@ cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R 
     tile_start_kernel<<<point_blocks(pb.ntile + 1), 256, 0, st>>>(pb);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (pb.M > 0) {
-        points_perm_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(pb, rec, perm);
+        points_perm_kernel<<<point_blocks(pb.M), 256, 0, st>>>(pb, perm);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         points_gather_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(pb, rec, perm, key, s1, s2, s3);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -253,10 +310,9 @@ namespace {
 
 __global__ void reduce_coords_kernel(const double *__restrict__ x, int64_t M, int n, int m, int *__restrict__ l0,
                                      double *__restrict__ s, float *__restrict__ s32, int *__restrict__ status) {
-    const double alpha = (double)m + 0.5, nd = (double)n;
-    const int L = log2_if_pow2(n);
+    const CoordParams cp = coord_params(n, m);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x) {
-        const Reduced r = reduce_coord(x[j], n, nd, alpha, L, 2 * m + 1, status);
+        const Reduced r = reduce_coord(x[j], cp, status);
         if (l0) l0[j] = r.l0;
         if (s) s[j] = offset_as<double>(r.s);
         if (s32) s32[j] = offset_as<float>(r.s);

@@ -40,15 +40,41 @@ template <> __device__ __forceinline__ float offset_as<float>(double s) {
     return __int_as_float(((e + 127) << 23) | (int)((b >> 29) & 0x7FFFFF));
 }
 
-// Round-to-nearest-even of a magnitude 0 < a < 2^63 to 53 significant bits
-// (the rounding of an FP64 result whose exact value is the integer a times a
-// power of two).
-__device__ __forceinline__ unsigned long long round53(unsigned long long a) {
-    const int p = 63 - __clzll((long long)a);
-    if (p <= 52) return a;
-    const int d = p - 52;
-    const unsigned long long q = a >> d, rem = a & ((1ull << d) - 1), half = 1ull << (d - 1);
-    return (q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull)) << d;
+// Per-dimension constants of the reduction (hoisted out of the point loops).
+// For n = 2^L the steps after t = x_w + 1/2 can run on fixed-point integers in
+// units of 2^-F grid cells, F = 62 - L: u = n t is U = t 2^62 (exact for
+// t >= 2^-10, whose 53-bit significand then sits at or above bit 0) and
+// alpha is A = (2m + 1) 2^(F - 1).  F = 0 marks n without that path.
+struct CoordParams {
+    int n;
+    double nd, alpha;
+    int F;
+    int Et_min;                  // smallest biased exponent of t the path takes
+    long long A, A_half, mask;   // A, A / 2, 2^F - 1
+};
+
+__device__ __forceinline__ CoordParams coord_params(int n, int m) {
+    CoordParams c;
+    c.n = n;
+    c.nd = (double)n;
+    c.alpha = (double)m + 0.5;
+    c.F = 0;
+    c.Et_min = 0;
+    c.A = c.A_half = c.mask = 0;
+    // 8 <= n <= 2^30 keeps A = (2m + 1) 2^(61 - L) below 2^63
+    if (n >= 8 && n <= (1 << 30) && (n & (n - 1)) == 0) {
+        int L = 0;
+        while ((1 << L) < n) ++L;
+        c.F = 62 - L;
+        // t >= 2^(Et_min - 1023): U is a multiple of 2^(Et - 1013) and so are
+        // V and the offset S < 2^F, which then has at most 53 significant
+        // bits when Et - 1013 >= F - 53
+        c.Et_min = 1013 + (c.F > 53 ? c.F - 53 : 0);
+        c.A = (long long)(2 * m + 1) << (c.F - 1);
+        c.A_half = c.A >> 1;
+        c.mask = (1ll << c.F) - 1;
+    }
+    return c;
 }
 
 // The double S 2^-F for 0 <= S < 2^63 holding at most 53 significant bits.
@@ -60,36 +86,51 @@ __device__ __forceinline__ double fixed_to_double(unsigned long long S, int F) {
                                             (mant & 0xFFFFFFFFFFFFFull)));
 }
 
-// The steps after t = x_w + 1/2 for n = 2^L, on the integer pipe.  With
-// F = 62 - L, every quantity is an integer in units of 2^-F grid cells:
-// u = n t is U = t 2^62 (exact for t >= 2^-10, whose 53-bit significand
-// then sits at or above bit 0), alpha is (2m + 1) 2^(F - 1), and the two
-// FP64 subtractions u - alpha and l0 - v are the exact integer differences
-// rounded to 53 significant bits (ties to even), i.e. the same doubles as the
-// FP64 sequence; ceil is a shift.  Returns false (nothing written) for
-// t < 2^-10, which takes the FP64 sequence.
-__device__ __forceinline__ bool reduce_fixed(double t, int L, int width, long long &l0, double &s) {
+// The fixed-point path for u >= alpha / 2 (all but a sliver next to
+// x = -1/2).  There V = U - A is a multiple of U's lowest significand bit
+// with |V| <= U, so it has at most 53 significant bits: the FP64 difference
+// u - alpha is exactly v = V 2^-F.  Then l0 = ceil(v) is a shift, and
+// l0 - v is S = (-V) mod 2^F, exact too (CoordParams::Et_min).  Returns false
+// (nothing written) for t below that bound or u < alpha / 2, which take the
+// FP64 sequence.
+__device__ __forceinline__ bool reduce_fixed(double t, const CoordParams &c, long long &l0, double &s) {
     const unsigned long long tb = (unsigned long long)__double_as_longlong(t);   // 0 <= t <= 1
     const int Et = (int)(tb >> 52);
-    if (Et < 1013) return false;
-    const int F = 62 - L;
+    if (Et < c.Et_min) return false;
     const long long U = (long long)(((tb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (Et - 1013));
-    long long V = U - ((long long)width << (F - 1));   // |V| < 2^62
-    if (V > 0) V = (long long)round53((unsigned long long)V);
-    else if (V < 0) V = -(long long)round53((unsigned long long)(-V));
-    l0 = (V + ((1ll << F) - 1)) >> F;                               // ceil(v), arithmetic shift
-    const unsigned long long S = (unsigned long long)(l0 * (1ll << F) - V);   // (l0 - v) 2^F in [0, 2^F)
-    s = fixed_to_double(S == 0 ? 0ull : round53(S), F);
+    if (U < c.A_half) return false;
+    const long long V = U - c.A;
+    l0 = (V + c.mask) >> c.F;                                                  // ceil(v), arithmetic shift
+    s = fixed_to_double((unsigned long long)(-V) & (unsigned long long)c.mask, c.F);
     return true;
 }
 
-// nd = (double)n and alpha = m + 1/2 (width = 2m + 1) are passed in (hoisted
-// by the caller); log2n = log2(n) when n is a power of two, else -1.  The
-// finiteness and range tests work on the bits; for n = 2^L only x_w + 1/2
-// runs on the FP64 pipe (the bound of this kernel on GB300), for other n the
-// whole sequence does.
-__device__ __forceinline__ Reduced reduce_coord(double x, int n, double nd, double alpha, int log2n, int width,
-                                                int *status) {
+// The rare paths of reduce_coord, kept out of line: inlined, the compiler
+// turns them into predicated FP64 instructions that every lane issues.
+// Wrap of |x| >= 1/2 onto [-1/2, 1/2].
+__device__ __noinline__ double wrap_coord(double x) { return __dsub_rn(x, floor(__dadd_rn(x, 0.5))); }
+
+// i mod n in [0, n) for any int i (grids smaller than the stencil).
+__device__ __noinline__ int wrap_index(int i, int n) {
+    const int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// The FP64 sequence after t = x_w + 1/2 (any n): l0 (not yet wrapped) and s.
+__device__ __noinline__ Reduced reduce_fp64(double t, double nd, double alpha) {
+    const double u = __dmul_rn(nd, t);
+    const double v = __dsub_rn(u, alpha);
+    const double l0 = ceil(v);
+    Reduced r;
+    r.s = __dsub_rn(l0, v);
+    r.l0 = int_of_integral(l0);
+    return r;
+}
+
+// The finiteness and range tests work on the bits; x_w + 1/2 is the one
+// step always on the FP64 pipe (the bound of this kernel on GB300), the rest
+// runs on integers where CoordParams allows it.
+__device__ __forceinline__ Reduced reduce_coord(double x, const CoordParams &c, int *status) {
     unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     if ((bits & 0x7FF0000000000000ull) == 0x7FF0000000000000ull) {
         atomicOr(status, 1);
@@ -102,35 +143,23 @@ __device__ __forceinline__ Reduced reduce_coord(double x, int n, double nd, doub
     // result they equal.
     const unsigned long long mag = bits & 0x7FFFFFFFFFFFFFFFull;
     const bool in_range = mag < 0x3FE0000000000000ull || bits == 0xBFE0000000000000ull;
-    const double xw = in_range ? x : __dsub_rn(x, floor(__dadd_rn(x, 0.5)));
+    const double xw = in_range ? x : wrap_coord(x);
     const double t = __dadd_rn(xw, 0.5);
     Reduced r;
     long long l0i;
-    if (!(log2n >= 0 && reduce_fixed(t, log2n, width, l0i, r.s))) {
-        const double u = __dmul_rn(nd, t);
-        const double v = __dsub_rn(u, alpha);
-        const double l0 = ceil(v);
-        r.s = __dsub_rn(l0, v);
-        l0i = int_of_integral(l0);
+    if (!(c.F > 0 && reduce_fixed(t, c, l0i, r.s))) {
+        r = reduce_fp64(t, c.nd, c.alpha);
+        l0i = r.l0;
     }
     // s >= 1 cannot happen for finite v; the bit test keeps s in [0, 1) regardless
     if (__double_as_longlong(r.s) >= 0x3FF0000000000000ll) r.s = 0.0;
     // xw lies in [-1/2, 1/2], so u in [0, n] and l0 in [-m, n - m]: one
-    // add wraps it unless n < m (small grids loop a few times)
+    // add wraps it unless n < m
     int li = (int)l0i;
-    while (li < 0) li += n;
-    while (li >= n) li -= n;
+    li += li < 0 ? c.n : 0;
+    if ((unsigned)li >= (unsigned)c.n) li = wrap_index(li, c.n);
     r.l0 = li;
     return r;
-}
-
-// log2(n) for a power of two 8 <= n <= 2^30 (the range in which the
-// fixed-point integers of reduce_fixed stay below 2^63), else -1
-__host__ __device__ __forceinline__ int log2_if_pow2(int n) {
-    if (n < 8 || n > (1 << 30) || (n & (n - 1))) return -1;
-    int L = 0;
-    while ((1 << L) < n) ++L;
-    return L;
 }
 
 }  // namespace

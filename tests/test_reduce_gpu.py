@@ -4,8 +4,8 @@ For every coordinate the library forms, with FP64 round-to-nearest steps,
     x_w = x - floor(x + 1/2),  u = n (x_w + 1/2),  v = u - (m + 1/2),
     l0 = ceil(v),  s = l0 - v,
 and stores l0 mod n with s (FP64 family) or s with its significand cut to
-FP32 (mixed family).  For n = 2^L the library takes the steps after
-x_w + 1/2 on the integer pipe; they must give the same bits as numpy's FP64
+FP32 (mixed family).  For n = 2^L >= 8 the library takes the steps after
+x_w + 1/2 on the integer pipe (except next to x = -1/2); they must give the same bits as numpy's FP64
 arithmetic here, on random, boundary and tie-producing inputs, and the
 stencil origins must be the oracle's.
 """
