@@ -386,18 +386,22 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_cols_kernel(const typenam
     const int l30 = (blockIdx.x - i1 * nblk3) * LPB;
     const int nl = a.n3 - l30 < LPB ? a.n3 - l30 : LPB;
     load_twiddles<A>(tws, tw2, L);
-    const S *src = in + ((int64_t)q * a.N1 + i1) * a.N2 * a.n3;
-    for (int e = threadIdx.x; e < LPB * a.N2; e += blockDim.x) {
-        const int i2 = e / LPB, line = e - i2 * LPB;
-        if (line < nl)
-            sm[line * LS + pidx<A>(band_pos(i2, a.N2, a.n2))] = src[(int64_t)i2 * a.n3 + l30 + line];
+    // each thread keeps one line (l3) and walks i2 / l2 with a constant stride
+    constexpr int STEP = (A::kElems / 8) / LPB;
+    const int line = threadIdx.x & (LPB - 1), r0 = threadIdx.x / LPB;
+    S *sl = sm + line * LS;
+    if (line < nl) {
+        const S *src = in + ((int64_t)q * a.N1 + i1) * a.N2 * a.n3 + l30 + line + (int64_t)r0 * a.n3;
+        const int64_t sstep = (int64_t)STEP * a.n3;
+        for (int i2 = r0; i2 < a.N2; i2 += STEP, src += sstep) sl[pidx<A>(band_pos(i2, a.N2, a.n2))] = *src;
     }
     __syncthreads();
     line_dft<A, LOGL>(sm, tws, LS, a.N2 / 2);
-    S *dst = out + ((int64_t)q * a.N1 + i1) * a.n2 * a.n3;
-    for (int e = threadIdx.x; e < LPB * L; e += blockDim.x) {
-        const int l2 = e / LPB, line = e - l2 * LPB;
-        if (line < nl) dst[(int64_t)l2 * a.n3 + l30 + line] = sm[line * LS + pidx<A>(l2)];
+    if (line < nl) {
+        S *dst = out + ((int64_t)q * a.N1 + i1) * a.n2 * a.n3 + l30 + line + (int64_t)r0 * a.n3;
+        const int64_t dstep = (int64_t)STEP * a.n3;
+#pragma unroll 4
+        for (int l2 = r0; l2 < L; l2 += STEP, dst += dstep) *dst = sl[pidx<A>(l2)];
     }
 }
 
@@ -420,44 +424,47 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_out_kernel(const typename
     const int l30 = (blockIdx.x - l2 * nblk3) * LPB;
     const int nl = a.n3 - l30 < LPB ? a.n3 - l30 : LPB;
     load_twiddles<A>(tws, tw1, L);
-    const S *src = in + (int64_t)q * a.N1 * a.n2 * a.n3 + (int64_t)l2 * a.n3 + l30;
-    for (int e = threadIdx.x; e < LPB * a.N1; e += blockDim.x) {
-        const int i1 = e / LPB, line = e - i1 * LPB;
-        if (line < nl)
-            sm[line * LS + pidx<A>(band_pos(i1, a.N1, a.n1))] =
-                src[(int64_t)i1 * a.n2 * a.n3 + line];
+    // each thread keeps one line (l3) and walks i1 / l1 with a constant stride
+    constexpr int STEP = (A::kElems / 8) / LPB;
+    const int line = threadIdx.x & (LPB - 1), r0 = threadIdx.x / LPB;
+    S *sl = sm + line * LS;
+    if (line < nl) {
+        const int64_t sstep = (int64_t)a.n2 * a.n3;
+        const S *src = in + (int64_t)q * a.N1 * sstep + (int64_t)l2 * a.n3 + l30 + line + r0 * sstep;
+        for (int i1 = r0; i1 < a.N1; i1 += STEP, src += STEP * sstep) sl[pidx<A>(band_pos(i1, a.N1, a.n1))] = *src;
     }
     __syncthreads();
     line_dft<A, LOGL>(sm, tws, LS, a.N1 / 2);
+    if (line >= nl) return;
     const int m2 = 2 * a.m;
     const int pn2 = a.n2 + m2, pn3 = a.n3 + m2;
     const int64_t plane = (int64_t)pn2 * pn3;
-    S *dstq = P + (int64_t)q * (a.n1 + m2) * plane;
     // every l has its primary position p = l + shift in [0, n + 2m) and at most
-    // one ghost copy (2m <= n): p + n if p < 2m, p - n if p >= n
+    // one ghost copy (2m <= n): p + n if p < 2m, p - n if p >= n.  Along l2
+    // and l3 the copies are fixed offsets from the primary element.
     const int p2 = l2 + a.shift, g2 = ghost_of(p2, a.n2, m2);
-    for (int e = threadIdx.x; e < LPB * L; e += blockDim.x) {
-        const int l1 = e / LPB, line = e - l1 * LPB;
-        if (line >= nl) continue;
-        const S v = sm[line * LS + pidx<A>(l1)];
-        const int p1 = l1 + a.shift, g1 = ghost_of(p1, a.n1, m2);
-        const int p3 = l30 + line + a.shift, g3 = ghost_of(p3, a.n3, m2);
-        S *r = dstq + (int64_t)p1 * plane + (int64_t)p2 * pn3;
-        r[p3] = v;
-        if (g3 >= 0) r[g3] = v;
+    const int p3 = l30 + line + a.shift, g3 = ghost_of(p3, a.n3, m2);
+    const int64_t d2 = g2 >= 0 ? (int64_t)(g2 - p2) * pn3 : 0;
+    const int d3 = g3 >= 0 ? g3 - p3 : 0;
+    const int64_t d1 = (int64_t)a.n1 * plane;
+    S *r = P + (int64_t)q * (a.n1 + m2) * plane + (int64_t)(r0 + a.shift) * plane + (int64_t)p2 * pn3 + p3;
+    const int64_t rstep = (int64_t)STEP * plane;
+    for (int l1 = r0; l1 < L; l1 += STEP, r += rstep) {
+        const S v = sl[pidx<A>(l1)];
+        const int p1 = l1 + a.shift;
+        r[0] = v;
+        if (g3 >= 0) r[d3] = v;
         if (g2 >= 0) {
-            S *rg = dstq + (int64_t)p1 * plane + (int64_t)g2 * pn3;
-            rg[p3] = v;
-            if (g3 >= 0) rg[g3] = v;
+            r[d2] = v;
+            if (g3 >= 0) r[d2 + d3] = v;
         }
-        if (g1 >= 0) {
-            S *r1 = dstq + (int64_t)g1 * plane + (int64_t)p2 * pn3;
-            r1[p3] = v;
-            if (g3 >= 0) r1[g3] = v;
+        if (p1 < m2 || p1 >= a.n1) {
+            S *rg = r + (p1 < m2 ? d1 : -d1);
+            rg[0] = v;
+            if (g3 >= 0) rg[d3] = v;
             if (g2 >= 0) {
-                S *rg = dstq + (int64_t)g1 * plane + (int64_t)g2 * pn3;
-                rg[p3] = v;
-                if (g3 >= 0) rg[g3] = v;
+                rg[d2] = v;
+                if (g3 >= 0) rg[d2 + d3] = v;
             }
         }
     }
