@@ -255,6 +255,22 @@ def run_ours(args, rank, world, local):
             e1.record(s)
             barrier()
             grad_ms[name] = e0.elapsed_time(e1) / min(args.steps, 3)
+        # adjoint throughput (points set), with its stages from the library's
+        # timing records: spread (clear + spread), forward FFT, deconvolution
+        h_out = torch.empty((N, N, N), dtype=cdt, device=dev)
+        plan.adjoint(f, out=h_out)
+        barrier()
+        _lib.lib().nfft3_timing_read(plan._h, None, None, None, 1)
+        e0.record(s)
+        for _ in range(min(args.steps, 3)):
+            plan.adjoint(f, out=h_out)
+        e1.record(s)
+        barrier()
+        adj_ms = e0.elapsed_time(e1) / min(args.steps, 3)
+        _lib.lib().nfft3_timing_read(plan._h, st_ms, st_n, None, 1)
+        adj_stages = {nm: (st_ms[i] / st_n[i] if st_n[i] else 0.0) for i, nm in enumerate(_lib.STAGES)
+                      if nm in ("spread", "fft_fwd", "deconv_adj")}
+        del h_out
         # accuracy on the fixed subsample (oracle on rank 0's host; computed later)
         idx = np.concatenate([wl.rng(99).choice(M // 2, SUBSAMPLE, replace=False),
                               M // 2 + wl.rng(98).choice(M - M // 2, SUBSAMPLE, replace=False)])
@@ -304,6 +320,7 @@ def run_ours(args, rank, world, local):
                             "%.0f %% of it" % (w, w, w, l1_floor_ms, 100 * l1_floor_ms / g_ms))
         results[fam] = {
             "m": m, "ms_per_step": ms, "ms_eval_only": ms_eval, "e2e_ms": e2e_ms, "grad_ms": grad_ms,
+            "adj_ms": adj_ms, "adj_stages": adj_stages,
             "stages_ms": stages, "launches_per_step": launches.value / args.steps,
             "clocks": clocks, "roofline": roof, "f_sub": f_sub, "idx": idx,
             "h2d": M * 3 * 8 + N ** 3 * 2 * rb, "d2h": M * 2 * rb,
@@ -342,6 +359,8 @@ def run_ours(args, rank, world, local):
             "ms_per_step": r["ms_per_step"], "m": r["m"], "rel_l2_vs_oracle": r["rel_l2"],
             "eval_only_mpoints_s": pts / (r["ms_eval_only"] * 1e-3) / 1e6,
             "gradient_mpoints_s": {k: pts / (v * 1e-3) / 1e6 for k, v in r["grad_ms"].items()},
+            "adjoint": {"mpoints_s": pts / (r["adj_ms"] * 1e-3) / 1e6, "ms": r["adj_ms"],
+                        "stages_ms": r["adj_stages"]},
             "stages_ms": r["stages_ms"], "roofline": r["roofline"],
             "fft_share": r["stages_ms"]["fft"] / max(sum(r["stages_ms"].values()), 1e-12),
             "e2e": {"value": pts / (r["e2e_ms"] * 1e-3) / 1e6, "unit": "Mpoints/s",
@@ -364,6 +383,7 @@ def run_ours(args, rank, world, local):
         "rel_l2_vs_oracle": main["rel_l2_vs_oracle"],
         "eval_only_mpoints_s": main["eval_only_mpoints_s"],
         "gradient_mpoints_s": main["gradient_mpoints_s"],
+        "adjoint": main["adjoint"],
         "stages_ms": main["stages_ms"], "fft_share": main["fft_share"],
         "roofline": main["roofline"],
         "e2e": main["e2e"],

@@ -397,6 +397,10 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         const char *g = std::getenv("GBNFFT_GATHER");
         const char *wv = std::getenv("GBNFFT_DF_WEIGHTS");
         p->df_weights_fp64 = !(wv && !std::strcmp(wv, "df"));
+        // adjoint spread: shared-memory tile boxes (default) or one thread per
+        // point with global atomics only (GBNFFT_SPREAD=direct)
+        const char *sp = std::getenv("GBNFFT_SPREAD");
+        p->spread_direct = sp && !std::strcmp(sp, "direct");
         p->gather_mode = !g                           ? 3
                          : !std::strcmp(g, "thread") ? 1
                          : !std::strcmp(g, "native") ? 2
@@ -939,7 +943,11 @@ template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
     const int rec = rec_begin(p, kRecAdjoint);
     cudaError_t e = cudaMemsetAsync(H, 0, sizeof(C) * nn, p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
-    e = launch_spread<R>((const C *)f, g, p->m, points_view<R>(p), win_table<R>(p), H, p->stream);
+    if (!p->spread_direct && p->nchunks > 0)
+        e = launch_spread_tiles<R>((const C *)f, g, p->m, points_view<R>(p), win_table<R>(p), p->pb.chunks,
+                                   p->nchunks, p->pb.nt2, p->pb.nt3, H, p->stream);
+    else
+        e = launch_spread<R>((const C *)f, g, p->m, points_view<R>(p), win_table<R>(p), H, p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     rec_mark(p, rec, 1);
     int st = exec_grid_fft(p, H, prec, CUFFT_FORWARD, 1);

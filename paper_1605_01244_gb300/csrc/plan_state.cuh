@@ -25,6 +25,7 @@ struct nfft3_plan_s {
     double window_err_df;
     int df_weights_fp64;       // GBNFFT_DF_WEIGHTS: FP64-pipe weights (default) or df ("df")
     int gather_mode;           // GBNFFT_GATHER: 0 col (default), 1 thread, 2 native (see plan.cu)
+    int spread_direct;         // GBNFFT_SPREAD=direct: one thread per point, global atomics only
     // tables and grid
     void *D[3];               // deconvolution factors, real type of the family
     void *grid;               // n1 n2 n3 complex (x4 once eval_grad ran)

@@ -1,0 +1,149 @@
+// Adjoint spread through shared memory (the first step of the transposed
+// NFFT: H[l] += f_j phi(x_j - l / n) over the 2m+1 stencil nodes per
+// dimension), one block per chunk of at most kChunk sorted points of one
+// kTile^3 tile.  The stencils of a tile's points lie in the box of
+// (kTile + 2m)^3 nodes starting m nodes before the tile, so the block
+// accumulates them there with shared-memory atomics and then adds the box to
+// the oversampled grid once (global atomics, node indices wrapped mod n).
+// Warps take points; the lanes of a warp take the (b, c) node pairs of a
+// stencil plane, so that within a warp no two lanes hit the same node.
+#include "internal.cuh"
+
+namespace gbnfft {
+namespace {
+
+// centre node l0 + m (mod n) of a stencil (l0 in [0, n))
+__device__ __forceinline__ int tile_centre(int l0, int m, int n) {
+    int c = l0 + m;
+    while (c >= n) c -= n;
+    return c;
+}
+
+__device__ __forceinline__ int wrap_node(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+template <typename R, int MM, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) spread_tile_kernel(const typename Cplx<R>::T *__restrict__ f, Grid3 g,
+                                                              PointsView<R> pts,
+                                                              const __grid_constant__ Poly<R, MM> P,
+                                                              const int4 *__restrict__ chunks, int nt2, int nt3,
+                                                              typename Cplx<R>::T *__restrict__ H) {
+    using C = typename Cplx<R>::T;
+    constexpr int W = 2 * MM + 1, B = kTile + 2 * MM, B3 = B * B * B, D = PolyDeg<R>::value;
+    constexpr int NSLOT = (W * W + 31) / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *box_re = reinterpret_cast<R *>(smem_raw);   // box node (i1, i2, i3) at (i1 B + i2) B + i3
+    R *box_im = box_re + B3;
+    const int4 ch = chunks[blockIdx.x];
+    const int t = ch.x;
+    const int tt3 = t % nt3, tt2 = (t / nt3) % nt2, tt1 = t / (nt3 * nt2);
+    for (int e = threadIdx.x; e < B3; e += THREADS) box_re[e] = box_im[e] = (R)0;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int tap = lane < W ? lane : 0;
+    for (int i = threadIdx.x >> 5; i < ch.z; i += THREADS / 32) {
+        const int64_t j = (int64_t)ch.y + i;
+        const int4 key = pts.key[j];
+        const C fv = f[key.w];
+        // lane a < W: the weight of tap a in each dimension (Horner in t = 2s - 1)
+        R w[3];
+        {
+            const R s[3] = {pts.s1[j], pts.s2[j], pts.s3[j]};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const R tv = (R)2 * s[d] - (R)1;
+                R v = P.c[d][tap][D];
+#pragma unroll
+                for (int k = D - 1; k >= 0; --k) v = fma(v, tv, P.c[d][tap][k]);
+                w[d] = v;
+            }
+        }
+        // stencil node a of dimension d sits at box index o_d + a
+        const int o1 = tile_centre(key.x, MM, g.n1) - kTile * tt1;
+        const int o2 = tile_centre(key.y, MM, g.n2) - kTile * tt2;
+        const int o3 = tile_centre(key.z, MM, g.n3) - kTile * tt3;
+        R fr[NSLOT], fi[NSLOT];
+        int off[NSLOT];
+#pragma unroll
+        for (int k = 0; k < NSLOT; ++k) {
+            const int slot = lane + 32 * k;
+            const bool in = slot < W * W;
+            const int b = in ? slot / W : 0, c = in ? slot - (slot / W) * W : 0;
+            const R w23 = __shfl_sync(0xffffffffu, w[1], b) * __shfl_sync(0xffffffffu, w[2], c);
+            fr[k] = in ? fv.x * w23 : (R)0;
+            fi[k] = in ? fv.y * w23 : (R)0;
+            off[k] = in ? (o2 + b) * B + (o3 + c) : -1;
+        }
+#pragma unroll 1
+        for (int a = 0; a < W; ++a) {
+            const R w1 = __shfl_sync(0xffffffffu, w[0], a);
+            const int base = (o1 + a) * B * B;
+#pragma unroll
+            for (int k = 0; k < NSLOT; ++k) {
+                if (off[k] < 0) continue;
+                atomicAdd(box_re + base + off[k], fr[k] * w1);
+                atomicAdd(box_im + base + off[k], fi[k] * w1);
+            }
+        }
+    }
+    __syncthreads();
+    // the box starts m nodes before the tile in every dimension
+    const int b1 = kTile * tt1 - MM, b2 = kTile * tt2 - MM, b3 = kTile * tt3 - MM;
+    for (int e = threadIdx.x; e < B3; e += THREADS) {
+        const R re = box_re[e], im = box_im[e];
+        if (re == (R)0 && im == (R)0) continue;
+        const int i1 = e / (B * B), i2 = (e / B) % B, i3 = e % B;
+        const int64_t node = ((int64_t)wrap_node(b1 + i1, g.n1) * g.n2 + wrap_node(b2 + i2, g.n2)) * g.n3 +
+                             wrap_node(b3 + i3, g.n3);
+        R *dst = reinterpret_cast<R *>(H + node);
+        atomicAdd(dst, re);
+        atomicAdd(dst + 1, im);
+    }
+}
+
+template <typename R, int MM>
+cudaError_t spread_tile_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsView<R> pts, const WinTable<R> &w,
+                                 const int4 *chunks, int nchunks, int nt2, int nt3, typename Cplx<R>::T *H,
+                                 cudaStream_t st) {
+    constexpr int B = kTile + 2 * MM;
+    // the FP64 boxes take most of an SM's shared memory: more threads per block
+    constexpr int THREADS = sizeof(R) == 8 ? 512 : 256;
+    const size_t smem = 2 * sizeof(R) * (size_t)B * B * B;
+    auto kern = spread_tile_kernel<R, MM, THREADS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)nchunks, THREADS, smem, st>>>(f, g, pts, make_poly<R, MM>(w), chunks, nt2, nt3, H);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_spread_tiles(const typename Cplx<R>::T *f, Grid3 g, int m, PointsView<R> pts,
+                                const WinTable<R> &w, const int4 *chunks, int nchunks, int nt2, int nt3,
+                                typename Cplx<R>::T *H, cudaStream_t st) {
+    if (nchunks <= 0) return cudaSuccess;
+    switch (m) {
+        case 1: return spread_tile_dispatch<R, 1>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
+        case 2: return spread_tile_dispatch<R, 2>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
+        case 3: return spread_tile_dispatch<R, 3>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
+        case 4: return spread_tile_dispatch<R, 4>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
+        case 5: return spread_tile_dispatch<R, 5>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
+        case 6: return spread_tile_dispatch<R, 6>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
+        case 7: return spread_tile_dispatch<R, 7>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
+        case 8: return spread_tile_dispatch<R, 8>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_spread_tiles<double>(const double2 *, Grid3, int, PointsView<double>,
+                                                 const WinTable<double> &, const int4 *, int, int, int, double2 *,
+                                                 cudaStream_t);
+template cudaError_t launch_spread_tiles<float>(const float2 *, Grid3, int, PointsView<float>,
+                                                const WinTable<float> &, const int4 *, int, int, int, float2 *,
+                                                cudaStream_t);
+
+}  // namespace gbnfft

@@ -472,3 +472,36 @@ def test_pruned_and_full_fft_agree(sigma, monkeypatch):
         assert max_rel(f, fc) <= 3e-13, mode
         assert max_rel(g, gc) <= 3e-13, mode
         assert max_rel(h, hc) <= 1e-12, mode
+
+
+@pytest.mark.parametrize("prec,m,N", [("f64", 6, (24, 20, 32)), ("f64", 8, (8, 8, 8)), ("f64", 1, (16, 10, 12)),
+                                      ("f32", 3, (24, 20, 32)), ("f32", 8, (10, 12, 8))])
+def test_tiled_spread_matches_direct_and_cpu(prec, m, N, monkeypatch):
+    """The adjoint's shared-memory tile spread (default) against the one-thread-
+    per-point spread (GBNFFT_SPREAD=direct) and the CPU NFFT restatement.  A
+    dense cluster puts hundreds of points in one tile (several chunks of one
+    tile); N = 8^3 at m = 8 gives n = 16 < the 24-node box, whose nodes wrap
+    onto each other."""
+    from paper_1605_01244_gb300 import Plan
+    x = np.concatenate([wl.uniform_points(900, seed=60), wl.cluster_points(1100, 0.002, seed=61)])
+    g = wl.rng(62)
+    f = g.standard_normal(len(x)) + 1j * g.standard_normal(len(x))
+    out = {}
+    for mode in ("tiles", "direct"):
+        if mode == "direct":
+            monkeypatch.setenv("GBNFFT_SPREAD", "direct")
+        else:
+            monkeypatch.delenv("GBNFFT_SPREAD", raising=False)
+        plan = Plan(N, len(x), m=m, precision=prec)
+        plan.set_points(to_dev(x))
+        out[mode] = to_np(plan.adjoint(to_dev(f, CD[prec]))).astype(np.complex128)
+    hc = nfft_cpu.adjoint(f, x, N, plan.n, m)
+    if prec == "f64":
+        assert max_rel(out["tiles"], out["direct"]) <= 1e-12
+        assert max_rel(out["tiles"], hc) <= 1e-12
+    else:
+        # FP32 sums of ~1000 contributions per node in the cluster: both spreads
+        # round at the FP32 level, in different orders; the tiled one may not be
+        # less accurate than the direct one
+        e_tiles, e_direct = rel_l2(out["tiles"], hc), rel_l2(out["direct"], hc)
+        assert e_tiles <= max(2 * e_direct, 1e-6), (e_tiles, e_direct)
