@@ -104,11 +104,135 @@ __global__ void __launch_bounds__(THREADS, 1) spread_tile_kernel(const typename 
     }
 }
 
+// ---- FP64 family: double-float accumulation without atomics ---------------
+// GB300's FP64 pipe runs at 1/64 of the FP32 rate, and shared-memory FP64
+// atomics add FP64 work of their own; the FP64 family therefore accumulates
+// its box in double-float (hi + lo floats) on the FP32 pipe.  Phase 1: the
+// block evaluates the FP64 tap weights of all the chunk's points and stages
+// them as float pairs.  Phase 2: warp p owns box plane p (B warps) and walks
+// every point of the chunk, adding the point's taps that fall in its plane;
+// no other warp touches that plane and the lanes of a warp take distinct
+// (b, c) nodes, so the node updates need no atomics.
+__device__ __forceinline__ float2 df2_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    const float h = __fadd_rn(p, e);
+    return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+__device__ __forceinline__ float2 df2_add(float2 a, float2 b) {
+    const float s = __fadd_rn(a.x, b.x);
+    const float bb = __fsub_rn(s, a.x);
+    float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+    const float h = __fadd_rn(s, e);
+    return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ float2 df2_split(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+// shared memory of the double-float spread: the box (float4 a node) and the
+// staged weights, values and box offsets of up to kChunk points
+template <int MM> constexpr size_t spread_df_smem() {
+    constexpr int W = 2 * MM + 1, B = kTile + 2 * MM;
+    return sizeof(float4) * (size_t)B * B * B + sizeof(float2) * (size_t)kChunk * 3 * W +
+           sizeof(float4) * (size_t)kChunk + sizeof(int4) * (size_t)kChunk;
+}
+
+template <int MM>
+__global__ void __launch_bounds__(32 * (kTile + 2 * MM), 1) spread_tile_df_kernel(
+    const double2 *__restrict__ f, Grid3 g, PointsView<double> pts, const __grid_constant__ Poly<double, MM> P,
+    const int4 *__restrict__ chunks, int nt2, int nt3, double2 *__restrict__ H) {
+    constexpr int W = 2 * MM + 1, B = kTile + 2 * MM, B3 = B * B * B, D = PolyDeg<double>::value;
+    constexpr int THREADS = 32 * B, NSLOT = (W * W + 31) / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *box = reinterpret_cast<float4 *>(smem_raw);                 // (re hi, re lo, im hi, im lo)
+    float2 *wts = reinterpret_cast<float2 *>(box + B3);                   // [point][d][tap]
+    float4 *fsm = reinterpret_cast<float4 *>(wts + kChunk * 3 * W);      // f_j as (re hi, re lo, im hi, im lo)
+    int4 *osm = reinterpret_cast<int4 *>(fsm + kChunk);                  // box index of the first node
+    const int4 ch = chunks[blockIdx.x];
+    const int t = ch.x;
+    const int tt3 = t % nt3, tt2 = (t / nt3) % nt2, tt1 = t / (nt3 * nt2);
+    for (int e = threadIdx.x; e < B3; e += THREADS) box[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // phase 1
+    for (int e = threadIdx.x; e < ch.z * 3 * W; e += THREADS) {
+        const int i = e / (3 * W), r = e - i * (3 * W), d = r / W, tap = r - d * W;
+        const int64_t j = (int64_t)ch.y + i;
+        const double s = d == 0 ? pts.s1[j] : d == 1 ? pts.s2[j] : pts.s3[j];
+        const double tv = 2.0 * s - 1.0;
+        double v = P.c[d][tap][D];
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) v = fma(v, tv, P.c[d][tap][k]);
+        wts[e] = df2_split(v);
+    }
+    for (int i = threadIdx.x; i < ch.z; i += THREADS) {
+        const int4 key = pts.key[(int64_t)ch.y + i];
+        const double2 fv = f[key.w];
+        const float2 re = df2_split(fv.x), im = df2_split(fv.y);
+        fsm[i] = make_float4(re.x, re.y, im.x, im.y);
+        osm[i] = make_int4(tile_centre(key.x, MM, g.n1) - kTile * tt1, tile_centre(key.y, MM, g.n2) - kTile * tt2,
+                           tile_centre(key.z, MM, g.n3) - kTile * tt3, 0);
+    }
+    __syncthreads();
+    // phase 2
+    const int lane = threadIdx.x & 31, plane = threadIdx.x >> 5;
+    for (int i = 0; i < ch.z; ++i) {
+        const int4 o = osm[i];
+        const int a = plane - o.x;
+        if (a < 0 || a >= W) continue;
+        const float2 *wi = wts + i * 3 * W;
+        const float4 fv = fsm[i];
+        const float2 w1 = wi[a];
+        const float2 fr = df2_mul(make_float2(fv.x, fv.y), w1), fi = df2_mul(make_float2(fv.z, fv.w), w1);
+        float4 *row = box + plane * B * B;
+#pragma unroll
+        for (int k = 0; k < NSLOT; ++k) {
+            const int slot = lane + 32 * k;
+            if (slot >= W * W) continue;
+            const int b = slot / W, c = slot - b * W;
+            const float2 w23 = df2_mul(wi[W + b], wi[2 * W + c]);
+            float4 &node = row[(o.y + b) * B + (o.z + c)];
+            const float4 v = node;
+            const float2 re = df2_add(make_float2(v.x, v.y), df2_mul(fr, w23));
+            const float2 im = df2_add(make_float2(v.z, v.w), df2_mul(fi, w23));
+            node = make_float4(re.x, re.y, im.x, im.y);
+        }
+    }
+    __syncthreads();
+    const int b1 = kTile * tt1 - MM, b2 = kTile * tt2 - MM, b3 = kTile * tt3 - MM;
+    for (int e = threadIdx.x; e < B3; e += THREADS) {
+        const float4 v = box[e];
+        if (v.x == 0.f && v.z == 0.f) continue;
+        const int i1 = e / (B * B), i2 = (e / B) % B, i3 = e % B;
+        const int64_t node = ((int64_t)wrap_node(b1 + i1, g.n1) * g.n2 + wrap_node(b2 + i2, g.n2)) * g.n3 +
+                             wrap_node(b3 + i3, g.n3);
+        double *dst = reinterpret_cast<double *>(H + node);
+        atomicAdd(dst, (double)v.x + (double)v.y);
+        atomicAdd(dst + 1, (double)v.z + (double)v.w);
+    }
+}
+
 template <typename R, int MM>
 cudaError_t spread_tile_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsView<R> pts, const WinTable<R> &w,
                                  const int4 *chunks, int nchunks, int nt2, int nt3, typename Cplx<R>::T *H,
                                  cudaStream_t st) {
     constexpr int B = kTile + 2 * MM;
+    if constexpr (sizeof(R) == 8) {
+        // FP64 family: the double-float kernel where its box and staged weights
+        // fit one SM's shared memory (m <= 7)
+        constexpr size_t smem_df = spread_df_smem<MM>();
+        if constexpr (smem_df <= 227 * 1024) {
+            auto kern = spread_tile_df_kernel<MM>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
+            if (e != cudaSuccess) return e;
+            kern<<<(unsigned)nchunks, 32 * B, smem_df, st>>>(f, g, pts, make_poly<double, MM>(w), chunks, nt2,
+                                                              nt3, H);
+            return cudaGetLastError();
+        }
+    }
     // the FP64 boxes take most of an SM's shared memory: more threads per block
     constexpr int THREADS = sizeof(R) == 8 ? 512 : 256;
     const size_t smem = 2 * sizeof(R) * (size_t)B * B * B;
