@@ -177,8 +177,8 @@ cudaError_t launch_spread(const typename Cplx<R>::T *f, Grid3 g, int m, PointsVi
 // per chunk of the set_points chunk list.
 template <typename R>
 cudaError_t launch_spread_tiles(const typename Cplx<R>::T *f, Grid3 g, int m, PointsView<R> pts,
-                                const WinTable<R> &w, const int4 *chunks, int nchunks, int nt2, int nt3,
-                                typename Cplx<R>::T *H, cudaStream_t st);
+                                const WinTable<R> &w, const WinTableDF *wdf, const int4 *chunks, int nchunks,
+                                int nt2, int nt3, typename Cplx<R>::T *H, cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_deconv_gather(const typename Cplx<R>::T *H, Grid3 g, const R *D1, const R *D2,

@@ -944,8 +944,9 @@ template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
     cudaError_t e = cudaMemsetAsync(H, 0, sizeof(C) * nn, p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     if (!p->spread_direct && p->nchunks > 0)
-        e = launch_spread_tiles<R>((const C *)f, g, p->m, points_view<R>(p), win_table<R>(p), p->pb.chunks,
-                                   p->nchunks, p->pb.nt2, p->pb.nt3, H, p->stream);
+        e = launch_spread_tiles<R>((const C *)f, g, p->m, points_view<R>(p), win_table<R>(p),
+                                   prec == 64 ? &p->wtdf : nullptr, p->pb.chunks, p->nchunks, p->pb.nt2,
+                                   p->pb.nt3, H, p->stream);
     else
         e = launch_spread<R>((const C *)f, g, p->m, points_view<R>(p), win_table<R>(p), H, p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;

@@ -108,8 +108,9 @@ __global__ void __launch_bounds__(THREADS, 1) spread_tile_kernel(const typename 
 // GB300's FP64 pipe runs at 1/64 of the FP32 rate, and shared-memory FP64
 // atomics add FP64 work of their own; the FP64 family therefore accumulates
 // its box in double-float (hi + lo floats) on the FP32 pipe.  Phase 1: the
-// block evaluates the FP64 tap weights of all the chunk's points and stages
-// them as float pairs.  Phase 2: warp p owns box plane p (B warps) and walks
+// block evaluates the tap weights of all the chunk's points by double-float
+// Horner (the plan's hi + lo coefficient table, copied to shared memory) and
+// stages them as float pairs.  Phase 2: warp p owns box plane p (B warps) and walks
 // every point of the chunk, adding the point's taps that fall in its plane;
 // no other warp touches that plane and the lanes of a warp take distinct
 // (b, c) nodes, so the node updates need no atomics.
@@ -139,34 +140,54 @@ __device__ __forceinline__ float2 df2_split(double v) {
 template <int MM> constexpr size_t spread_df_smem() {
     constexpr int W = 2 * MM + 1, B = kTile + 2 * MM;
     return sizeof(float4) * (size_t)B * B * B + sizeof(float2) * (size_t)kChunk * 3 * W +
-           sizeof(float4) * (size_t)kChunk + sizeof(int4) * (size_t)kChunk;
+           sizeof(float4) * (size_t)kChunk + sizeof(int4) * (size_t)kChunk + sizeof(PolyDF<MM>);
+}
+
+// exact float -> double from the bits (no FP64 conversion instruction) for
+// normal floats; zeros, subnormals and non-finite values take the conversion
+__device__ __forceinline__ double f2d_bits(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned ex = (u >> 23) & 0xFFu;
+    if (ex == 0u || ex == 0xFFu) return (double)x;
+    return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                            ((unsigned long long)(ex + 896u) << 52) |
+                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
 }
 
 template <int MM>
 __global__ void __launch_bounds__(32 * (kTile + 2 * MM), 1) spread_tile_df_kernel(
-    const double2 *__restrict__ f, Grid3 g, PointsView<double> pts, const __grid_constant__ Poly<double, MM> P,
+    const double2 *__restrict__ f, Grid3 g, PointsView<double> pts, const __grid_constant__ PolyDF<MM> P,
     const int4 *__restrict__ chunks, int nt2, int nt3, double2 *__restrict__ H) {
-    constexpr int W = 2 * MM + 1, B = kTile + 2 * MM, B3 = B * B * B, D = PolyDeg<double>::value;
+    constexpr int W = 2 * MM + 1, B = kTile + 2 * MM, B3 = B * B * B, D = kPolyDegDF;
     constexpr int THREADS = 32 * B, NSLOT = (W * W + 31) / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *box = reinterpret_cast<float4 *>(smem_raw);                 // (re hi, re lo, im hi, im lo)
     float2 *wts = reinterpret_cast<float2 *>(box + B3);                   // [point][d][tap]
     float4 *fsm = reinterpret_cast<float4 *>(wts + kChunk * 3 * W);      // f_j as (re hi, re lo, im hi, im lo)
     int4 *osm = reinterpret_cast<int4 *>(fsm + kChunk);                  // box index of the first node
+    PolyDF<MM> *tab = reinterpret_cast<PolyDF<MM> *>(osm + kChunk);       // double-float tap polynomials
     const int4 ch = chunks[blockIdx.x];
     const int t = ch.x;
     const int tt3 = t % nt3, tt2 = (t / nt3) % nt2, tt1 = t / (nt3 * nt2);
     for (int e = threadIdx.x; e < B3; e += THREADS) box[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-    // phase 1
+    {
+        const float *src = &P.ch[0][0][0];
+        float *dst = &tab->ch[0][0][0];
+        constexpr int NC = 2 * 3 * W * (D + 1);   // ch then cl
+        for (int e = threadIdx.x; e < NC; e += THREADS) dst[e] = src[e];
+    }
+    __syncthreads();
+    // phase 1: tap weights by double-float Horner in t = 2s - 1 (FP32 pipe)
     for (int e = threadIdx.x; e < ch.z * 3 * W; e += THREADS) {
         const int i = e / (3 * W), r = e - i * (3 * W), d = r / W, tap = r - d * W;
         const int64_t j = (int64_t)ch.y + i;
         const double s = d == 0 ? pts.s1[j] : d == 1 ? pts.s2[j] : pts.s3[j];
-        const double tv = 2.0 * s - 1.0;
-        double v = P.c[d][tap][D];
+        const float2 tv = df2_split(2.0 * s - 1.0);
+        float2 v = make_float2(tab->ch[d][tap][D], tab->cl[d][tap][D]);
 #pragma unroll
-        for (int k = D - 1; k >= 0; --k) v = fma(v, tv, P.c[d][tap][k]);
-        wts[e] = df2_split(v);
+        for (int k = D - 1; k >= 0; --k)
+            v = df2_add(df2_mul(v, tv), make_float2(tab->ch[d][tap][k], tab->cl[d][tap][k]));
+        wts[e] = v;
     }
     for (int i = threadIdx.x; i < ch.z; i += THREADS) {
         const int4 key = pts.key[(int64_t)ch.y + i];
@@ -210,25 +231,26 @@ __global__ void __launch_bounds__(32 * (kTile + 2 * MM), 1) spread_tile_df_kerne
         const int64_t node = ((int64_t)wrap_node(b1 + i1, g.n1) * g.n2 + wrap_node(b2 + i2, g.n2)) * g.n3 +
                              wrap_node(b3 + i3, g.n3);
         double *dst = reinterpret_cast<double *>(H + node);
-        atomicAdd(dst, (double)v.x + (double)v.y);
-        atomicAdd(dst + 1, (double)v.z + (double)v.w);
+        atomicAdd(dst, f2d_bits(v.x) + f2d_bits(v.y));
+        atomicAdd(dst + 1, f2d_bits(v.z) + f2d_bits(v.w));
     }
 }
 
 template <typename R, int MM>
 cudaError_t spread_tile_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsView<R> pts, const WinTable<R> &w,
-                                 const int4 *chunks, int nchunks, int nt2, int nt3, typename Cplx<R>::T *H,
-                                 cudaStream_t st) {
+                                 const WinTableDF *wdf, const int4 *chunks, int nchunks, int nt2, int nt3,
+                                 typename Cplx<R>::T *H, cudaStream_t st) {
     constexpr int B = kTile + 2 * MM;
     if constexpr (sizeof(R) == 8) {
         // FP64 family: the double-float kernel where its box and staged weights
         // fit one SM's shared memory (m <= 7)
         constexpr size_t smem_df = spread_df_smem<MM>();
         if constexpr (smem_df <= 227 * 1024) {
+            if (!wdf) return cudaErrorInvalidValue;
             auto kern = spread_tile_df_kernel<MM>;
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
             if (e != cudaSuccess) return e;
-            kern<<<(unsigned)nchunks, 32 * B, smem_df, st>>>(f, g, pts, make_poly<double, MM>(w), chunks, nt2,
+            kern<<<(unsigned)nchunks, 32 * B, smem_df, st>>>(f, g, pts, make_poly_df<MM>(*wdf), chunks, nt2,
                                                               nt3, H);
             return cudaGetLastError();
         }
@@ -247,27 +269,27 @@ cudaError_t spread_tile_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsVi
 
 template <typename R>
 cudaError_t launch_spread_tiles(const typename Cplx<R>::T *f, Grid3 g, int m, PointsView<R> pts,
-                                const WinTable<R> &w, const int4 *chunks, int nchunks, int nt2, int nt3,
-                                typename Cplx<R>::T *H, cudaStream_t st) {
+                                const WinTable<R> &w, const WinTableDF *wdf, const int4 *chunks, int nchunks,
+                                int nt2, int nt3, typename Cplx<R>::T *H, cudaStream_t st) {
     if (nchunks <= 0) return cudaSuccess;
     switch (m) {
-        case 1: return spread_tile_dispatch<R, 1>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
-        case 2: return spread_tile_dispatch<R, 2>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
-        case 3: return spread_tile_dispatch<R, 3>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
-        case 4: return spread_tile_dispatch<R, 4>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
-        case 5: return spread_tile_dispatch<R, 5>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
-        case 6: return spread_tile_dispatch<R, 6>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
-        case 7: return spread_tile_dispatch<R, 7>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
-        case 8: return spread_tile_dispatch<R, 8>(f, g, pts, w, chunks, nchunks, nt2, nt3, H, st);
+        case 1: return spread_tile_dispatch<R, 1>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
+        case 2: return spread_tile_dispatch<R, 2>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
+        case 3: return spread_tile_dispatch<R, 3>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
+        case 4: return spread_tile_dispatch<R, 4>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
+        case 5: return spread_tile_dispatch<R, 5>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
+        case 6: return spread_tile_dispatch<R, 6>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
+        case 7: return spread_tile_dispatch<R, 7>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
+        case 8: return spread_tile_dispatch<R, 8>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template cudaError_t launch_spread_tiles<double>(const double2 *, Grid3, int, PointsView<double>,
-                                                 const WinTable<double> &, const int4 *, int, int, int, double2 *,
-                                                 cudaStream_t);
+                                                 const WinTable<double> &, const WinTableDF *, const int4 *, int,
+                                                 int, int, double2 *, cudaStream_t);
 template cudaError_t launch_spread_tiles<float>(const float2 *, Grid3, int, PointsView<float>,
-                                                const WinTable<float> &, const int4 *, int, int, int, float2 *,
-                                                cudaStream_t);
+                                                const WinTable<float> &, const WinTableDF *, const int4 *, int,
+                                                int, int, float2 *, cudaStream_t);
 
 }  // namespace gbnfft
