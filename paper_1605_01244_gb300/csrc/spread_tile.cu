@@ -3,10 +3,13 @@
 // dimension), one block per chunk of at most kChunk sorted points of one
 // kTile^3 tile.  The stencils of a tile's points lie in the box of
 // (kTile + 2m)^3 nodes starting m nodes before the tile, so the block
-// accumulates them there with shared-memory atomics and then adds the box to
-// the oversampled grid once (global atomics, node indices wrapped mod n).
-// Warps take points; the lanes of a warp take the (b, c) node pairs of a
-// stencil plane, so that within a warp no two lanes hit the same node.
+// accumulates them there and then adds the box to the oversampled grid once
+// (global atomics, node indices wrapped mod n).
+// spread_tile_df_kernel (FP64, m <= 7) and spread_tile_f32_kernel (mixed)
+// give each warp one plane of the box, so no node update needs an atomic;
+// spread_tile_kernel (FP64 at m = 8, whose box and staged weights exceed
+// shared memory) has warps take points, the lanes of a warp take the (b, c)
+// node pairs of a stencil plane, and shared-memory atomics resolve the rest.
 #include "internal.cuh"
 
 namespace gbnfft {
@@ -236,6 +239,92 @@ __global__ void __launch_bounds__(32 * (kTile + 2 * MM), 1) spread_tile_df_kerne
     }
 }
 
+// ---- mixed family: plane-owned FP32 box, no atomics in shared memory ------
+// Same scheme as spread_tile_df_kernel in FP32: the block stages the chunk's
+// tap weights (FP32 Horner), then warp p owns box plane p and adds every
+// point's taps in that plane with plain shared-memory updates.
+template <int MM> constexpr size_t spread_f32_smem() {
+    constexpr int W = 2 * MM + 1, B = kTile + 2 * MM;
+    return sizeof(float2) * (size_t)B * B * B + sizeof(float) * (size_t)kChunk * 3 * W +
+           sizeof(float2) * (size_t)kChunk + sizeof(int4) * (size_t)kChunk + sizeof(Poly<float, MM>);
+}
+
+template <int MM>
+__global__ void __launch_bounds__(32 * (kTile + 2 * MM)) spread_tile_f32_kernel(
+    const float2 *__restrict__ f, Grid3 g, PointsView<float> pts, const __grid_constant__ Poly<float, MM> P,
+    const int4 *__restrict__ chunks, int nt2, int nt3, float2 *__restrict__ H) {
+    constexpr int W = 2 * MM + 1, B = kTile + 2 * MM, B3 = B * B * B, D = PolyDeg<float>::value;
+    constexpr int THREADS = 32 * B, NSLOT = (W * W + 31) / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *box = reinterpret_cast<float2 *>(smem_raw);                  // (re, im) per node
+    float *wts = reinterpret_cast<float *>(box + B3);                     // [point][d][tap]
+    float2 *fsm = reinterpret_cast<float2 *>(wts + kChunk * 3 * W);      // f_j
+    int4 *osm = reinterpret_cast<int4 *>(fsm + kChunk);                  // box index of the first node
+    Poly<float, MM> *tab = reinterpret_cast<Poly<float, MM> *>(osm + kChunk);
+    const int4 ch = chunks[blockIdx.x];
+    const int t = ch.x;
+    const int tt3 = t % nt3, tt2 = (t / nt3) % nt2, tt1 = t / (nt3 * nt2);
+    for (int e = threadIdx.x; e < B3; e += THREADS) box[e] = make_float2(0.f, 0.f);
+    {
+        const float *src = &P.c[0][0][0];
+        float *dst = &tab->c[0][0][0];
+        for (int e = threadIdx.x; e < 3 * W * (D + 1); e += THREADS) dst[e] = src[e];
+    }
+    __syncthreads();
+    // phase 1
+    for (int e = threadIdx.x; e < ch.z * 3 * W; e += THREADS) {
+        const int i = e / (3 * W), r = e - i * (3 * W), d = r / W, tap = r - d * W;
+        const int64_t j = (int64_t)ch.y + i;
+        const float s = d == 0 ? pts.s1[j] : d == 1 ? pts.s2[j] : pts.s3[j];
+        const float tv = 2.f * s - 1.f;
+        float v = tab->c[d][tap][D];
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) v = fmaf(v, tv, tab->c[d][tap][k]);
+        wts[e] = v;
+    }
+    for (int i = threadIdx.x; i < ch.z; i += THREADS) {
+        const int4 key = pts.key[(int64_t)ch.y + i];
+        fsm[i] = f[key.w];
+        osm[i] = make_int4(tile_centre(key.x, MM, g.n1) - kTile * tt1, tile_centre(key.y, MM, g.n2) - kTile * tt2,
+                           tile_centre(key.z, MM, g.n3) - kTile * tt3, 0);
+    }
+    __syncthreads();
+    // phase 2
+    const int lane = threadIdx.x & 31, plane = threadIdx.x >> 5;
+    for (int i = 0; i < ch.z; ++i) {
+        const int4 o = osm[i];
+        const int a = plane - o.x;
+        if (a < 0 || a >= W) continue;
+        const float *wi = wts + i * 3 * W;
+        const float2 fv = fsm[i];
+        const float w1 = wi[a];
+        const float fr = fv.x * w1, fi = fv.y * w1;
+        float2 *row = box + plane * B * B;
+#pragma unroll
+        for (int k = 0; k < NSLOT; ++k) {
+            const int slot = lane + 32 * k;
+            if (slot >= W * W) continue;
+            const int b = slot / W, c = slot - b * W;
+            const float w23 = wi[W + b] * wi[2 * W + c];
+            float2 &node = row[(o.y + b) * B + (o.z + c)];
+            const float2 v = node;
+            node = make_float2(fmaf(fr, w23, v.x), fmaf(fi, w23, v.y));
+        }
+    }
+    __syncthreads();
+    const int b1 = kTile * tt1 - MM, b2 = kTile * tt2 - MM, b3 = kTile * tt3 - MM;
+    for (int e = threadIdx.x; e < B3; e += THREADS) {
+        const float2 v = box[e];
+        if (v.x == 0.f && v.y == 0.f) continue;
+        const int i1 = e / (B * B), i2 = (e / B) % B, i3 = e % B;
+        const int64_t node = ((int64_t)wrap_node(b1 + i1, g.n1) * g.n2 + wrap_node(b2 + i2, g.n2)) * g.n3 +
+                             wrap_node(b3 + i3, g.n3);
+        float *dst = reinterpret_cast<float *>(H + node);
+        atomicAdd(dst, v.x);
+        atomicAdd(dst + 1, v.y);
+    }
+}
+
 template <typename R, int MM>
 cudaError_t spread_tile_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsView<R> pts, const WinTable<R> &w,
                                  const WinTableDF *wdf, const int4 *chunks, int nchunks, int nt2, int nt3,
@@ -255,7 +344,15 @@ cudaError_t spread_tile_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsVi
             return cudaGetLastError();
         }
     }
-    // the FP64 boxes take most of an SM's shared memory: more threads per block
+    if constexpr (sizeof(R) == 4) {
+        constexpr size_t smem_f = spread_f32_smem<MM>();
+        auto kern = spread_tile_f32_kernel<MM>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)nchunks, 32 * B, smem_f, st>>>(f, g, pts, make_poly<float, MM>(w), chunks, nt2, nt3, H);
+        return cudaGetLastError();
+    }
+    // FP64 at m = 8: the box takes most of an SM's shared memory, 512 threads
     constexpr int THREADS = sizeof(R) == 8 ? 512 : 256;
     const size_t smem = 2 * sizeof(R) * (size_t)B * B * B;
     auto kern = spread_tile_kernel<R, MM, THREADS>;
