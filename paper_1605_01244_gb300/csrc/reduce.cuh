@@ -1,12 +1,14 @@
-// FP64 reduction of a coordinate to its stencil origin and offset, shared by
-// set_points (points.cu) and the one- and two-dimensional NFFT (nfft_low.cu).
+// Reduction of a coordinate to its stencil origin and offset, with the
+// results of FP64 round-to-nearest arithmetic (mostly computed on the integer
+// pipe for n = 2^L), shared by set_points (points.cu) and the one- and
+// two-dimensional NFFT (nfft_low.cu).
 #pragma once
 #include "internal.cuh"
 
 namespace gbnfft {
 namespace {
 
-// Reduction of one coordinate (FP64):
+// Reduction of one coordinate (each step rounded as in FP64):
 //   xw = x - floor(x + 1/2)                 (wrap onto [-1/2, 1/2); the series is periodic)
 //   u  = n (xw + 1/2)                       (grid units; grid node l sits at x = -1/2 + l/n)
 //   v  = u - alpha, l0 = ceil(v), s = l0 - v in [0, 1)
