@@ -3,6 +3,8 @@
 // pipe for n = 2^L), shared by set_points (points.cu) and the one- and
 // two-dimensional NFFT (nfft_low.cu).
 #pragma once
+#include <cstring>
+
 #include "internal.cuh"
 
 namespace gbnfft {
@@ -42,6 +44,34 @@ template <> __device__ __forceinline__ float offset_as<float>(double s) {
     return __int_as_float(((e + 127) << 23) | (int)((b >> 29) & 0x7FFFFF));
 }
 
+// Bit casts and count-leading-zeros for the integer path below, which is also
+// compiled for the host by a CPU test of its exactness (same arithmetic).
+__host__ __device__ __forceinline__ long long bits_of(double v) {
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(v);
+#else
+    long long b;
+    std::memcpy(&b, &v, sizeof b);
+    return b;
+#endif
+}
+__host__ __device__ __forceinline__ double double_of(long long b) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(b);
+#else
+    double v;
+    std::memcpy(&v, &b, sizeof v);
+    return v;
+#endif
+}
+__host__ __device__ __forceinline__ int clz64(long long v) {
+#ifdef __CUDA_ARCH__
+    return __clzll(v);
+#else
+    return v == 0 ? 64 : __builtin_clzll((unsigned long long)v);
+#endif
+}
+
 // Per-dimension constants of the reduction (hoisted out of the point loops).
 // For n = 2^L the steps after t = x_w + 1/2 can run on fixed-point integers in
 // units of 2^-F grid cells, F = 62 - L: u = n t is U = t 2^62 (exact for
@@ -55,7 +85,7 @@ struct CoordParams {
     long long A, A_half, mask;   // A, A / 2, 2^F - 1
 };
 
-__device__ __forceinline__ CoordParams coord_params(int n, int m) {
+__host__ __device__ __forceinline__ CoordParams coord_params(int n, int m) {
     CoordParams c;
     c.n = n;
     c.nd = (double)n;
@@ -80,12 +110,11 @@ __device__ __forceinline__ CoordParams coord_params(int n, int m) {
 }
 
 // The double S 2^-F for 0 <= S < 2^63 holding at most 53 significant bits.
-__device__ __forceinline__ double fixed_to_double(unsigned long long S, int F) {
+__host__ __device__ __forceinline__ double fixed_to_double(unsigned long long S, int F) {
     if (S == 0) return 0.0;
-    const int p = 63 - __clzll((long long)S);
+    const int p = 63 - clz64((long long)S);
     const unsigned long long mant = p <= 52 ? S << (52 - p) : S >> (p - 52);
-    return __longlong_as_double((long long)(((unsigned long long)(p - F + 1023) << 52) |
-                                            (mant & 0xFFFFFFFFFFFFFull)));
+    return double_of((long long)(((unsigned long long)(p - F + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
 // The fixed-point path for u >= alpha / 2 (all but a sliver next to
@@ -95,8 +124,8 @@ __device__ __forceinline__ double fixed_to_double(unsigned long long S, int F) {
 // l0 - v is S = (-V) mod 2^F, exact too (CoordParams::Et_min).  Returns false
 // (nothing written) for t below that bound or u < alpha / 2, which take the
 // FP64 sequence.
-__device__ __forceinline__ bool reduce_fixed(double t, const CoordParams &c, long long &l0, double &s) {
-    const unsigned long long tb = (unsigned long long)__double_as_longlong(t);   // 0 <= t <= 1
+__host__ __device__ __forceinline__ bool reduce_fixed(double t, const CoordParams &c, long long &l0, double &s) {
+    const unsigned long long tb = (unsigned long long)bits_of(t);   // 0 <= t <= 1
     const int Et = (int)(tb >> 52);
     if (Et < c.Et_min) return false;
     const long long U = (long long)(((tb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (Et - 1013));
