@@ -87,3 +87,16 @@ def test_null_handles(lib):
     assert lib.nfft3f_adjoint(None, None, None) == _lib.NFFT3_ERR_ARG
     assert lib.nfft3d_set_points(None, None) == _lib.NFFT3_ERR_ARG
     assert lib.nfft3_sync(None) == _lib.NFFT3_ERR_ARG
+
+
+def test_reduce_coords_rejects_bad_arguments(lib):
+    """Argument checks of nfft3_reduce_coords come before any CUDA call."""
+    dummy = ctypes.c_void_p(16)
+    st = ctypes.c_void_p(32)
+    E = _lib.NFFT3_ERR_ARG
+    assert lib.nfft3_reduce_coords(1, 3, dummy, 10, None, None, None, st, None) == E      # n < 2
+    assert lib.nfft3_reduce_coords(64, 0, dummy, 10, None, None, None, st, None) == E     # m < 1
+    assert lib.nfft3_reduce_coords(64, 9, dummy, 10, None, None, None, st, None) == E     # m > 8
+    assert lib.nfft3_reduce_coords(64, 3, dummy, -1, None, None, None, st, None) == E     # M < 0
+    assert lib.nfft3_reduce_coords(64, 3, dummy, 10, None, None, None, None, None) == E   # no status word
+    assert lib.nfft3_reduce_coords(64, 3, None, 10, None, None, None, st, None) == E      # no x
