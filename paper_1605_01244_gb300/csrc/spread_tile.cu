@@ -330,35 +330,30 @@ cudaError_t spread_tile_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsVi
                                  const WinTableDF *wdf, const int4 *chunks, int nchunks, int nt2, int nt3,
                                  typename Cplx<R>::T *H, cudaStream_t st) {
     constexpr int B = kTile + 2 * MM;
-    if constexpr (sizeof(R) == 8) {
-        // FP64 family: the double-float kernel where its box and staged weights
-        // fit one SM's shared memory (m <= 7)
-        constexpr size_t smem_df = spread_df_smem<MM>();
-        if constexpr (smem_df <= 227 * 1024) {
-            if (!wdf) return cudaErrorInvalidValue;
-            auto kern = spread_tile_df_kernel<MM>;
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
-            if (e != cudaSuccess) return e;
-            kern<<<(unsigned)nchunks, 32 * B, smem_df, st>>>(f, g, pts, make_poly_df<MM>(*wdf), chunks, nt2,
-                                                              nt3, H);
-            return cudaGetLastError();
-        }
-    }
     if constexpr (sizeof(R) == 4) {
         constexpr size_t smem_f = spread_f32_smem<MM>();
         auto kern = spread_tile_f32_kernel<MM>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f);
         if (e != cudaSuccess) return e;
         kern<<<(unsigned)nchunks, 32 * B, smem_f, st>>>(f, g, pts, make_poly<float, MM>(w), chunks, nt2, nt3, H);
-        return cudaGetLastError();
+    } else if constexpr (spread_df_smem<MM>() <= 227 * 1024) {
+        // FP64 family: the double-float kernel where its box and staged weights
+        // fit one SM's shared memory (m <= 7)
+        constexpr size_t smem_df = spread_df_smem<MM>();
+        if (!wdf) return cudaErrorInvalidValue;
+        auto kern = spread_tile_df_kernel<MM>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)nchunks, 32 * B, smem_df, st>>>(f, g, pts, make_poly_df<MM>(*wdf), chunks, nt2, nt3, H);
+    } else {
+        // FP64 at m = 8: the box alone takes most of an SM's shared memory;
+        // FP64 shared-memory atomics, 512 threads
+        const size_t smem = 2 * sizeof(R) * (size_t)B * B * B;
+        auto kern = spread_tile_kernel<R, MM, 512>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)nchunks, 512, smem, st>>>(f, g, pts, make_poly<R, MM>(w), chunks, nt2, nt3, H);
     }
-    // FP64 at m = 8: the box takes most of an SM's shared memory, 512 threads
-    constexpr int THREADS = sizeof(R) == 8 ? 512 : 256;
-    const size_t smem = 2 * sizeof(R) * (size_t)B * B * B;
-    auto kern = spread_tile_kernel<R, MM, THREADS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<(unsigned)nchunks, THREADS, smem, st>>>(f, g, pts, make_poly<R, MM>(w), chunks, nt2, nt3, H);
     return cudaGetLastError();
 }
 
