@@ -344,6 +344,8 @@ def run_ours(args, rank, world, local):
     for fam in results:
         r = results[fam]
         r["rel_l2"] = float(np.linalg.norm(r["f_sub"] - fd) / np.linalg.norm(fd))
+        err = np.abs(r["f_sub"] - fd)
+        r["inf_err"] = {"abs": float(err.max()), "rel_to_max": float(err.max() / np.abs(fd).max())}
     cpu = None
     if not args.no_cpu_baseline:
         S = 8192          # about 10 s of direct summation on 16 Arm cores at N = 256^3
@@ -360,6 +362,7 @@ def run_ours(args, rank, world, local):
         return {
             "value": pts / (r["ms_per_step"] * 1e-3) / 1e6,
             "ms_per_step": r["ms_per_step"], "m": r["m"], "rel_l2_vs_oracle": r["rel_l2"],
+            "inf_err_vs_oracle": r["inf_err"],
             "eval_only_mpoints_s": pts / (r["ms_eval_only"] * 1e-3) / 1e6,
             "gradient_mpoints_s": {k: pts / (v * 1e-3) / 1e6 for k, v in r["grad_ms"].items()},
             "adjoint": {"mpoints_s": pts / (r["adj_ms"] * 1e-3) / 1e6, "ms": r["adj_ms"],
@@ -384,6 +387,7 @@ def run_ours(args, rank, world, local):
             "l2": "inputs larger than L2 (grid %.2f GB FP64), no flush" % ((2 * N) ** 3 * 16 / 1e9),
             "parallelism": "points sharded, no collective" if world > 1 else "single GPU"}),
         "rel_l2_vs_oracle": main["rel_l2_vs_oracle"],
+        "inf_err_vs_oracle": main["inf_err_vs_oracle"],
         "eval_only_mpoints_s": main["eval_only_mpoints_s"],
         "gradient_mpoints_s": main["gradient_mpoints_s"],
         "adjoint": main["adjoint"],
