@@ -15,6 +15,7 @@
 // the mixed family in FP32; the padded output is what the gathers expect
 // (float4 re_hi, re_lo, im_hi, im_lo, or float2).
 // With ng = 4 the same passes also produce the gradient grids 2 pi i k_d g.
+#include "fastdiv.cuh"
 #include "internal.cuh"
 
 #ifndef GBNFFT_F32_LINE_ELEMS
@@ -297,16 +298,6 @@ __device__ __forceinline__ ArithF32::C series_value(ArithF32, float2 c, float d,
 // padded ghost copy of primary position p (or -1), for 2m <= n
 __device__ __forceinline__ int ghost_of(int p, int n, int m2) { return p < m2 ? p + n : (p >= n ? p - n : -1); }
 
-// exact unsigned division by a runtime divisor d >= 1 for 32-bit dividends:
-// q = (umulhi(M, x) + x) >> s with s = ceil(log2 d), M = floor(2^32 (2^s - d) / d) + 1
-struct FastDiv {
-    unsigned M;
-    int s;
-    __device__ __forceinline__ unsigned div(unsigned x) const {
-        return (unsigned)(((unsigned long long)__umulhi(M, x) + x) >> s);
-    }
-};
-
 __device__ __forceinline__ int band_pos(int i, int N, int n) {   // k = i - N/2 -> l = k mod n
     const int k = i - N / 2;
     return k < 0 ? k + n : k;
@@ -318,14 +309,6 @@ struct FusedArgs {
     int m, shift, ng;
     FastDiv divN2, divN3;
 };
-
-FastDiv make_fastdiv(unsigned d) {
-    FastDiv f;
-    f.s = 0;
-    while ((1ull << f.s) < d) ++f.s;
-    f.M = (unsigned)((((1ull << f.s) - d) << 32) / d + 1);
-    return f;
-}
 
 // Pass 1: rows along l3 for the in-band (k1, k2); input c deconvolved.
 // A[q][i1 N2 + i2][l3].
