@@ -270,8 +270,10 @@ template <class A> __device__ __forceinline__ void load_twiddles(typename A::S *
     for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = src[i];
 }
 
-// deconvolved input value of grid q (0: c_k D; d = 1..3: 2 pi i k_d c_k D)
-__device__ __forceinline__ ArithDF::C series_value(ArithDF, double2 c, double d, int q, int kq) {
+// deconvolved input value of grid q (0: c_k D; d = 1..3: 2 pi i k_d c_k D);
+// the FP64 family's c enters scaled by 2^vs (range scaling, internal.cuh)
+__device__ __forceinline__ ArithDF::C series_value(ArithDF, double2 c, double d, int q, int kq, int vs) {
+    c = scale_value(c, vs);
     double re = c.x * d, im = c.y * d;
     if (q > 0) {
         const double f = 6.283185307179586476925286766559 * (double)kq;
@@ -284,7 +286,7 @@ __device__ __forceinline__ ArithDF::C series_value(ArithDF, double2 c, double d,
     split_df(im, o.ih, o.il);
     return o;
 }
-__device__ __forceinline__ ArithF32::C series_value(ArithF32, float2 c, float d, int q, int kq) {
+__device__ __forceinline__ ArithF32::C series_value(ArithF32, float2 c, float d, int q, int kq, int) {
     float re = c.x * d, im = c.y * d;
     if (q > 0) {
         const float f = 6.283185307179586476925286766559f * (float)kq;
@@ -308,6 +310,7 @@ struct FusedArgs {
     int logn1, logn2, logn3;
     int m, shift, ng;
     FastDiv divN2, divN3;
+    const int *vexp;   // FP64 family's range word (nullptr: no scaling)
 };
 
 // Pass 1: rows along l3 for the in-band (k1, k2); input c deconvolved.
@@ -327,6 +330,7 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_rows_kernel(
     const int64_t nrows = (int64_t)a.N1 * a.N2;
     const int64_t row0 = (int64_t)blockIdx.x * LPB;
     load_twiddles<A>(tws, tw3, L);
+    const int vs = value_shift(a.vexp);
     // the N3 deconvolved coefficients of each row, at their band positions
     // (the first pass reads the rest of the line as zero)
     for (int e = threadIdx.x; e < LPB * a.N3; e += blockDim.x) {
@@ -338,7 +342,7 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_rows_kernel(
         const int kq = q == 1 ? i1 - a.N1 / 2 : q == 2 ? i2 - a.N2 / 2 : i3 - a.N3 / 2;
         const R d = D1[i1] * D2[i2] * D3[i3];
         sm[line * LS + pidx<A>(band_pos(i3, a.N3, a.n3))] =
-            A::st(series_value(A{}, c[row * a.N3 + i3], d, q, kq));
+            A::st(series_value(A{}, c[row * a.N3 + i3], d, q, kq, vs));
     }
     __syncthreads();
     line_dft<A, LOGL>(sm, tws, LS, a.N3 / 2);
@@ -570,8 +574,9 @@ size_t fused_scratch_bytes(const int N[3], const int n[3], int ng, int prec) {
 template <typename R>
 cudaError_t launch_fused_series(const typename Cplx<R>::T *c, const int N[3], const int n[3], const R *D1,
                                 const R *D2, const R *D3, const void *const tw[3], void *scratch,
-                                void *P, int m, int shift, int ng, cudaStream_t st) {
+                                void *P, int m, int shift, int ng, const int *vexp, cudaStream_t st) {
     FusedArgs a;
+    a.vexp = vexp;
     a.N1 = N[0];
     a.N2 = N[1];
     a.N3 = N[2];
@@ -595,9 +600,9 @@ cudaError_t launch_fused_series(const typename Cplx<R>::T *c, const int N[3], co
 template cudaError_t launch_fused_series<double>(const double2 *, const int[3], const int[3],
                                                  const double *, const double *, const double *,
                                                  const void *const[3], void *, void *, int, int, int,
-                                                 cudaStream_t);
+                                                 const int *, cudaStream_t);
 template cudaError_t launch_fused_series<float>(const float2 *, const int[3], const int[3], const float *,
                                                 const float *, const float *, const void *const[3],
-                                                void *, void *, int, int, int, cudaStream_t);
+                                                void *, void *, int, int, int, const int *, cudaStream_t);
 
 }  // namespace gbnfft

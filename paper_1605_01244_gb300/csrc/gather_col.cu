@@ -287,7 +287,9 @@ __global__ void __launch_bounds__(256, GBNFFT_SLOT_MINB) gather_slot_df_kernel(
         df_add(T[0], T[1], orh, orl);
         df_add(T[2], T[3], oih, oil);
     }
-    if (valid && sub == 0) f[key.w] = make_double2((double)T[0] + (double)T[1], (double)T[2] + (double)T[3]);
+    if (valid && sub == 0)
+        f[key.w] = scale_value(make_double2((double)T[0] + (double)T[1], (double)T[2] + (double)T[3]),
+                               -value_shift(pts.vexp));
 }
 
 template <int MM, int NG, class Wt>
@@ -374,8 +376,7 @@ __global__ void __launch_bounds__(256, NG == 1 ? GBNFFT_DF_MINB : 2) gather_col_
             df_add(rh, rl, orh, orl);
             df_add(ih, il, oih, oil);
         }
-        out[q].x = (double)rh + (double)rl;
-        out[q].y = (double)ih + (double)il;
+        out[q] = scale_value(make_double2((double)rh + (double)rl, (double)ih + (double)il), -value_shift(pts.vexp));
     }
     if (valid && sub == 0) {
         if (NG == 1) {

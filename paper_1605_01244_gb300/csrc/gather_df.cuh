@@ -147,10 +147,9 @@ __global__ void __launch_bounds__(128) gather_df_kernel(const float4 *__restrict
     const int64_t o = key.w;
     double2 r[NG];
 #pragma unroll
-    for (int q = 0; q < NG; ++q) {
-        r[q].x = (double)acc[q][0] + (double)acc[q][1];
-        r[q].y = (double)acc[q][2] + (double)acc[q][3];
-    }
+    for (int q = 0; q < NG; ++q)
+        r[q] = scale_value(make_double2((double)acc[q][0] + (double)acc[q][1], (double)acc[q][2] + (double)acc[q][3]),
+                           -value_shift(pts.vexp));
     if (NG == 1) {
         f[o] = r[0];
     } else {

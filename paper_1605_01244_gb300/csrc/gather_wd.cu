@@ -117,8 +117,8 @@ __global__ void __launch_bounds__(256, 2) gather_wd_df_kernel(const float4 *__re
             df_add(R[q][0], R[q][1], o[0], o[1]);
             df_add(R[q][2], R[q][3], o[2], o[3]);
         }
-        out[q].x = (double)R[q][0] + (double)R[q][1];
-        out[q].y = (double)R[q][2] + (double)R[q][3];
+        out[q] = scale_value(make_double2((double)R[q][0] + (double)R[q][1], (double)R[q][2] + (double)R[q][3]),
+                             -value_shift(pts.vexp));
     }
     if (valid && sub == 0) {
         if (f) f[key.w] = out[0];

@@ -56,10 +56,15 @@ template <typename R, int MM> Poly<R, MM> make_poly(const WinTable<R> &t) {
 //   key[j] = (l0_1, l0_2, l0_3, original index); l0_d in [0, n_d) is the
 //   first stencil node (wrapped), the stencil is l0_d + {0..2m} mod n_d.
 //   s_d[j] in [0,1): tau of tap a is alpha - s_d - a.
+//   vexp: FP64 family only (nullptr otherwise): device word holding the
+//   exponent rank (value_rank) of the largest input magnitude of the call;
+//   the inputs entered the arithmetic scaled by 2^value_shift(vexp) and the
+//   results leave scaled back (see the range scaling below).
 template <typename R> struct PointsView {
     const int4 *key;
     const R *s1, *s2, *s3;
     int64_t M;
+    const int *vexp;
 };
 
 struct Grid3 {
@@ -89,10 +94,50 @@ template <int MM> PolyDF<MM> make_poly_df(const WinTableDF &t) {
     return p;
 }
 
+// ---- range scaling of the FP64 family ---------------------------------------
+// The FP64 family computes its window sums, transform and adjoint spread in
+// double-float (float pairs), whose exponent range is FP32's.  So that any
+// finite FP64 input is served, each call first finds the largest magnitude
+// among its input values (the coefficients c of eval / eval_grad /
+// precompute, the values f of adjoint) and scales every input by the exact
+// power of two 2^s that brings that magnitude into [1, 2); the results are
+// scaled back by 2^-s when they are written as FP64.  Scaling by a power of
+// two is exact, so an input already of order one gives the same bits as
+// without it.  After scaling, entries below 2^-100 of the largest are
+// dropped by split_df (their share of any result is below 2^-100 of the
+// result's scale), and no double-float intermediate comes near FP32's
+// overflow: for every plan the library accepts (N_d <= 4096, sigma >= 1.25,
+// m <= 8) the grid values are bounded by sum_k |c_k D(k)| 2 pi |k| < 2^64
+// and the window sums by 2^76.
+//
+// value_rank(bits of |v|) = floor(log2 |v|) + 1100 for finite nonzero v
+// (subnormals included), 0 for zero and kRankNonFinite for inf / NaN.
+constexpr int kRankNonFinite = 4000;
+__device__ __forceinline__ int value_rank(unsigned long long b) {
+    b &= 0x7FFFFFFFFFFFFFFFull;
+    const int e = (int)(b >> 52);
+    if (e == 0x7ff) return kRankNonFinite;
+    if (e > 0) return e + 77;                         // (e - 1023) + 1100
+    const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    return mant ? 89 - __clzll((long long)mant) : 0;  // (63 - clz) - 1074 + 1100
+}
+// the shift s of a call from its stored rank (0 when all inputs are zero or
+// one is not finite: those pass through unscaled)
+__device__ __forceinline__ int value_shift(const int *vexp) {
+    if (!vexp) return 0;
+    const int r = *vexp;
+    return (r == 0 || r >= kRankNonFinite) ? 0 : 1100 - r;
+}
+__device__ __forceinline__ double2 scale_value(double2 v, int s) {
+    return s ? make_double2(scalbn(v.x, s), scalbn(v.y, s)) : v;
+}
+__device__ __forceinline__ float2 scale_value(float2 v, int) { return v; }
+
 // Split an FP64 value into floats hi + lo without FP64 arithmetic: hi keeps
 // the leading 24 significant bits (exact truncation), lo is the remaining 29
 // bits rounded to a float, so hi + lo carries ~48 bits.  Values below 2^-100
-// in magnitude (never reached by the normalised grids) are flushed to zero.
+// in magnitude are flushed to zero; callers pass values scaled as above, so
+// the largest is of order one and nothing reaches FP32's overflow.
 __device__ __forceinline__ void split_df(double v, float &hi, float &lo) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const unsigned int sign = (unsigned int)(b >> 63) << 31;
@@ -129,7 +174,12 @@ size_t fused_scratch_bytes(const int N[3], const int n[3], int ng, int prec);
 template <typename R>
 cudaError_t launch_fused_series(const typename Cplx<R>::T *c, const int N[3], const int n[3], const R *D1,
                                 const R *D2, const R *D3, const void *const tw[3], void *scratch,
-                                void *P, int m, int shift, int ng, cudaStream_t st);
+                                void *P, int m, int shift, int ng, const int *vexp, cudaStream_t st);
+
+// ---- range scaling (range.cu) -----------------------------------------------
+// *rank = max(*rank, value_rank of each of the count doubles at v); the caller
+// zeroes *rank first.
+cudaError_t launch_value_rank(const double *v, int64_t count, int *rank, cudaStream_t st);
 
 // ---- launchers implemented in gather_df.cu ---------------------------------
 cudaError_t launch_grid_to_df(double2 *G, int64_t total, cudaStream_t st);
@@ -156,10 +206,17 @@ cudaError_t launch_gather_col_df(const float4 *G, Grid3 g, int m, PointsView<dou
 
 // ---- launchers implemented in kernels.cu (all enqueue on `st`) ------------
 
+// vexp (here and in launch_deconv_gather, launch_fused_series): the call's
+// range word; c enters scaled by 2^s, the adjoint's output leaves scaled by
+// 2^-s (nullptr: no scaling, the mixed family and the FP64-pipe paths).
 template <typename R>
 cudaError_t launch_deconv_scatter(const typename Cplx<R>::T *c, int N1, int N2, int N3,
                                   const R *D1, const R *D2, const R *D3, typename Cplx<R>::T *G,
-                                  Grid3 g, int with_grad, cudaStream_t st);
+                                  Grid3 g, int with_grad, const int *vexp, cudaStream_t st);
+
+// Force-load the deconvolve + scatter kernel and the 4-grid gather of cutoff
+// m on the current device (modules load lazily on first use otherwise).
+template <typename R> cudaError_t preload_grad_kernels(int m);
 
 template <typename R>
 cudaError_t launch_gather(const typename Cplx<R>::T *G, Grid3 g, int m, PointsView<R> pts,
@@ -183,7 +240,7 @@ cudaError_t launch_spread_tiles(const typename Cplx<R>::T *f, Grid3 g, int m, Po
 template <typename R>
 cudaError_t launch_deconv_gather(const typename Cplx<R>::T *H, Grid3 g, const R *D1, const R *D2,
                                  const R *D3, int N1, int N2, int N3, typename Cplx<R>::T *c,
-                                 cudaStream_t st);
+                                 const int *vexp, cudaStream_t st);
 
 // ---- launchers implemented in points.cu ------------------------------------
 

@@ -44,14 +44,16 @@ template <typename C> __device__ __forceinline__ C cmul_real(C z, decltype(z.x) 
 // zero elsewhere.  One block per grid row (l1, l2), threads along the
 // contiguous dimension l3; whether the row lies in the band |k1|, |k2| < N/2
 // is decided once per row.  With with_grad, four grids are written back to
-// back: G, then 2 pi i k_d G for d = 1..3.
+// back: G, then 2 pi i k_d G for d = 1..3.  With vexp (FP64 family) every
+// coefficient is first scaled by 2^value_shift(vexp).
 // ----------------------------------------------------------------------------
 template <typename R>
 __global__ void deconv_scatter_kernel(const typename Cplx<R>::T *__restrict__ c, int N1, int N2,
                                       int N3, const R *__restrict__ D1, const R *__restrict__ D2,
                                       const R *__restrict__ D3, typename Cplx<R>::T *__restrict__ G,
-                                      Grid3 g, int with_grad) {
+                                      Grid3 g, int with_grad, const int *__restrict__ vexp) {
     using C = typename Cplx<R>::T;
+    const int vs = value_shift(vexp);
     const int64_t total = (int64_t)g.n1 * g.n2 * g.n3;
     const R two_pi = (R)6.283185307179586476925286766559;
     const int64_t rows = (int64_t)g.n1 * g.n2;
@@ -84,7 +86,7 @@ __global__ void deconv_scatter_kernel(const typename Cplx<R>::T *__restrict__ c,
             v.y = 0;
             if (k3 != INT32_MIN) {
                 const int i3 = k3 + N3 / 2;
-                v = cmul_real(crow[i3], d12 * D3[i3]);
+                v = cmul_real(scale_value(crow[i3], vs), d12 * D3[i3]);
             }
             out[l3] = v;
             if (with_grad) {
@@ -163,24 +165,25 @@ __global__ void __launch_bounds__(128) gather_kernel(const typename Cplx<R>::T *
         if (++ia == g.n1) ia = 0;
     }
     const int64_t o = key.w;
+    const int vs = -value_shift(pts.vexp);
     if (NG == 1) {
         C r;
         r.x = acc[0][0];
         r.y = acc[0][1];
-        f[o] = r;
+        f[o] = scale_value(r, vs);
     } else {
         if (f) {
             C r;
             r.x = acc[0][0];
             r.y = acc[0][1];
-            f[o] = r;
+            f[o] = scale_value(r, vs);
         }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             C r;
             r.x = acc[d + 1][0];
             r.y = acc[d + 1][1];
-            grad[3 * o + d] = r;
+            grad[3 * o + d] = scale_value(r, vs);
         }
     }
 }
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(128) spread_kernel(const typename Cplx<R>::T *
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= pts.M) return;
     const int4 key = pts.key[j];
-    const C fv = f[key.w];
+    const C fv = scale_value(f[key.w], value_shift(pts.vexp));
     R w1[W], w2[W], w3[W];
     window_row<R, MM>(pts.s1[j], P.c[0], w1);
     window_row<R, MM>(pts.s2[j], P.c[1], w2);
@@ -229,13 +232,15 @@ __global__ void __launch_bounds__(128) spread_kernel(const typename Cplx<R>::T *
     }
 }
 
-// adjoint deconvolution: c[i] = H[k mod n] D1[i1] D2[i2] D3[i3], one thread per coefficient.
+// adjoint deconvolution: c[i] = H[k mod n] D1[i1] D2[i2] D3[i3], one thread per
+// coefficient; with vexp the result is scaled back by 2^-value_shift(vexp).
 template <typename R>
 __global__ void deconv_gather_kernel(const typename Cplx<R>::T *__restrict__ H, Grid3 g,
                                      const R *__restrict__ D1, const R *__restrict__ D2,
                                      const R *__restrict__ D3, int N1, int N2, int N3,
-                                     typename Cplx<R>::T *__restrict__ c) {
+                                     typename Cplx<R>::T *__restrict__ c, const int *__restrict__ vexp) {
     const int64_t total = (int64_t)N1 * N2 * N3;
+    const int vs = -value_shift(vexp);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int i3 = (int)(e % N3);
@@ -246,7 +251,7 @@ __global__ void deconv_gather_kernel(const typename Cplx<R>::T *__restrict__ H, 
         const int l2 = i2 - N2 / 2 < 0 ? i2 - N2 / 2 + g.n2 : i2 - N2 / 2;
         const int l3 = i3 - N3 / 2 < 0 ? i3 - N3 / 2 + g.n3 : i3 - N3 / 2;
         const R d = D1[i1] * D2[i2] * D3[i3];
-        c[e] = cmul_real(H[((int64_t)l1 * g.n2 + l2) * g.n3 + l3], d);
+        c[e] = scale_value(cmul_real(H[((int64_t)l1 * g.n2 + l2) * g.n3 + l3], d), vs);
     }
 }
 
@@ -302,11 +307,11 @@ cudaError_t spread_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsView<R>
 template <typename R>
 cudaError_t launch_deconv_scatter(const typename Cplx<R>::T *c, int N1, int N2, int N3,
                                   const R *D1, const R *D2, const R *D3, typename Cplx<R>::T *G,
-                                  Grid3 g, int with_grad, cudaStream_t st) {
+                                  Grid3 g, int with_grad, const int *vexp, cudaStream_t st) {
     const int threads = 128;
     const int64_t rows = (int64_t)g.n1 * g.n2;
     deconv_scatter_kernel<R><<<(unsigned)(rows < (1ll << 30) ? rows : (1ll << 30)), threads, 0, st>>>(
-        c, N1, N2, N3, D1, D2, D3, G, g, with_grad);
+        c, N1, N2, N3, D1, D2, D3, G, g, with_grad, vexp);
     return cudaGetLastError();
 }
 
@@ -343,18 +348,39 @@ cudaError_t launch_spread(const typename Cplx<R>::T *f, Grid3 g, int m, PointsVi
 template <typename R>
 cudaError_t launch_deconv_gather(const typename Cplx<R>::T *H, Grid3 g, const R *D1, const R *D2,
                                  const R *D3, int N1, int N2, int N3, typename Cplx<R>::T *c,
-                                 cudaStream_t st) {
+                                 const int *vexp, cudaStream_t st) {
     const int threads = 256;
     const int64_t total = (int64_t)N1 * N2 * N3;
     deconv_gather_kernel<R><<<grid_blocks(total, threads), threads, 0, st>>>(H, g, D1, D2, D3, N1,
-                                                                             N2, N3, c);
+                                                                             N2, N3, c, vexp);
     return cudaGetLastError();
 }
 
+// Load the kernels of deconvolve + scatter and the 4-grid gather for cutoff m
+// onto the current device now (CUDA loads modules lazily, on first use, and
+// a load may allocate device memory).
+template <typename R> cudaError_t preload_grad_kernels(int m) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, deconv_scatter_kernel<R>);
+    switch (m) {
+        case 1: if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gather_kernel<R, 1, 4>); break;
+        case 2: if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gather_kernel<R, 2, 4>); break;
+        case 3: if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gather_kernel<R, 3, 4>); break;
+        case 4: if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gather_kernel<R, 4, 4>); break;
+        case 5: if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gather_kernel<R, 5, 4>); break;
+        case 6: if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gather_kernel<R, 6, 4>); break;
+        case 7: if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gather_kernel<R, 7, 4>); break;
+        case 8: if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, gather_kernel<R, 8, 4>); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return e;
+}
+
 #define GBNFFT_INSTANTIATE(R)                                                                     \
+    template cudaError_t preload_grad_kernels<R>(int);                                            \
     template cudaError_t launch_deconv_scatter<R>(const Cplx<R>::T *, int, int, int, const R *,    \
                                                   const R *, const R *, Cplx<R>::T *, Grid3, int,  \
-                                                  cudaStream_t);                                   \
+                                                  const int *, cudaStream_t);                      \
     template cudaError_t launch_gather<R>(const Cplx<R>::T *, Grid3, int, PointsView<R>,          \
                                           const WinTable<R> &, Cplx<R>::T *, cudaStream_t);        \
     template cudaError_t launch_gather_grad<R>(const Cplx<R>::T *, Grid3, int, PointsView<R>,     \
@@ -364,6 +390,6 @@ cudaError_t launch_deconv_gather(const typename Cplx<R>::T *H, Grid3 g, const R 
                                           const WinTable<R> &, Cplx<R>::T *, cudaStream_t);        \
     template cudaError_t launch_deconv_gather<R>(const Cplx<R>::T *, Grid3, const R *, const R *, \
                                                  const R *, int, int, int, Cplx<R>::T *,           \
-                                                 cudaStream_t);
+                                                 const int *, cudaStream_t);
 
 }  // namespace gbnfft

@@ -314,6 +314,10 @@ void release(nfft3_plan p) {
     }
     dev_free(p->grid);
     dev_free(p->pgrid);
+    {
+        void *v = p->vexp;
+        dev_free(v);
+    }
     for (int d = 0; d < 3; ++d) dev_free(p->tw[d]);
     dev_free(p->fscratch);
     void *k = p->key;
@@ -441,6 +445,11 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
     }
     const int64_t nn = (int64_t)p->n[0] * p->n[1] * p->n[2];
     if (st == NFFT3_OK) {
+        void *v = nullptr;
+        st = dev_alloc(p, &v, 2 * sizeof(int));
+        p->vexp = (int *)v;
+    }
+    if (st == NFFT3_OK) {
         p->grid_count = 1;
         st = dev_alloc(p, &p->grid, 2 * rs * nn);
     }
@@ -507,6 +516,7 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int4) * (M + 1)), p->key = (int4 *)v;
         for (int d = 0; d < 3 && st == NFFT3_OK; ++d) st = dev_alloc(p, &p->s[d], rs * (M + 1));
     }
+    if (st == NFFT3_OK) st = noalloc_setup(p);
     if (st != NFFT3_OK) {
         release(p);
         return st;
@@ -515,6 +525,10 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
     return warn;
 }
 
+// Range word of the forward calls (FP64 family; nullptr for the mixed family).
+const int *fwd_vexp(nfft3_plan p) { return p->prec == 64 ? p->vexp : nullptr; }
+
+// Points of the plan, with the forward range word; the adjoint substitutes its own.
 template <typename R> PointsView<R> points_view(nfft3_plan p) {
     PointsView<R> v;
     v.key = p->key;
@@ -522,8 +536,24 @@ template <typename R> PointsView<R> points_view(nfft3_plan p) {
     v.s2 = (const R *)p->s[1];
     v.s3 = (const R *)p->s[2];
     v.M = p->M;
+    v.vexp = sizeof(R) == 8 ? fwd_vexp(p) : nullptr;
     return v;
 }
+
+// FP64 family: record the exponent rank of the largest of `count` complex
+// input values in p->vexp[slot] (0: coefficients, 1: adjoint values), so the
+// call's kernels can scale its double-float arithmetic into range.
+int range_scan(nfft3_plan p, int slot, const void *values, int64_t count) {
+    if (p->prec != 64) return NFFT3_OK;
+    if (cudaMemsetAsync(p->vexp + slot, 0, sizeof(int), p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
+    if (count <= 0) return NFFT3_OK;
+    if (launch_value_rank((const double *)values, 2 * count, p->vexp + slot, p->stream) != cudaSuccess)
+        return NFFT3_ERR_CUDA;
+    p->launches += 1;
+    return NFFT3_OK;
+}
+
+int64_t num_coeffs(nfft3_plan p) { return (int64_t)p->N[0] * p->N[1] * p->N[2]; }
 
 int exec_fft(cufftHandle h, void *data, int prec, int direction) {
     cufftResult r;
@@ -696,7 +726,8 @@ template <typename R> int fused_transform(nfft3_plan p, const R *c, int ng, bool
     const void *tw[3] = {p->tw[0], p->tw[1], p->tw[2]};
     const cudaError_t e = launch_fused_series<R>(
         (const typename Cplx<R>::T *)c, p->N, p->n, (const R *)p->D[0], (const R *)p->D[1],
-        (const R *)p->D[2], tw, p->fscratch, p->pgrid, p->m, pad_shift(p, ng, allow_tile), ng, p->stream);
+        (const R *)p->D[2], tw, p->fscratch, p->pgrid, p->m, pad_shift(p, ng, allow_tile), ng, fwd_vexp(p),
+        p->stream);
     p->launches += 3;
     return cuda_status(e);
 }
@@ -726,10 +757,12 @@ template <typename R> int eval_impl(nfft3_plan p, const R *c, R *f) {
     C *G = (C *)p->grid;
     p->stored_ng = 0;
     const int rec = rec_begin(p, kRecEval);
+    const int rs = range_scan(p, 0, c, num_coeffs(p));
+    if (rs != NFFT3_OK) return rs;
     if (p->fused) return fused_eval<R>(p, c, f, nullptr, 1, rec);
     cudaError_t e = launch_deconv_scatter<R>((const C *)c, p->N[0], p->N[1], p->N[2],
                                              (const R *)p->D[0], (const R *)p->D[1],
-                                             (const R *)p->D[2], G, g, 0, p->stream);
+                                             (const R *)p->D[2], G, g, 0, fwd_vexp(p), p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     rec_mark(p, rec, 1);
     int st = exec_grid_fft(p, G, prec, CUFFT_INVERSE, 1);
@@ -780,7 +813,10 @@ template <typename R> int eval_grad_impl(nfft3_plan p, const R *c, R *f, R *grad
     if (p->M == 0) return NFFT3_OK;
     if (p->fused) {
         p->stored_ng = 0;
-        return fused_eval<R>(p, c, f, grad, 4, rec_begin(p, kRecGrad));
+        const int rec = rec_begin(p, kRecGrad);
+        const int rs = range_scan(p, 0, c, num_coeffs(p));
+        if (rs != NFFT3_OK) return rs;
+        return fused_eval<R>(p, c, f, grad, 4, rec);
     }
     int st = ensure_grad_grids<R>(p);
     if (st != NFFT3_OK) return st;
@@ -788,9 +824,11 @@ template <typename R> int eval_grad_impl(nfft3_plan p, const R *c, R *f, R *grad
     C *G = (C *)p->grid;
     p->stored_ng = 0;
     const int rec = rec_begin(p, kRecGrad);
+    st = range_scan(p, 0, c, num_coeffs(p));
+    if (st != NFFT3_OK) return st;
     cudaError_t e = launch_deconv_scatter<R>((const C *)c, p->N[0], p->N[1], p->N[2],
                                              (const R *)p->D[0], (const R *)p->D[1],
-                                             (const R *)p->D[2], G, g, 1, p->stream);
+                                             (const R *)p->D[2], G, g, 1, fwd_vexp(p), p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     rec_mark(p, rec, 1);
     st = exec_grid_fft(p, G, prec, CUFFT_INVERSE, 4);
@@ -810,8 +848,12 @@ template <typename R> int precompute_impl(nfft3_plan p, const R *c, int with_gra
     constexpr int prec = sizeof(R) == 8 ? 64 : 32;
     if (!p || p->prec != prec || !c || (p->gather_mode != 0 && p->gather_mode != 3)) return NFFT3_ERR_ARG;
     const int ng = with_grad ? 4 : 1;
+    p->stored_ng = 0;
+    {
+        const int rs = range_scan(p, 0, c, num_coeffs(p));
+        if (rs != NFFT3_OK) return rs;
+    }
     if (p->fused) {
-        p->stored_ng = 0;
         const int st = fused_transform<R>(p, c, ng);
         if (st != NFFT3_OK) return st;
         p->stored_ng = ng;
@@ -826,7 +868,7 @@ template <typename R> int precompute_impl(nfft3_plan p, const R *c, int with_gra
     C *G = (C *)p->grid;
     cudaError_t e = launch_deconv_scatter<R>((const C *)c, p->N[0], p->N[1], p->N[2],
                                              (const R *)p->D[0], (const R *)p->D[1],
-                                             (const R *)p->D[2], G, g, ng == 4, p->stream);
+                                             (const R *)p->D[2], G, g, ng == 4, fwd_vexp(p), p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     st = exec_grid_fft(p, G, prec, CUFFT_INVERSE, ng);
     if (st != NFFT3_OK) return st;
@@ -876,14 +918,17 @@ template <typename R> cudaError_t gather_wd(nfft3_plan p, R *f, R *grad) {
 // deconvolution + cuFFT + padding.
 template <typename R> int series_to_origin_pgrid(nfft3_plan p, const R *c) {
     using C = typename Cplx<R>::T;
+    int st = range_scan(p, 0, c, num_coeffs(p));
+    if (st != NFFT3_OK) return st;
     if (p->fused) return fused_transform<R>(p, c, 1, false);
-    int st = ensure_pgrid(p, 1);
+    st = ensure_pgrid(p, 1);
     if (st != NFFT3_OK) return st;
     const Grid3 g{p->n[0], p->n[1], p->n[2]};
     const Grid3 pg{g.n1 + 2 * p->m, g.n2 + 2 * p->m, g.n3 + 2 * p->m};
     C *G = (C *)p->grid;
     cudaError_t e = launch_deconv_scatter<R>((const C *)c, p->N[0], p->N[1], p->N[2], (const R *)p->D[0],
-                                             (const R *)p->D[1], (const R *)p->D[2], G, g, 0, p->stream);
+                                             (const R *)p->D[1], (const R *)p->D[2], G, g, 0, fwd_vexp(p),
+                                             p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     st = exec_grid_fft(p, G, sizeof(R) == 8 ? 64 : 32, CUFFT_INVERSE, 1);
     if (st != NFFT3_OK) return st;
@@ -941,21 +986,26 @@ template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
     C *H = (C *)p->grid;
     p->stored_ng = 0;
     const int rec = rec_begin(p, kRecAdjoint);
+    // FP64 family: f's range word, used by the spread (input) and the deconvolution (output)
+    const int *avexp = prec == 64 ? p->vexp + 1 : nullptr;
+    int st = range_scan(p, 1, f, p->M);
+    if (st != NFFT3_OK) return st;
+    PointsView<R> pv = points_view<R>(p);
+    pv.vexp = avexp;
     cudaError_t e = cudaMemsetAsync(H, 0, sizeof(C) * nn, p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     if (!p->spread_direct && p->nchunks > 0)
-        e = launch_spread_tiles<R>((const C *)f, g, p->m, points_view<R>(p), win_table<R>(p),
-                                   prec == 64 ? &p->wtdf : nullptr, p->pb.chunks, p->nchunks, p->pb.nt2,
-                                   p->pb.nt3, H, p->stream);
+        e = launch_spread_tiles<R>((const C *)f, g, p->m, pv, win_table<R>(p), prec == 64 ? &p->wtdf : nullptr,
+                                   p->pb.chunks, p->nchunks, p->pb.nt2, p->pb.nt3, H, p->stream);
     else
-        e = launch_spread<R>((const C *)f, g, p->m, points_view<R>(p), win_table<R>(p), H, p->stream);
+        e = launch_spread<R>((const C *)f, g, p->m, pv, win_table<R>(p), H, p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     rec_mark(p, rec, 1);
-    int st = exec_grid_fft(p, H, prec, CUFFT_FORWARD, 1);
+    st = exec_grid_fft(p, H, prec, CUFFT_FORWARD, 1);
     if (st != NFFT3_OK) return st;
     rec_mark(p, rec, 2);
     e = launch_deconv_gather<R>(H, g, (const R *)p->D[0], (const R *)p->D[1], (const R *)p->D[2],
-                                p->N[0], p->N[1], p->N[2], (C *)c_out, p->stream);
+                                p->N[0], p->N[1], p->N[2], (C *)c_out, avexp, p->stream);
     rec_mark(p, rec, 3);
     rec_end(p, rec, 3);
     p->launches += p->M > 0 ? 2 : 1;

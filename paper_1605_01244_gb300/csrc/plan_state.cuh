@@ -34,6 +34,10 @@ struct nfft3_plan_s {
     int pgrid_count;
     int pgrid_shift;          // layout shift of its current contents (0 or m)
     int stored_ng;            // grids precomputed by nfft3*_precompute (0: none valid)
+    // FP64 family range scaling: device words with the exponent rank of the
+    // largest input of the current call; [0] coefficients (eval, eval_grad,
+    // precompute; read again by the stored gathers), [1] adjoint values
+    int *vexp;
     alignas(64) unsigned char tmap[128];  // CUtensorMap of the padded FP32 grid (tile-staged gather)
     int tmap_ok;
     int nchunks;              // chunks of the tile-staged gather for the current points
@@ -74,3 +78,7 @@ struct nfft3_plan_s {
     int64_t stage_calls[NFFT3_NSTAGES];
     int64_t launches;         // kernels this library enqueued (cuFFT's own not counted)
 };
+
+// Set-up of the allocation-free entry point on the plan's device (noalloc.cu):
+// run by plan creation for FP64 plans; a no-op for plans it cannot serve.
+int noalloc_setup(nfft3_plan p);

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(THREADS, 1) spread_tile_kernel(const typename 
     for (int i = threadIdx.x >> 5; i < ch.z; i += THREADS / 32) {
         const int64_t j = (int64_t)ch.y + i;
         const int4 key = pts.key[j];
-        const C fv = f[key.w];
+        const C fv = scale_value(f[key.w], value_shift(pts.vexp));
         // lane a < W: the weight of tap a in each dimension (Horner in t = 2s - 1)
         R w[3];
         {
@@ -194,7 +194,8 @@ __global__ void __launch_bounds__(32 * (kTile + 2 * MM), 1) spread_tile_df_kerne
     }
     for (int i = threadIdx.x; i < ch.z; i += THREADS) {
         const int4 key = pts.key[(int64_t)ch.y + i];
-        const double2 fv = f[key.w];
+        // FP64 family: f enters scaled by 2^s, so the float pairs keep its range
+        const double2 fv = scale_value(f[key.w], value_shift(pts.vexp));
         const float2 re = df2_split(fv.x), im = df2_split(fv.y);
         fsm[i] = make_float4(re.x, re.y, im.x, im.y);
         osm[i] = make_int4(tile_centre(key.x, MM, g.n1) - kTile * tt1, tile_centre(key.y, MM, g.n2) - kTile * tt2,
