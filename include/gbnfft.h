@@ -28,9 +28,19 @@
  *   f    : M complex values (same real type as c).
  *   grad : M*3 complex values, grad[3j+d] = d f_j / d x_{j,d}.
  *
- * Families: nfft3d_* computes in FP64 throughout.  nfft3f_* ("mixed") keeps
- * the coordinate reduction and the deconvolution tables in FP64 and runs the
- * grid, FFT, window sums and spreading in FP32.
+ * Families: nfft3d_* ("FP64") takes and returns FP64 values and meets an
+ * FP64 accuracy class (relative l2 error <= 1e-12 at m >= 6, sigma = 2),
+ * but its transform, window sums and adjoint spread run in double-float
+ * arithmetic: pairs of floats carrying about 48 significant bits, on the
+ * FP32 pipe (GB300's FP64 pipe is 64x slower).  The coordinate reduction,
+ * the deconvolution tables and the adjoint's FFT and final deconvolution are
+ * FP64.  Range: every call scales its input values (c, or f for the adjoint)
+ * by the exact power of two that brings the largest magnitude into [1, 2),
+ * and scales its results back, so any finite FP64 input is served; input
+ * entries below 2^-100 of the largest are dropped (their share of any result
+ * is below 2^-100 of its scale).  nfft3f_* ("mixed") keeps the coordinate
+ * reduction and the deconvolution tables in FP64 and runs the grid, FFT,
+ * window sums and spreading in FP32, with FP32's range.
  *
  * Ownership: the plan owns all device workspaces.  Pointers passed to a call
  * are borrowed for the duration of the call (the work is enqueued on the
@@ -153,13 +163,19 @@ int nfft3f_eval_grad_window_stored(nfft3_plan p, float *f, float *grad);
  * loop that cannot take cudaMalloc's implicit device synchronisation.
  * nfft3d_eval_grad allocates its four gradient grids on first use; this
  * variant computes the same f and grad (same layout and meaning) with those
- * grids in a fixed 16 MiB device array compiled into the library (every GPU
- * that loads the library holds it until the process exits).  It calls no
- * cudaMalloc, cudaFree or allocating library routine.
+ * grids in a fixed 16 MiB device array compiled into the library.  It calls
+ * no cudaMalloc, cudaFree or allocating library routine, and it loads no
+ * device code: CUDA loads a library's device code lazily, and loading the
+ * code that holds the array is what creates the array on a device, so the
+ * set-up happens when an FP64 plan whose grids fit is created
+ * (nfft3d_plan looks up the array's device address with
+ * cudaGetSymbolAddress, loads the kernels this call launches and runs the
+ * plan's FFT once).  From the first such plan on, the device holds the
+ * 16 MiB until the process exits.  Create the plan before any stream
+ * capture.
  *   Limit: 4 * n1*n2*n3 complex doubles must fit, i.e. n1*n2*n3 <= 262144
- *   (64^3); larger plans get NFFT3_ERR_TOO_LARGE.  FP64 plans only.
- *   The first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   (64^3); larger plans get NFFT3_ERR_TOO_LARGE.  FP64 plans only
+ *   (NFFT3_ERR_ARG for a mixed plan).
  *   All calls share the array: calls whose work overlaps on the GPU (other
  *   streams or host threads) race and give wrong results.  Each call rewrites
  *   every grid element before reading it, so leftover contents are harmless.
