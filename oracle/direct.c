@@ -170,6 +170,49 @@ void oracle_adjoint(int N1, int N2, int N3, int64_t M, const double *x,
     }
 }
 
+/*
+ * Adjoint at selected frequencies: h_q = sum_j f_j exp(-2 pi i k_q.x_j) for
+ * the nk frequency triples k (nk x 3 ints, each k_d any integer), over all M
+ * points, for checking large adjoints on a sample of their outputs.  Each
+ * phase k_d x_d is formed with an error-free product and reduced mod 1, the
+ * three are added and reduced again, and the sum over j is compensated
+ * (Neumaier), so the result stays accurate to rounding for M = 10^7.
+ */
+static void neumaier(double *s, double *comp, double v)
+{
+    double t = *s + v;
+    if (fabs(*s) >= fabs(v))
+        *comp += (*s - t) + v;
+    else
+        *comp += (v - t) + *s;
+    *s = t;
+}
+
+void oracle_adjoint_at(int nk, const int *k, int64_t M, const double *x,
+                       const double *f, double *h)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int q = 0; q < nk; q++) {
+        double sr = 0, cr = 0, si = 0, ci = 0;
+        for (int64_t j = 0; j < M; j++) {
+            double r = 0;
+            for (int d = 0; d < 3; d++) {
+                double kd = (double)k[3 * q + d];
+                double p = kd * x[3 * j + d];
+                double e = fma(kd, x[3 * j + d], -p);   /* k_d x_d = p + e exactly */
+                r += (p - nearbyint(p)) + e;            /* each term in [-1/2, 1/2] */
+            }
+            r -= nearbyint(r);
+            double er = cos(TWO_PI * r), ei = -sin(TWO_PI * r);
+            double fr = f[2 * j], fi = f[2 * j + 1];
+            neumaier(&sr, &cr, fr * er - fi * ei);
+            neumaier(&si, &ci, fr * ei + fi * er);
+        }
+        h[2 * q] = sr + cr;
+        h[2 * q + 1] = si + ci;
+    }
+}
+
 /* Number of OpenMP threads the oracle runs with (for reporting). */
 int oracle_num_threads(void)
 {

@@ -99,6 +99,34 @@ def test_adjoint_single_point_closed_form():
     assert np.max(np.abs(h - ref)) <= 1e-14
 
 
+def test_adjoint_at_selected_frequencies():
+    """The sampled-frequency adjoint (one compensated sum over all points per
+    k) against the separable full adjoint at every k of a small band, the
+    closed form of one point at frequencies far outside any band, and a
+    40-digit brute force of a few terms."""
+    N = (4, 6, 8)
+    x = wl.mixed_points(300, 0.05, seed=41)
+    g = wl.rng(42)
+    f = g.standard_normal(300) + 1j * g.standard_normal(300)
+    k1, k2, k3 = wl.freq_grid(N)
+    ks = np.stack(np.broadcast_arrays(k1, k2, k3), -1).reshape(-1, 3)
+    h = oracle.adjoint_at(f, x, ks)
+    hf = oracle.adjoint(f, x, N).reshape(-1)
+    assert np.max(np.abs(h - hf)) <= 1e-13 * np.max(np.abs(hf))
+    big = np.array([[1000, -37, 2 ** 20], [-(2 ** 24), 5, 0], [0, 0, 0]])
+    xp = np.array([[0.1234, -0.377, 0.4101]])
+    h1 = oracle.adjoint_at(np.array([1.0 + 0j]), xp, big)
+    with mpmath.workdps(40):
+        for q in range(3):
+            ph = sum(int(big[q, d]) * mpmath.mpf(float(xp[0, d])) for d in range(3))
+            ref = complex(mpmath.exp(-2j * mpmath.pi * ph))
+            assert abs(h1[q] - ref) <= 1e-15
+    # many equal terms: compensated summation keeps the exact multiple
+    xs = np.tile(np.array([[0.25, 0.0, 0.0]]), (100000, 1))
+    hs = oracle.adjoint_at(np.full(100000, 0.1 + 0j), xs, np.array([[1, 0, 0]]))
+    assert abs(hs[0] - (-1j * 0.1 * 100000)) <= 1e-15 * 1e4
+
+
 def test_brute_force_high_precision():
     N = (4, 4, 6)
     c = wl.gaussian_coeffs(N, 2.0, seed=11)
