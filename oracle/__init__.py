@@ -11,11 +11,15 @@ Contents
     Plain FP64 direct sums, the authority for parity:
     forward  f_j = sum_k c_k e^{+2 pi i k.x_j}     (paper eq. (fs)/(Fs), Sec. 2.2)
     gradient d_d f_j = sum_k 2 pi i k_d c_k e^{..} (paper eq. (Lambda))
-    adjoint  h_k = sum_j f_j e^{-2 pi i k.x_j}     (transpose of the above)
+    adjoint  h_k = sum_j f_j e^{-2 pi i k.x_j}     (transpose of the above; also at
+                                                    selected k over many points)
 ``nfft_cpu.py``
     A plain, unblocked numpy restatement of the NFFT approximation of the
     same sums (deconvolve / oversampled FFT / window sum), used to pin the
     window mathematics and as a same-algorithm reference.
+``nfft_omp.c`` + ``cpu_nfft.py``
+    The plain CPU NFFT (OpenMP C steps, scipy's FFT), the timed CPU baseline
+    of the method.
 ``mp_reference.py``
     Arbitrary-precision brute force for tiny cases (pins the C direct sum).
 
@@ -39,19 +43,25 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile ``direct.c`` with gcc/OpenMP into ``_build/liboracle.so``."""
-    src = os.path.join(_HERE, "direct.c")
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
-        return _SO
+def _compile(src: str, so: str, force: bool) -> str:
+    if not force and os.path.exists(so) and os.path.getmtime(so) >= os.path.getmtime(src):
+        return so
     os.makedirs(_BUILD, exist_ok=True)
-    tmp = _SO + ".tmp%d" % os.getpid()
+    tmp = so + ".tmp%d" % os.getpid()
     # No -ffast-math: the oracle keeps IEEE semantics and the libm cos/sin.
     cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
-           "-fno-fast-math", src, "-o", tmp, "-lm"]
+           "-fno-fast-math", "-ffp-contract=off", src, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
+
+
+def build(force: bool = False) -> str:
+    """Compile ``direct.c`` (``_build/liboracle.so``) and the plain CPU NFFT
+    ``nfft_omp.c`` (``_build/libcpunfft.so``) with gcc/OpenMP; returns the
+    direct-sum library's path."""
+    _compile(os.path.join(_HERE, "nfft_omp.c"), os.path.join(_BUILD, "libcpunfft.so"), force)
+    return _compile(os.path.join(_HERE, "direct.c"), _SO, force)
 
 
 def _load():
@@ -66,6 +76,9 @@ def _load():
             lib.oracle_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int64, dp, dp, dp]
             lib.oracle_adjoint.restype = None
+            lib.oracle_adjoint_at.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int64,
+                                              dp, dp, dp]
+            lib.oracle_adjoint_at.restype = None
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -119,6 +132,21 @@ def adjoint(f, x, N) -> np.ndarray:
         raise ValueError("f and x disagree on M")
     h = np.zeros(N, dtype=np.complex128)
     _load().oracle_adjoint(*N, x.shape[0], _dptr(x), _dptr(f), _dptr(h))
+    return h
+
+
+def adjoint_at(f, x, k) -> np.ndarray:
+    """Direct FP64 adjoint at selected frequencies: h_q = sum_j f_j exp(-2 pi i k_q.x_j)
+    for the integer triples k (nk, 3), over all points, with compensated sums."""
+    f = np.ascontiguousarray(f, dtype=np.complex128).reshape(-1)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    k = np.ascontiguousarray(k, dtype=np.int32).reshape(-1, 3)
+    if f.shape[0] != x.shape[0]:
+        raise ValueError("f and x disagree on M")
+    h = np.zeros(k.shape[0], dtype=np.complex128)
+    if k.shape[0]:
+        _load().oracle_adjoint_at(k.shape[0], k.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), x.shape[0],
+                                  _dptr(x), _dptr(f), _dptr(h))
     return h
 
 
