@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the eps sweep and the GPE-snapshot workload (run at N=1 only)")
     ap.add_argument("--points", type=int, default=M_POINTS)
     ap.add_argument("--n", type=int, default=N_EDGE)
     return ap.parse_args()
@@ -169,6 +171,141 @@ def workload_config(N: int, M: int) -> dict:
     return {"workload": "precision sweep: N=%d^3 gaussian(40) coefficients, M=%d points (half uniform, "
                         "half gaussian std 0.02), sigma=2" % (N, M),
             "N": N, "M_per_gpu": M, "sigma": 2.0, "m_fp64": M_FP64, "m_mixed": M_MIXED}
+
+
+SWEEP_EPS = (1e-4, 1e-6, 1e-10, 1e-13)
+
+
+def timed_set_points_eval(plan, x, c, f, steps, s):
+    """ms per set_points + eval, CUDA events on the plan's stream."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(steps):
+        plan.set_points(x)
+        plan.eval(c, out=f)
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_sweep(c_np, x, idx, fd, dev, s, steps):
+    """The precision sweep: for each eps target and family, the plan's own m
+    rule (nfft3_choose_m), Mpoints/s of set_points + eval and the errors on
+    the fixed subsample against the FP64 direct sum."""
+    import torch
+    from paper_1605_01244_gb300.nfft import Plan, choose_m
+    N = c_np.shape[0]
+    M = x.shape[0]
+    out = []
+    sel = torch.from_numpy(idx).to(dev)
+    for fam, cdt, gate in (("f64", torch.complex128, 1e-12), ("f32", torch.complex64, 1e-6)):
+        c = torch.from_numpy(c_np).to(cdt).to(dev)
+        f = torch.empty(M, dtype=cdt, device=dev)
+        for eps in SWEEP_EPS:
+            m = choose_m(eps)
+            plan = Plan((N, N, N), M, m=m, sigma=2.0, precision=fam)
+            plan.set_points(x)
+            plan.eval(c, out=f)
+            ms = timed_set_points_eval(plan, x, c, f, steps, s)
+            fs = f[sel].cpu().numpy().astype(np.complex128)
+            err = float(np.linalg.norm(fs - fd) / np.linalg.norm(fd))
+            einf = float(np.abs(fs - fd).max() / np.abs(fd).max())
+            row = {"eps": eps, "family": fam, "m": m, "mpoints_s": M / (ms * 1e-3) / 1e6, "ms": ms,
+                   "rel_l2": err, "inf_err_rel_to_max": einf, "reached": err <= eps}
+            if not row["reached"]:
+                row["note"] = ("not reachable in FP32: floor %.1e" % err if fam == "f32"
+                               else "above eps at the rule's m")
+            out.append(row)
+            plan.close()
+        del c, f
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_gpe_snapshot(dev, s, steps):
+    """The GPE-snapshot workload: N = 128^3 two-vortex coefficients, 100^3
+    lattice points in the physical box [-0.025, 0.025]^3 plus 10^6 uniform
+    points; Mpoints/s of set_points + eval for both families and the errors on
+    2000 sampled points (1000 of each population) against the direct sum."""
+    import torch
+    import oracle
+    from paper_1605_01244_gb300 import workloads as wl
+    from paper_1605_01244_gb300.nfft import Plan
+    c_np, x_np = wl.gpe_snapshot()
+    M = len(x_np)
+    n_lat = 100 ** 3
+    idx = np.concatenate([wl.rng(97).choice(n_lat, 1000, replace=False),
+                          n_lat + wl.rng(96).choice(M - n_lat, 1000, replace=False)])
+    x = torch.from_numpy(x_np).to(dev)
+    res = {"workload": "GPE snapshot: N=128^3 two-vortex coefficients (L=8), 100^3 lattice points in the "
+                       "physical box [-0.025,0.025]^3 + 10^6 uniform points, sigma=2", "M": M}
+    fsubs = {}
+    for fam, m, cdt in (("f64", M_FP64, torch.complex128), ("f32", M_MIXED, torch.complex64)):
+        c = torch.from_numpy(c_np).to(cdt).to(dev)
+        f = torch.empty(M, dtype=cdt, device=dev)
+        plan = Plan(c_np.shape, M, m=m, sigma=2.0, precision=fam)
+        plan.set_points(x)
+        plan.eval(c, out=f)
+        ms = timed_set_points_eval(plan, x, c, f, steps, s)
+        fsubs[fam] = f[torch.from_numpy(idx).to(dev)].cpu().numpy().astype(np.complex128)
+        res[fam] = {"m": m, "mpoints_s": M / (ms * 1e-3) / 1e6, "ms": ms}
+        plan.close()
+        del c, f
+    fd = oracle.forward(c_np, x_np[idx])
+    for fam, fs in fsubs.items():
+        res[fam]["rel_l2"] = float(np.linalg.norm(fs - fd) / np.linalg.norm(fd))
+    del x
+    torch.cuda.empty_cache()
+    return res
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def run_cpu_nfft(c3, fd3):
+    """The plain CPU NFFT (FP64, m = 6, sigma = 2; OpenMP C steps around
+    scipy's FFT) on the host cores: configs 1-3 in full on all cores, and on
+    one core with the window gather timed on at most 200,000 points and scaled
+    to the full point count (deconvolution and FFT always on the full grid)."""
+    from oracle import cpu_nfft
+    from paper_1605_01244_gb300 import workloads as wl
+    cores = cpu_nfft.host_cores()
+    c1, x1 = wl.small_random()
+    c2, x2 = wl.gpe_snapshot()
+    cases = (("config 1: N=16^3, M=1000", c1, x1), ("config 2: GPE snapshot, N=128^3, M=2e6", c2, x2),
+             ("config 3: precision sweep, N=256^3, M=1e7", c3[0], c3[1]))
+    out = {"kind": "cpu_nfft", "unit": "Mpoints/s", "cores": cores, "cpu_model": cpu_model(), "m": M_FP64,
+           "sigma": 2.0, "fft": "scipy.fft (pocketfft), workers = cores", "dtype": "f64", "configs": []}
+    for name, c, x in cases:
+        n = tuple(2 * v for v in c.shape)
+        M = len(x)
+        f, t = cpu_nfft.forward(c, x, n, M_FP64, threads=cores)
+        row = {"config": name, "all_cores": {"value": M / sum(t.values()) / 1e6, "seconds": t}}
+        S = min(M, 200_000)
+        _, t1 = cpu_nfft.forward(c, x[:S], n, M_FP64, threads=1)
+        full1 = t1["tables"] + t1["deconv"] + t1["fft"] + t1["gather"] * M / S
+        row["one_core"] = {"value": M / full1 / 1e6, "seconds": t1,
+                           "sample": "gather on %d of %d points, scaled" % (S, M) if S < M else "full"}
+        if fd3 is not None and c is c3[0]:
+            fs = f[c3[2]]
+            row["rel_l2_vs_oracle"] = float(np.linalg.norm(fs - fd3) / np.linalg.norm(fd3))
+        out["configs"].append(row)
+        del f
+    main = out["configs"][-1]
+    out["value"] = main["all_cores"]["value"]
+    out["sample"] = "config 3 in full on %d cores (%.1f s); per-config rows also on one core" % (
+        cores, sum(main["all_cores"]["seconds"].values()))
+    return out
 
 
 def run_ours(args, rank, world, local):
@@ -341,6 +478,11 @@ def run_ours(args, rank, world, local):
 
     import oracle
     fd = oracle.forward(c_np, x_np[results["f64"]["idx"]])
+    extras = {}
+    if world == 1 and not args.no_extras:
+        s = torch.cuda.current_stream(dev)
+        extras["sweep"] = run_sweep(c_np, x, results["f64"]["idx"], fd, dev, s, min(args.steps, 3))
+        extras["gpe_snapshot"] = run_gpe_snapshot(dev, s, min(args.steps, 3))
     for fam in results:
         r = results[fam]
         r["rel_l2"] = float(np.linalg.norm(r["f_sub"] - fd) / np.linalg.norm(fd))
@@ -355,6 +497,8 @@ def run_ours(args, rank, world, local):
         dt = time.perf_counter() - t0
         cpu = {"value": S / dt / 1e6, "unit": "Mpoints/s", "cores": oracle.num_threads(),
                "kind": "oracle", "sample": "%d uniform points of the workload, FP64 direct sum at N=256^3 (%.1f s)" % (S, dt)}
+        if world == 1 and not args.no_extras and N == N_EDGE:
+            cpu["cpu_nfft"] = run_cpu_nfft((c_np, x_np, results["f64"]["idx"]), fd)
 
     def fam_line(fam):
         r = results[fam]
@@ -399,6 +543,15 @@ def run_ours(args, rank, world, local):
         "mixed": mixed,
         "cpu_baseline": cpu,
     }
+    if extras:
+        line["sweep"] = extras["sweep"]
+        line["c2"] = extras["gpe_snapshot"]
+        rule = [r for r in extras["sweep"] if r["family"] == "f32" and r["eps"] == 1e-6]
+        if rule:
+            line["mixed"]["at_rule_m"] = {"m": rule[0]["m"], "value": rule[0]["mpoints_s"],
+                                          "rel_l2_vs_oracle": rule[0]["rel_l2"],
+                                          "note": "the library's m rule for eps = 1e-6; the headline "
+                                                  "mixed line uses m = %d" % M_MIXED}
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
