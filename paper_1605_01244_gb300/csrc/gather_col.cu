@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(256) gather_col_f32_kernel(const float2 *__res
                                                              PointsView<float> pts,
                                                              const __grid_constant__ Poly<float, MM> P,
                                                              float2 *__restrict__ f,
-                                                             float2 *__restrict__ grad) {
+                                                             float2 *__restrict__ grad,
+                                                             const int *__restrict__ sel, int64_t nwork) {
     constexpr int W = 2 * MM + 1;
     constexpr int GS = GroupSize<W>::value;
     constexpr int D = PolyDeg<float>::value;
@@ -43,10 +44,11 @@ __global__ void __launch_bounds__(256) gather_col_f32_kernel(const float2 *__res
     const int lane = threadIdx.x & 31;
     const int sub = lane & (GS - 1);
     const int gbase = lane & ~(GS - 1);
-    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / GS;
-    const bool valid = j < pts.M;
-    const int64_t jj = valid ? j : 0;
-    const int4 key = pts.M > 0 ? pts.key[jj] : make_int4(0, 0, 0, 0);
+    // work item w: sorted point sel[w] (sel given) or w
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / GS;
+    const bool valid = w < nwork;
+    const int64_t jj = valid ? (sel ? (int64_t)sel[w] : w) : (sel ? (int64_t)sel[0] : 0);
+    const int4 key = pts.key[jj];
     const int tap = sub < W ? sub : 0;
     float myw[3];
     {
@@ -130,7 +132,8 @@ template <int MM>
 __global__ void __launch_bounds__(256) gather_col_f32_cube_kernel(const float2 *__restrict__ G, Grid3 pg,
                                                                   PointsView<float> pts,
                                                                   const __grid_constant__ Poly<float, MM> P,
-                                                                  float2 *__restrict__ f) {
+                                                                  float2 *__restrict__ f,
+                                                                  const int *__restrict__ sel, int64_t nwork) {
     constexpr int W = 2 * MM + 1;
     constexpr int GS = GroupSize<W>::value;
     constexpr int PPW = 32 / GS;
@@ -144,11 +147,13 @@ __global__ void __launch_bounds__(256) gather_col_f32_cube_kernel(const float2 *
     for (int k = 0; k <= D; ++k) cf[k] = P.c[0][tap][k];
     const int64_t s1 = (int64_t)pg.n2 * pg.n3;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t jb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * PPW; jb < pts.M;
-         jb += nwarps * PPW) {
-        const int64_t j = jb + lane / GS;
-        const bool valid = j < pts.M;
-        const int64_t jj = valid ? j : jb;
+    // work item w: sorted point sel[w] (sel given) or w
+    for (int64_t wb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * PPW; wb < nwork;
+         wb += nwarps * PPW) {
+        const int64_t w = wb + lane / GS;
+        const bool valid = w < nwork;
+        const int64_t ww = valid ? w : wb;
+        const int64_t jj = sel ? (int64_t)sel[ww] : ww;
         const int4 key = pts.key[jj];
         float myw[3];
         {
@@ -444,11 +449,12 @@ int pad_blocks(int64_t rows) {
 
 template <int MM, int NG>
 cudaError_t col_f32_dispatch(const float2 *G, Grid3 g, PointsView<float> pts,
-                             const WinTable<float> &w, float2 *f, float2 *grad, cudaStream_t st) {
+                             const WinTable<float> &w, float2 *f, float2 *grad, const int *sel, int64_t nwork,
+                             cudaStream_t st) {
     constexpr int W = 2 * MM + 1;
     constexpr int GS = GroupSize<W>::value;
     const int threads = 256;
-    const int64_t want = (pts.M * GS + threads - 1) / threads;
+    const int64_t want = (nwork * GS + threads - 1) / threads;
     bool shared_table = NG == 1 && !std::getenv("GBNFFT_F32_NO_CUBE");
     for (int d = 1; d < 3 && shared_table; ++d)
         for (int a = 0; a < W && shared_table; ++a)
@@ -464,11 +470,108 @@ cudaError_t col_f32_dispatch(const float2 *G, Grid3 g, PointsView<float> pts,
             resident = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
         }
         const int64_t blocks = want < resident ? want : resident;
-        gather_col_f32_cube_kernel<MM><<<(unsigned)blocks, threads, 0, st>>>(G, g, pts, make_poly<float, MM>(w), f);
+        gather_col_f32_cube_kernel<MM><<<(unsigned)blocks, threads, 0, st>>>(G, g, pts, make_poly<float, MM>(w), f,
+                                                                              sel, nwork);
         return cudaGetLastError();
     }
-    gather_col_f32_kernel<MM, NG><<<(unsigned)want, threads, 0, st>>>(G, g, pts, make_poly<float, MM>(w), f, grad);
+    gather_col_f32_kernel<MM, NG><<<(unsigned)want, threads, 0, st>>>(G, g, pts, make_poly<float, MM>(w), f, grad,
+                                                                       sel, nwork);
     return cudaGetLastError();
+}
+
+// ---- dense batches (mixed family) --------------------------------------------
+// One warp per batch of <= 32 sorted points that share their first stencil
+// nodes in dimensions 1 and 2 (they come from one sort key: one tile and one
+// (x, y) cell of stencil centres), one point per lane.  Each lane evaluates
+// its own 3 (2m+1) tap weights; for every stencil row (a, b) the row's start
+// is the same for the whole warp and the lanes' third-dimension origins lie
+// within 8 cells of each other (away from the grid's first and last tiles,
+// where they wrap), so each load instruction of the warp touches one span of
+// at most 2m + 8 grid values (one or two 128-byte lines) instead of one line
+// per point as in the column kernel.
+template <int MM>
+__global__ void __launch_bounds__(256) gather_dense_f32_kernel(const float2 *__restrict__ G, Grid3 pg,
+                                                               PointsView<float> pts,
+                                                               const __grid_constant__ Poly<float, MM> P,
+                                                               const int2 *__restrict__ batches, int nbatch,
+                                                               float2 *__restrict__ f) {
+    constexpr int W = 2 * MM + 1;
+    constexpr int D = PolyDeg<float>::value;
+    const int lane = threadIdx.x & 31;
+    const int64_t s1 = (int64_t)pg.n2 * pg.n3;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nbatch; b += nwarps) {
+        const int2 bt = batches[b];
+        const bool valid = lane < bt.y;
+        const int64_t j = (int64_t)bt.x + (valid ? lane : 0);
+        const int4 key = pts.key[j];
+        float w1[W], w2[W], w3[W];
+        {
+            const float t1 = 2.f * pts.s1[j] - 1.f, t2 = 2.f * pts.s2[j] - 1.f, t3 = 2.f * pts.s3[j] - 1.f;
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                float v1 = P.c[0][a][D], v2 = P.c[1][a][D], v3 = P.c[2][a][D];
+#pragma unroll
+                for (int k = D - 1; k >= 0; --k) {
+                    v1 = fmaf(v1, t1, P.c[0][a][k]);
+                    v2 = fmaf(v2, t2, P.c[1][a][k]);
+                    v3 = fmaf(v3, t3, P.c[2][a][k]);
+                }
+                w1[a] = v1;
+                w2[a] = v2;
+                w3[a] = v3;
+            }
+        }
+        const float2 *base = G + (int64_t)key.x * s1 + (int64_t)key.y * pg.n3 + key.z;
+        float Tr = 0.f, Ti = 0.f;
+#pragma unroll 1
+        for (int a = 0; a < W; ++a) {
+            float Sr = 0.f, Si = 0.f;
+            const float2 *row = base;
+#pragma unroll
+            for (int bb = 0; bb < W; ++bb) {
+                float Rr = 0.f, Ri = 0.f;
+#pragma unroll
+                for (int c = 0; c < W; ++c) {
+                    const float2 v = __ldg(row + c);
+                    Rr = fmaf(w3[c], v.x, Rr);
+                    Ri = fmaf(w3[c], v.y, Ri);
+                }
+                Sr = fmaf(w2[bb], Rr, Sr);
+                Si = fmaf(w2[bb], Ri, Si);
+                row += pg.n3;
+            }
+            Tr = fmaf(w1[0], Sr, Tr);
+            Ti = fmaf(w1[0], Si, Ti);
+#pragma unroll
+            for (int k = 0; k < W - 1; ++k) w1[k] = w1[k + 1];
+            base += s1;
+        }
+        if (valid) f[key.w] = make_float2(Tr, Ti);
+    }
+}
+
+template <int MM>
+cudaError_t split_f32_dispatch(const float2 *G, Grid3 g, PointsView<float> pts, const WinTable<float> &w,
+                               const int2 *batches, int nbatch, const int *sparse_idx, int nsparse, float2 *f,
+                               cudaStream_t st) {
+    if (nbatch > 0) {
+        static int resident = 0;   // blocks per SM x SMs for this instantiation
+        if (resident == 0) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gather_dense_f32_kernel<MM>, 256, 0);
+            resident = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+        }
+        const int64_t want = ((int64_t)nbatch * 32 + 255) / 256;
+        gather_dense_f32_kernel<MM><<<(unsigned)(want < resident ? want : resident), 256, 0, st>>>(
+            G, g, pts, make_poly<float, MM>(w), batches, nbatch, f);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (nsparse > 0) return col_f32_dispatch<MM, 1>(G, g, pts, w, f, nullptr, sparse_idx, nsparse, st);
+    return cudaSuccess;
 }
 
 template <int MM, int NG>
@@ -494,14 +597,14 @@ cudaError_t col_f32_select(const float2 *G, Grid3 g, int m, PointsView<float> pt
                            const WinTable<float> &w, float2 *f, float2 *grad, cudaStream_t st) {
     if (pts.M == 0) return cudaSuccess;
     switch (m) {
-        case 1: return col_f32_dispatch<1, NG>(G, g, pts, w, f, grad, st);
-        case 2: return col_f32_dispatch<2, NG>(G, g, pts, w, f, grad, st);
-        case 3: return col_f32_dispatch<3, NG>(G, g, pts, w, f, grad, st);
-        case 4: return col_f32_dispatch<4, NG>(G, g, pts, w, f, grad, st);
-        case 5: return col_f32_dispatch<5, NG>(G, g, pts, w, f, grad, st);
-        case 6: return col_f32_dispatch<6, NG>(G, g, pts, w, f, grad, st);
-        case 7: return col_f32_dispatch<7, NG>(G, g, pts, w, f, grad, st);
-        case 8: return col_f32_dispatch<8, NG>(G, g, pts, w, f, grad, st);
+        case 1: return col_f32_dispatch<1, NG>(G, g, pts, w, f, grad, nullptr, pts.M, st);
+        case 2: return col_f32_dispatch<2, NG>(G, g, pts, w, f, grad, nullptr, pts.M, st);
+        case 3: return col_f32_dispatch<3, NG>(G, g, pts, w, f, grad, nullptr, pts.M, st);
+        case 4: return col_f32_dispatch<4, NG>(G, g, pts, w, f, grad, nullptr, pts.M, st);
+        case 5: return col_f32_dispatch<5, NG>(G, g, pts, w, f, grad, nullptr, pts.M, st);
+        case 6: return col_f32_dispatch<6, NG>(G, g, pts, w, f, grad, nullptr, pts.M, st);
+        case 7: return col_f32_dispatch<7, NG>(G, g, pts, w, f, grad, nullptr, pts.M, st);
+        case 8: return col_f32_dispatch<8, NG>(G, g, pts, w, f, grad, nullptr, pts.M, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -545,6 +648,23 @@ cudaError_t launch_gather_col_f32(const float2 *G, Grid3 g, int m, PointsView<fl
                                   cudaStream_t st) {
     return ng == 4 ? col_f32_select<4>(G, g, m, pts, w, f, grad, st)
                    : col_f32_select<1>(G, g, m, pts, w, f, nullptr, st);
+}
+
+cudaError_t launch_gather_split_f32(const float2 *G, Grid3 g, int m, PointsView<float> pts,
+                                    const WinTable<float> &w, const int2 *batches, int nbatch,
+                                    const int *sparse_idx, int nsparse, float2 *f, cudaStream_t st) {
+    if (pts.M == 0) return cudaSuccess;
+    switch (m) {
+        case 1: return split_f32_dispatch<1>(G, g, pts, w, batches, nbatch, sparse_idx, nsparse, f, st);
+        case 2: return split_f32_dispatch<2>(G, g, pts, w, batches, nbatch, sparse_idx, nsparse, f, st);
+        case 3: return split_f32_dispatch<3>(G, g, pts, w, batches, nbatch, sparse_idx, nsparse, f, st);
+        case 4: return split_f32_dispatch<4>(G, g, pts, w, batches, nbatch, sparse_idx, nsparse, f, st);
+        case 5: return split_f32_dispatch<5>(G, g, pts, w, batches, nbatch, sparse_idx, nsparse, f, st);
+        case 6: return split_f32_dispatch<6>(G, g, pts, w, batches, nbatch, sparse_idx, nsparse, f, st);
+        case 7: return split_f32_dispatch<7>(G, g, pts, w, batches, nbatch, sparse_idx, nsparse, f, st);
+        case 8: return split_f32_dispatch<8>(G, g, pts, w, batches, nbatch, sparse_idx, nsparse, f, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_gather_col_df(const float4 *G, Grid3 g, int m, PointsView<double> pts,

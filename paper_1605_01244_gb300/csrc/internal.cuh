@@ -280,16 +280,34 @@ struct PointsBuild {
     int *chunk_start;       // ntile + 1 (exclusive scan; last entry = number of chunks)
     int4 *chunks;           // (tile, first sorted point, count, 0), chunk_cap entries
     int64_t chunk_cap;
+    // split of the mixed family's value gather (nsub > 1 only): sort keys
+    // holding at least dense_min points are "dense" and gathered in batches
+    // of <= 32 points that share their first two stencil nodes (one point per
+    // lane); the points of the other keys are "sparse" and gathered by the
+    // column kernel through an index list.  Counts and starts are per tile.
+    int dense_min;          // 0: no split
+    int *tile_dense;        // ntile + 1: batches per tile
+    int *tile_dense_start;  // ntile + 1: exclusive scan
+    int *tile_sparse;       // ntile + 1: sparse points per tile
+    int *tile_sparse_start; // ntile + 1
+    int2 *batches;          // (first sorted point, count <= 32), batch_cap entries
+    int64_t batch_cap;
+    int *sparse_idx;        // sorted indices of the sparse points, M_cap entries
 };
+
+constexpr int kDenseBatch = 32;       // points per batch of the dense gather (one per lane)
+constexpr int kDenseMinDefault = 12;  // points a sort key needs to go to the dense gather
 
 constexpr int kChunk = 128;   // points per chunk of the tile-staged gather
 
 // Tile-staged FP32 gather (gather_tma.cu).  tmap: a CUtensorMap (128 bytes)
 // from encode_padded_tmap for the padded grid.
 int encode_padded_tmap(void *tmap_out, const void *P, Grid3 pg, int m);
+// first_wait_limit: polls of the first mbarrier wait before the kernel gives
+// up (clamped to the normal limit); lowered only by the failure-detection test.
 cudaError_t launch_gather_tma_f32(const void *tmap, const int4 *chunks, int nchunks, int nt2, int nt3,
                                   Grid3 g, int m, PointsView<float> pts, const WinTable<float> &w,
-                                  float2 *f, int *status, cudaStream_t st);
+                                  float2 *f, int *status, unsigned first_wait_limit, cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R *s2, R *s3,
@@ -298,6 +316,18 @@ cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R 
 // Chunk list from tile_start (after launch_points); the number of chunks is
 // left in chunk_start[ntile].
 cudaError_t launch_chunks(PointsBuild &pb, cudaStream_t st);
+// Dense batches and sparse index list of the split gather (after
+// launch_points, nsub > 1 and dense_min > 0); their numbers are left in
+// tile_dense_start[ntile] and tile_sparse_start[ntile].
+cudaError_t launch_split_lists(PointsBuild &pb, cudaStream_t st);
+int split_list_launches(const PointsBuild &pb);
+
+// Split value gather of the mixed family over the padded grid (G = P, g = pg):
+// dense batches (one point per lane, shared first two stencil nodes) and the
+// sparse points through the column kernel.
+cudaError_t launch_gather_split_f32(const float2 *G, Grid3 g, int m, PointsView<float> pts,
+                                    const WinTable<float> &w, const int2 *batches, int nbatch,
+                                    const int *sparse_idx, int nsparse, float2 *f, cudaStream_t st);
 
 size_t scan_tmp_ints(int64_t n);
 // Exclusive scan of n ints on the stream; tmp must hold scan_tmp_ints(n) ints.

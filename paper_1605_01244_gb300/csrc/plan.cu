@@ -333,6 +333,12 @@ void release(nfft3_plan p) {
     v = p->pb.chunk_count; dev_free(v);
     v = p->pb.chunk_start; dev_free(v);
     v = p->pb.chunks; dev_free(v);
+    v = p->pb.tile_dense; dev_free(v);
+    v = p->pb.tile_dense_start; dev_free(v);
+    v = p->pb.tile_sparse; dev_free(v);
+    v = p->pb.tile_sparse_start; dev_free(v);
+    v = p->pb.batches; dev_free(v);
+    v = p->pb.sparse_idx; dev_free(v);
     v = p->x_dev; dev_free(v);
     dev_free(p->c_dev);
     dev_free(p->f_dev);
@@ -405,6 +411,10 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         // point with global atomics only (GBNFFT_SPREAD=direct)
         const char *sp = std::getenv("GBNFFT_SPREAD");
         p->spread_direct = sp && !std::strcmp(sp, "direct");
+        // GBNFFT_TMA_FIRST_WAIT: polls of the tile-staged gather's first
+        // mbarrier wait (failure-detection test only; default: the full limit)
+        const char *fw = std::getenv("GBNFFT_TMA_FIRST_WAIT");
+        p->tma_first_wait = fw ? (unsigned)std::strtoul(fw, nullptr, 10) : ~0u;
         p->gather_mode = !g                           ? 3
                          : !std::strcmp(g, "thread") ? 1
                          : !std::strcmp(g, "native") ? 2
@@ -513,6 +523,25 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1)), pb.chunk_count = (int *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1)), pb.chunk_start = (int *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int4) * pb.chunk_cap), pb.chunks = (int4 *)v;
+        // split value gather of the mixed family (sort keys of one tile and
+        // (x, y) cell): keys with at least dense_min points go to the dense
+        // batches; GBNFFT_DENSE_MIN overrides the threshold, 0 disables the split
+        pb.dense_min = 0;
+        if (prec == 32 && pb.nsub == 64 && (p->gather_mode == 0 || p->gather_mode == 3)) {
+            const char *dm = std::getenv("GBNFFT_DENSE_MIN");
+            pb.dense_min = dm ? std::atoi(dm) : kDenseMinDefault;
+            if (pb.dense_min > 0 && pb.dense_min < 4) pb.dense_min = 4;   // batch_cap below needs >= 4
+        }
+        if (pb.dense_min > 0) {
+            // a dense key of cnt >= dense_min >= 4 points makes ceil(cnt / 32) <= cnt / 4 batches
+            pb.batch_cap = M / 4 + 1;
+            if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1)), pb.tile_dense = (int *)v;
+            if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1)), pb.tile_dense_start = (int *)v;
+            if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1)), pb.tile_sparse = (int *)v;
+            if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (pb.ntile + 1)), pb.tile_sparse_start = (int *)v;
+            if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int2) * pb.batch_cap), pb.batches = (int2 *)v;
+            if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * (M + 1)), pb.sparse_idx = (int *)v;
+        }
         if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int4) * (M + 1)), p->key = (int4 *)v;
         for (int d = 0; d < 3 && st == NFFT3_OK; ++d) st = dev_alloc(p, &p->s[d], rs * (M + 1));
     }
@@ -596,6 +625,7 @@ int set_points_impl(nfft3_plan p, const double *x, int prec) {
     if (!p || p->prec != prec) return NFFT3_ERR_ARG;
     if (!x && p->M > 0) return NFFT3_ERR_ARG;
     p->points_ok = 0;
+    p->split_ok = 0;
     const int rec = rec_begin(p, kRecSetPoints);
     cudaError_t e;
     if (prec == 64)
@@ -608,18 +638,31 @@ int set_points_impl(nfft3_plan p, const double *x, int prec) {
     p->launches += (p->M > 0 ? 4 : 1) + scan_launches(p->pb.nkey + 1);
     if (launch_chunks(p->pb, p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
     p->launches += 2 + scan_launches(p->pb.ntile + 1);
+    const bool split = p->pb.dense_min > 0 && p->M > 0;
+    if (split) {
+        if (launch_split_lists(p->pb, p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
+        p->launches += split_list_launches(p->pb);
+    }
     rec_mark(p, rec, 1);
     rec_end(p, rec, 1);
-    int status = 0, nch = 0;
+    int status = 0, nch = 0, nbs[2] = {0, 0};
     if (cudaMemcpyAsync(&status, p->pb.status, sizeof(int), cudaMemcpyDeviceToHost, p->stream) !=
             cudaSuccess ||
         cudaMemcpyAsync(&nch, p->pb.chunk_start + p->pb.ntile, sizeof(int), cudaMemcpyDeviceToHost,
                         p->stream) != cudaSuccess)
         return NFFT3_ERR_CUDA;
+    if (split && (cudaMemcpyAsync(&nbs[0], p->pb.tile_dense_start + p->pb.ntile, sizeof(int),
+                                  cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+                  cudaMemcpyAsync(&nbs[1], p->pb.tile_sparse_start + p->pb.ntile, sizeof(int),
+                                  cudaMemcpyDeviceToHost, p->stream) != cudaSuccess))
+        return NFFT3_ERR_CUDA;
     if (cudaStreamSynchronize(p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
     if (status & 2) return NFFT3_ERR_CUDA;   // a tile-staged gather timed out on its copy
     if (status & 1) return NFFT3_ERR_POINTS;
     p->nchunks = nch <= p->pb.chunk_cap ? nch : 0;
+    p->nbatch = nbs[0];
+    p->nsparse = nbs[1];
+    p->split_ok = split && nbs[0] <= p->pb.batch_cap && nbs[1] <= p->M;
     p->points_ok = 1;
     return NFFT3_OK;
 }
@@ -667,8 +710,15 @@ cudaError_t gather_padded(nfft3_plan p, int ng, typename Cplx<R>::T *f, typename
                                     p->wt64, p->df_weights_fp64, (double2 *)f, (double2 *)grad, ng, p->stream);
     if (ng == 1 && p->pgrid_shift != 0 && p->tmap_ok && p->nchunks > 0)
         return launch_gather_tma_f32(p->tmap, p->pb.chunks, p->nchunks, p->pb.nt2, p->pb.nt3, g, p->m,
-                                     points_view<float>(p), p->wt32, (float2 *)f, p->pb.status, p->stream);
+                                     points_view<float>(p), p->wt32, (float2 *)f, p->pb.status,
+                                     p->tma_first_wait, p->stream);
     if (p->pgrid_shift != 0) return cudaErrorInvalidValue;  // centre layout, no tile list: not reachable
+    if (ng == 1 && p->split_ok) {
+        p->launches += (p->nbatch > 0) + (p->nsparse > 0) - 1;
+        return launch_gather_split_f32((const float2 *)p->pgrid, pg, p->m, points_view<float>(p), p->wt32,
+                                       p->pb.batches, p->nbatch, p->pb.sparse_idx, p->nsparse, (float2 *)f,
+                                       p->stream);
+    }
     return launch_gather_col_f32((const float2 *)p->pgrid, pg, p->m, points_view<float>(p), p->wt32,
                                  (float2 *)f, (float2 *)grad, ng, p->stream);
 }

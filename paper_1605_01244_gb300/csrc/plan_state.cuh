@@ -26,6 +26,7 @@ struct nfft3_plan_s {
     int df_weights_fp64;       // GBNFFT_DF_WEIGHTS: FP64-pipe weights (default) or df ("df")
     int gather_mode;           // GBNFFT_GATHER: 0 col (default), 1 thread, 2 native (see plan.cu)
     int spread_direct;         // GBNFFT_SPREAD=direct: one thread per point, global atomics only
+    unsigned tma_first_wait;   // GBNFFT_TMA_FIRST_WAIT (test of the tile-staged gather's bounded wait)
     // tables and grid
     void *D[3];               // deconvolution factors, real type of the family
     void *grid;               // n1 n2 n3 complex (x4 once eval_grad ran)
@@ -41,6 +42,8 @@ struct nfft3_plan_s {
     alignas(64) unsigned char tmap[128];  // CUtensorMap of the padded FP32 grid (tile-staged gather)
     int tmap_ok;
     int nchunks;              // chunks of the tile-staged gather for the current points
+    int nbatch, nsparse;      // split gather lists for the current points (mixed family)
+    int split_ok;             // the split lists describe the current points
     cufftHandle fft1;
     cufftHandle fft4;
     int have_fft4;

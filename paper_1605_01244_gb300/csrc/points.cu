@@ -214,6 +214,71 @@ __global__ void chunk_fill_kernel(PointsBuild pb) {
     }
 }
 
+// Split lists of the mixed family's gather, one warp per tile: each lane
+// takes two of the tile's nsub = 64 sort keys; a key with at least dense_min
+// points contributes ceil(count / 32) batches, any other key its points to
+// the sparse list.
+__device__ __forceinline__ void key_split(const PointsBuild &pb, int64_t k, int &nb, int &ns, int &first,
+                                          int &cnt) {
+    first = pb.key_start[k];
+    cnt = pb.key_start[k + 1] - first;
+    const bool dense = cnt >= pb.dense_min;
+    nb = dense ? (cnt + kDenseBatch - 1) / kDenseBatch : 0;
+    ns = dense ? 0 : cnt;
+}
+
+__global__ void __launch_bounds__(256) split_count_kernel(PointsBuild pb) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t <= pb.ntile; t += nw) {
+        int nb = 0, ns = 0;
+        if (t < pb.ntile) {
+            for (int h = 0; h < 2; ++h) {
+                int b, s, first, cnt;
+                key_split(pb, t * pb.nsub + h * 32 + lane, b, s, first, cnt);
+                nb += b;
+                ns += s;
+            }
+        }
+        nb = __reduce_add_sync(0xffffffffu, nb);
+        ns = __reduce_add_sync(0xffffffffu, ns);
+        if (lane == 0) {
+            pb.tile_dense[t] = nb;
+            pb.tile_sparse[t] = ns;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) split_fill_kernel(PointsBuild pb) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < pb.ntile; t += nw) {
+        int nb[2], ns[2], first[2], cnt[2];
+        for (int h = 0; h < 2; ++h) key_split(pb, t * pb.nsub + h * 32 + lane, nb[h], ns[h], first[h], cnt[h]);
+        // positions: keys in order h = 0 (lanes 0..31), then h = 1
+        int ob = pb.tile_dense_start[t], os = pb.tile_sparse_start[t];
+        for (int h = 0; h < 2; ++h) {
+            const int ib = warp_incl_scan(nb[h]), is = warp_incl_scan(ns[h]);
+            const int pb0 = ob + ib - nb[h], ps0 = os + is - ns[h];
+            // the batches of each dense key, written by the whole warp (a key
+            // can hold millions of points: a lattice inside one cell)
+            for (unsigned dense = __ballot_sync(0xffffffffu, nb[h] > 0); dense; dense &= dense - 1) {
+                const int src = __ffs(dense) - 1;
+                const int kb = __shfl_sync(0xffffffffu, nb[h], src), kp = __shfl_sync(0xffffffffu, pb0, src);
+                const int kf = __shfl_sync(0xffffffffu, first[h], src), kc = __shfl_sync(0xffffffffu, cnt[h], src);
+                for (int b = lane; b < kb; b += 32) {
+                    const int n = kc - b * kDenseBatch < kDenseBatch ? kc - b * kDenseBatch : kDenseBatch;
+                    if (kp + b < pb.batch_cap) pb.batches[kp + b] = make_int2(kf + b * kDenseBatch, n);
+                }
+            }
+            for (int i = 0; i < ns[h]; ++i)
+                if (ps0 + i < pb.M_cap) pb.sparse_idx[ps0 + i] = first[h] + i;
+            ob += __shfl_sync(0xffffffffu, ib, 31);
+            os += __shfl_sync(0xffffffffu, is, 31);
+        }
+    }
+}
+
 int point_blocks(int64_t M) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -297,6 +362,23 @@ cudaError_t launch_chunks(PointsBuild &pb, cudaStream_t st) {
     chunk_fill_kernel<<<point_blocks(pb.ntile), 256, 0, st>>>(pb);
     return cudaGetLastError();
 }
+
+cudaError_t launch_split_lists(PointsBuild &pb, cudaStream_t st) {
+    if (pb.nsub != 64 || pb.dense_min <= 0) return cudaErrorInvalidValue;
+    const int64_t n = pb.ntile + 1;
+    const int blocks = point_blocks(n * 32);
+    split_count_kernel<<<blocks, 256, 0, st>>>(pb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = exclusive_scan(pb.tile_dense, pb.tile_dense_start, n, pb.scan_tmp, st);
+    if (e != cudaSuccess) return e;
+    e = exclusive_scan(pb.tile_sparse, pb.tile_sparse_start, n, pb.scan_tmp, st);
+    if (e != cudaSuccess) return e;
+    split_fill_kernel<<<blocks, 256, 0, st>>>(pb);
+    return cudaGetLastError();
+}
+
+int split_list_launches(const PointsBuild &pb) { return 2 + 2 * scan_launches(pb.ntile + 1); }
 
 template cudaError_t launch_points<double>(const double *, PointsBuild &, int4 *, double *,
                                            double *, double *, cudaStream_t);

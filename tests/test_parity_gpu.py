@@ -325,6 +325,36 @@ def test_f32_shared_table_gather(m, monkeypatch):
     assert max_rel(out["cube"], out["table"]) <= 1e-6
 
 
+@pytest.mark.parametrize("N,m", [((32, 32, 32), 3), ((32, 32, 32), 8), ((16, 24, 20), 2), ((16, 24, 20), 5)])
+def test_split_value_gather(N, m, monkeypatch):
+    """The mixed family's value gather splits the points: sort keys (one tile,
+    one (x, y) cell of stencil centres) with at least GBNFFT_DENSE_MIN points
+    (default 12) go to dense batches, one point per lane; the rest go to the
+    column kernel through an index list.  Every threshold -- no split (0), all
+    keys of >= 4 points dense, none dense -- must match the CPU NFFT and each
+    other, on a tight cluster (hundreds of points per cell), a wider one and
+    uniform points, with ragged batch sizes, on cubic and non-cubic grids."""
+    from paper_1605_01244_gb300 import Plan
+    c = wl.gaussian_coeffs(N, 1e9, seed=60 + m)
+    x = np.concatenate([wl.cluster_points(20011, 0.004, seed=61), wl.cluster_points(5003, 0.05, seed=62),
+                        wl.uniform_points(3001, seed=63)])
+    fc = nfft_cpu.forward(c, x, tuple(2 * v for v in N), m)
+    out = {}
+    for dm in ("default", "0", "4", "1000000"):
+        monkeypatch.delenv("GBNFFT_DENSE_MIN", raising=False)
+        if dm != "default":
+            monkeypatch.setenv("GBNFFT_DENSE_MIN", dm)
+        plan = Plan(N, len(x), m=m, precision="f32")
+        plan.set_points(to_dev(x))
+        out[dm] = to_np(plan.eval(to_dev(c, torch.complex64))).astype(np.complex128)
+        assert rel_l2(out[dm], fc) <= 2e-6, dm
+        # the stored-grid gather takes the same split
+        plan.precompute(to_dev(c, torch.complex64))
+        assert np.array_equal(to_np(plan.eval_stored()).astype(np.complex128), out[dm]), dm
+    for dm in ("0", "4", "1000000"):
+        assert max_rel(out["default"], out[dm]) <= 1e-6, dm
+
+
 @pytest.mark.parametrize("N", [(16, 32, 8), (8, 1024, 8), (64, 64, 64)])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_fused_transform_matches_cufft_and_cpu(N, prec, monkeypatch):
