@@ -8,7 +8,10 @@
 // list with two box buffers: the copy of chunk i + 2's box (armed on an
 // mbarrier with the box's byte count) overlaps the evaluation of chunk i.
 // Waits are bounded: after kWaitLimit polls the CTA records an error bit in
-// the plan's status word and returns without touching shared memory again.
+// the plan's status word, waits (again bounded) for every copy it issued that
+// may still be in flight -- the late one and the other buffer's -- and
+// returns without touching shared memory again.  The first wait's limit is a
+// launch parameter (normally kWaitLimit), so that a test can make it run out.
 // Evaluation uses the column-group mapping of gather_col.cu on shared memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -71,7 +74,8 @@ __global__ void __launch_bounds__(256) gather_tma_f32_kernel(const __grid_consta
                                                              PointsView<float> pts,
                                                              const __grid_constant__ Poly<float, MM> P,
                                                              float2 *__restrict__ f,
-                                                             int *__restrict__ status) {
+                                                             int *__restrict__ status,
+                                                             unsigned first_wait_limit) {
     constexpr int W = 2 * MM + 1;
     constexpr int G = GS<W>::value;
     constexpr int B = kTile + 2 * MM;           // box edge
@@ -111,14 +115,19 @@ __global__ void __launch_bounds__(256) gather_tma_f32_kernel(const __grid_consta
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x, ++it) {
         const int b = it & 1;
         bool ready = false;
-        for (unsigned k = 0; k < kWaitLimit; ++k)
+        const unsigned limit = it == 0 ? first_wait_limit : kWaitLimit;
+        for (unsigned k = 0; k < limit; ++k)
             if ((ready = mbar_try_wait(&bar[b], phase[b]))) break;
         // the decision is taken by the whole block, so that no thread is left
         // waiting at a later barrier
         if (!__syncthreads_and(ready)) {
             if (threadIdx.x == 0) {
                 atomicOr(status, 2);
-                // let the other buffer's copy, if one was issued, land before exiting
+                // let the copies still in flight land before the block's shared
+                // memory is released: this buffer's, and the other buffer's if
+                // one was issued for the next chunk
+                for (unsigned k = 0; k < kWaitLimit; ++k)
+                    if (mbar_try_wait(&bar[b], phase[b])) break;
                 if (c + (int)gridDim.x < nchunks)
                     for (unsigned k = 0; k < kWaitLimit; ++k)
                         if (mbar_try_wait(&bar[b ^ 1], phase[b ^ 1])) break;
@@ -198,7 +207,7 @@ template <int MM> size_t tma_smem_bytes() {
 template <int MM>
 cudaError_t tma_dispatch(const CUtensorMap &map, const int4 *chunks, int nchunks, int nt2, int nt3,
                          Grid3 g, PointsView<float> pts, const WinTable<float> &w, float2 *f,
-                         int *status, cudaStream_t st) {
+                         int *status, unsigned first_wait_limit, cudaStream_t st) {
     const size_t sm = tma_smem_bytes<MM>();
     static int blocks_per_sm = 0;  // per process; the attribute and occupancy are per function
     if (!blocks_per_sm) {
@@ -211,7 +220,7 @@ cudaError_t tma_dispatch(const CUtensorMap &map, const int4 *chunks, int nchunks
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = nchunks < sms * blocks_per_sm ? nchunks : sms * blocks_per_sm;
     gather_tma_f32_kernel<MM><<<grid, 256, sm, st>>>(map, chunks, nchunks, nt2, nt3, g, pts,
-                                                     make_poly<float, MM>(w), f, status);
+                                                     make_poly<float, MM>(w), f, status, first_wait_limit);
     return cudaGetLastError();
 }
 
@@ -247,18 +256,19 @@ int encode_padded_tmap(void *tmap_out, const void *P, Grid3 pg, int m) {
 
 cudaError_t launch_gather_tma_f32(const void *tmap, const int4 *chunks, int nchunks, int nt2, int nt3,
                                   Grid3 g, int m, PointsView<float> pts, const WinTable<float> &w,
-                                  float2 *f, int *status, cudaStream_t st) {
+                                  float2 *f, int *status, unsigned first_wait_limit, cudaStream_t st) {
     if (nchunks <= 0 || pts.M == 0) return cudaSuccess;
     const CUtensorMap &map = *reinterpret_cast<const CUtensorMap *>(tmap);
+    if (first_wait_limit > kWaitLimit) first_wait_limit = kWaitLimit;
     switch (m) {
-        case 1: return tma_dispatch<1>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, st);
-        case 2: return tma_dispatch<2>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, st);
-        case 3: return tma_dispatch<3>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, st);
-        case 4: return tma_dispatch<4>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, st);
-        case 5: return tma_dispatch<5>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, st);
-        case 6: return tma_dispatch<6>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, st);
-        case 7: return tma_dispatch<7>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, st);
-        case 8: return tma_dispatch<8>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, st);
+        case 1: return tma_dispatch<1>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, first_wait_limit, st);
+        case 2: return tma_dispatch<2>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, first_wait_limit, st);
+        case 3: return tma_dispatch<3>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, first_wait_limit, st);
+        case 4: return tma_dispatch<4>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, first_wait_limit, st);
+        case 5: return tma_dispatch<5>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, first_wait_limit, st);
+        case 6: return tma_dispatch<6>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, first_wait_limit, st);
+        case 7: return tma_dispatch<7>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, first_wait_limit, st);
+        case 8: return tma_dispatch<8>(map, chunks, nchunks, nt2, nt3, g, pts, w, f, status, first_wait_limit, st);
         default: return cudaErrorInvalidValue;
     }
 }

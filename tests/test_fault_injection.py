@@ -67,3 +67,35 @@ def test_plan_survives_bad_calls():
     f = plan.eval(torch.from_numpy(c).cuda()).cpu().numpy()
     fd = oracle.forward(c, x)
     assert np.linalg.norm(f - fd) / np.linalg.norm(fd) <= 1e-9   # m = 5 window error
+
+
+@pytest.mark.gpu
+def test_tile_staged_gather_bounded_wait_reports_error(monkeypatch):
+    """The tile-staged gather's mbarrier waits are bounded.  With the first
+    wait's limit set to zero polls (GBNFFT_TMA_FIRST_WAIT=0) every block gives
+    up at once: it records the error bit, waits (bounded) for the copies it
+    issued, and returns; nfft3_sync reports NFFT3_ERR_CUDA and the context
+    stays usable for the next plan."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1605_01244_gb300 import Plan, workloads as wl
+    from paper_1605_01244_gb300._lib import NFFTError, NFFT3_ERR_CUDA
+    c = wl.gaussian_coeffs((16, 16, 16), 4.0, seed=5)
+    x = wl.mixed_points(3000, 0.05, seed=6)
+    monkeypatch.setenv("GBNFFT_GATHER", "tma")
+    monkeypatch.setenv("GBNFFT_TMA_FIRST_WAIT", "0")
+    plan = Plan((16, 16, 16), len(x), m=3, precision="f32")
+    plan.set_points(torch.from_numpy(x).cuda())
+    plan.eval(torch.from_numpy(c).to(torch.complex64).cuda())
+    with pytest.raises(NFFTError) as e:
+        plan.sync()
+    assert e.value.code == NFFT3_ERR_CUDA
+    plan.close()
+    monkeypatch.delenv("GBNFFT_TMA_FIRST_WAIT")
+    p2 = Plan((16, 16, 16), len(x), m=3, precision="f32")
+    p2.set_points(torch.from_numpy(x).cuda())
+    f = p2.eval(torch.from_numpy(c).to(torch.complex64).cuda()).cpu().numpy().astype(np.complex128)
+    p2.sync()
+    fd = oracle.forward(c, x)
+    assert np.linalg.norm(f - fd) / np.linalg.norm(fd) <= 2e-6
