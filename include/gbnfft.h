@@ -335,12 +335,15 @@ int nfft_lowdim_eval(int dim, const int *N, int64_t M, int m, double sigma, cons
  *   f[(i1 M2 + i2) M3 + i3] = sum_k c_k exp(+2 pi i (k1 y1[i1] + k2 y2[i2] + k3 y3[i3]))
  * for the grid y1 x y2 x y3 (device arrays of M1, M2, M3 torus coordinates),
  * computed exactly (no window approximation) as three dense complex
- * contractions, one dimension at a time (cuBLAS Z/CGEMM).  c as in eval,
- * f: M1 M2 M3 complex (device, overwritten).  workspace: device memory of
- * nfft3_grid_eval_workspace_bytes bytes (the three exponential matrices and
- * two partial contractions: M1 N1 + M2 N2 + M3 N3 + N1 N2 M3 + N1 M2 M3
- * complex).  Asynchronous on the stream.  N1 N2 and M2 M3 must stay below
- * 2^31 (NFFT3_ERR_TOO_LARGE).
+ * contractions, one dimension at a time (the library's own complex matrix
+ * products: FP32 for nfft3f_*, FP64 for nfft3d_* -- or double-float on the
+ * FP32 pipe, about 48 significant bits, with GBNFFT_GRID_DF=1).  c as in
+ * eval, f: M1 M2 M3 complex (device, overwritten).  workspace: device memory
+ * of nfft3_grid_eval_workspace_bytes bytes (the three exponential matrices,
+ * two partial contractions and one range word: M1 N1 + M2 N2 + M3 N3 +
+ * N1 N2 M3 + N1 M2 M3 + 1 complex).  Asynchronous on the stream.  N1 N2 and
+ * M2 M3 must stay below 2^31, N1 N2 and M1, M2 below 65535 * 64 and N1
+ * below 65536 (NFFT3_ERR_TOO_LARGE).
  */
 size_t nfft3_grid_eval_workspace_bytes(int prec, int N1, int N2, int N3, int M1, int M2, int M3);
 int nfft3d_grid_eval(const double *c, int N1, int N2, int N3, const double *y1, int M1, const double *y2, int M2,
@@ -409,6 +412,35 @@ int nfft3_fma_peak(int prec, int iters, void *stream, double *tflops);
  * (returns 1..8, or 8 when eps is below what m = 8 reaches).
  */
 int nfft3_choose_m(double eps, double sigma);
+
+/*
+ * Gross-Pitaevskii solver: time-splitting pseudospectral (TSSP) integration
+ * of the paper's eq. (GPE) (Sec. 3),
+ *     psi_t = (i/2) Lap psi + (i/2) (1 - |psi|^2) psi,
+ * by the Strang splitting of Sec. 3.1 on a periodic box of sides L1, L2, L3
+ * sampled at n1 x n2 x n3 points x = a + L_d i_d / n_d (the solver does not
+ * need the origin a).  psi: device, n1*n2*n3 FP64 complex (re, im
+ * interleaved), row-major with i3 fastest; it is advanced in place.  A step
+ * is a potential half step (exact: psi <- exp(i t (1 - |psi|^2) / 2) psi
+ * with t = tau / 2), the kinetic step (exact in Fourier space: psi_hat_k <-
+ * exp(-i tau |kappa_k|^2 / 2) psi_hat_k, kappa_d = 2 pi k_d / L_d, cuFFT
+ * Z2Z transforms) and a second potential half step; consecutive half steps
+ * within one gpe_steps call are merged.  Work is enqueued on the plan's
+ * stream.  The plan owns a FP64 complex work grid (for the diagnostics) and
+ * a cuFFT plan.
+ *   gpe_plan_create: n_d >= 1, L_d > 0; NFFT3_ERR_ALLOC / _CUFFT on failure.
+ *   gpe_steps: nsteps >= 0 steps of size tau (the kinetic tables are rebuilt
+ *     when tau changes; that call synchronises the stream).
+ *   gpe_mass_energy: the discrete mass sum |psi|^2 dV and the energy of the
+ *     paper's eq. (energy), (1/2) int |grad psi|^2 + (1/4) int (1 - |psi|^2)^2
+ *     (the gradient spectrally), dV = L1 L2 L3 / (n1 n2 n3); synchronises.
+ *     Either output pointer may be NULL.
+ */
+typedef struct gpe_plan_s *gpe_plan;
+int gpe_plan_create(gpe_plan *out, int n1, int n2, int n3, double L1, double L2, double L3, void *stream);
+int gpe_steps(gpe_plan p, double *psi, double tau, int nsteps);
+int gpe_mass_energy(gpe_plan p, const double *psi, double *mass, double *energy);
+int gpe_destroy(gpe_plan p);
 
 #ifdef __cplusplus
 }

@@ -13,6 +13,9 @@ Workloads (torus points live in [-1/2, 1/2)^3):
   CN(0,1) having independent N(0, 1/2) real and imaginary parts.
 * ``uniform_points(M)`` -- uniform in [-1/2, 1/2)^3.
 * ``cluster_points(M, std)`` -- N(0, std^2) per coordinate, wrapped mod 1.
+* ``two_vortex_initial`` -- two perpendicular straight vortices with the
+  q = 2 Pade density profile, periodic on [-L, L)^3 (initial data of the
+  Gross-Pitaevskii solver).
 * ``two_vortex_psi`` / ``gpe_coeffs`` -- the wavefunction
   psi(x) = exp(-|x|^2/18) ((x1 - a) + i x2) ((x1 + a) - i x3) / (1 + |x|^2)
   sampled on the regular grid of [-L, L)^3 and turned into series
@@ -100,6 +103,50 @@ def torus_coeffs_from_samples(psi: np.ndarray) -> np.ndarray:
 def gpe_coeffs(N, L: float = 8.0, a: float = 0.5) -> np.ndarray:
     """Two-vortex ansatz coefficients on the torus for the box [-L, L)^3."""
     return torus_coeffs_from_samples(two_vortex_psi(N, L, a))
+
+
+# --- straight-vortex initial data of the Gross-Pitaevskii equation ---------
+
+# Diagonal Pade approximation rho_q(r) = (a1 r^2 + .. + aq r^2q) / (1 + b1 r^2
+# + .. + bq r^2q) of the density of a two-dimensional vortex (Sec. 3: the
+# density rho = f^2 solves eq. (GPErho), rho(0) = 0, rho(inf) = 1), obtained
+# by the paper's recipe: substitute rho_q into eq. (GPErho), set the first
+# 2q - 1 coefficients of the resulting series in r^2 to zero, and take
+# aq = bq (rho -> 1).  The paper uses q = 4 and does not print its
+# coefficients; q = 2 gives the exact rationals below (tests/test_gpe.py
+# re-derives them).
+PADE2_A = (11.0 / 32.0, 11.0 / 384.0)
+PADE2_B = (1.0 / 3.0, 11.0 / 384.0)
+
+
+def vortex_density(r):
+    """rho_2(r): the q = 2 Pade density of a two-dimensional vortex."""
+    r2 = np.asarray(r, dtype=np.float64) ** 2
+    return (PADE2_A[0] * r2 + PADE2_A[1] * r2 * r2) / (1.0 + PADE2_B[0] * r2 + PADE2_B[1] * r2 * r2)
+
+
+def periodic_vortex(u, v, L: float):
+    """A straight vortex crossing the (u, v) plane at the origin, made
+    periodic with period 2L in u and v: its wave function f(R) e^{i Theta},
+    with R = (L/pi) sqrt(sin^2(pi u / L) + sin^2(pi v / L)) and Theta =
+    atan2(sin(pi v / L), sin(pi u / L)).  Near the origin this is the vortex
+    f(r) e^{i theta}; the sines add its three mirror images at distance L
+    (circulations -1, -1, +1), so the winding around the periodic box is
+    zero -- the periodic counterpart of the mirroring of Sec. 3."""
+    su, sv = np.sin(np.pi * u / L), np.sin(np.pi * v / L)
+    R = (L / np.pi) * np.sqrt(su * su + sv * sv)
+    return np.sqrt(vortex_density(R)) * np.exp(1j * np.arctan2(sv, su))
+
+
+def two_vortex_initial(n: int = 64, L: float = 8.0, d: float = 1.0) -> np.ndarray:
+    """Two perpendicular straight vortices on the periodic box [-L, L)^3
+    (n^3 points x = -L + 2 L i / n): one parallel to x3 through (x1, x2) =
+    (-d, 0), one parallel to x2 through (x1, x3) = (d, 0); the initial
+    condition is the product of their wave functions (Sec. 3).  complex128
+    (n, n, n)."""
+    x = -L + (2.0 * L / n) * np.arange(n)
+    x1, x2, x3 = np.meshgrid(x, x, x, indexing="ij")
+    return (periodic_vortex(x1 + d, x2, L) * periodic_vortex(x1 - d, x3, L)).astype(np.complex128)
 
 
 # --- named workloads -------------------------------------------------------
