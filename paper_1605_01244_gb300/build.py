@@ -74,7 +74,7 @@ def build(force: bool = False, extra_flags: tuple[str, ...] = (), verbose: bool 
     tmp = SO + ".tmp%d" % os.getpid()
     lib = os.path.join(home, "lib64")
     cmd = [nvcc, "-shared", *ARCH, "-cudart", "shared", "-o", tmp, *objs,
-           "-L", lib, "-lcufft", "-lcublas", "-Xlinker", "-rpath=" + lib]
+           "-L", lib, "-lcufft", "-Xlinker", "-rpath=" + lib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

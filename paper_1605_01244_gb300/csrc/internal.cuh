@@ -181,6 +181,16 @@ cudaError_t launch_fused_series(const typename Cplx<R>::T *c, const int N[3], co
 // zeroes *rank first.
 cudaError_t launch_value_rank(const double *v, int64_t count, int *rank, cudaStream_t st);
 
+// ---- complex matrix products (cgemm.cu) -------------------------------------
+// C[b] = A[b] B[b] for b < batch (strides sA, sB, sC elements), A (M x K),
+// B (K x N) or, with transb, B(k, n) at B[n ldb + k]; row-major, complex
+// (float2 for kGemmF32, double2 otherwise).  kGemmDF: A scaled by 2^s on load
+// (scale_a) or C by 2^-s on store (scale_c), s = value_shift(vexp).
+enum { kGemmF32 = 0, kGemmF64 = 1, kGemmDF = 2 };
+cudaError_t launch_cgemm(int arith, const void *A, int64_t lda, int64_t sA, const void *B, int64_t ldb, int64_t sB,
+                         bool transb, void *C, int64_t ldc, int64_t sC, int M, int N, int K, int batch,
+                         const int *vexp, int scale_a, int scale_c, cudaStream_t st);
+
 // ---- launchers implemented in gather_df.cu ---------------------------------
 cudaError_t launch_grid_to_df(double2 *G, int64_t total, cudaStream_t st);
 cudaError_t launch_gather_df(const float4 *G, Grid3 g, int m, PointsView<double> pts,

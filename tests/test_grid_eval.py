@@ -87,3 +87,39 @@ def test_two_dimensional_grid_as_unit_third_dimension():
     pts = np.stack(np.meshgrid(y1, y2, indexing="ij"), -1).reshape(-1, 2)
     ref = nfft_cpu.direct_lowdim(c2, pts).reshape(9, 13)
     assert np.max(np.abs(f - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("scale", [0, -200, 200])
+def test_double_float_products_against_direct_sum(scale, monkeypatch):
+    """GBNFFT_GRID_DF=1: the FP64 family's contractions in double-float on the
+    FP32 pipe (about 48 significant bits), with c scaled into range by its
+    largest magnitude; against the FP64 direct sum, on shapes that leave
+    ragged edges in every tile of the product kernels."""
+    from paper_1605_01244_gb300.grid import grid_eval
+    monkeypatch.setenv("GBNFFT_GRID_DF", "1")
+    N = (20, 34, 18)
+    c = wl.gaussian_coeffs(N, 1e9, seed=56)
+    c = np.ldexp(c.real, scale) + 1j * np.ldexp(c.imag, scale)
+    g = wl.rng(57)
+    ys = [g.uniform(-0.5, 0.5, M) for M in (67, 5, 71)]
+    f = grid_eval(torch.from_numpy(c).cuda(), *[torch.from_numpy(y).cuda() for y in ys])
+    pts = np.stack(np.meshgrid(*ys, indexing="ij"), -1).reshape(-1, 3)
+    ref = oracle.forward(c, pts)
+    assert rel_l2(f.cpu().numpy().reshape(-1), ref) <= 1e-13
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-14), ("f32", 5e-6)])
+def test_products_over_several_tiles(prec, tol):
+    """Shapes spanning several 64 x 64 output tiles and K-slices with ragged
+    tails in every dimension, against the direct sum on sampled grid points."""
+    from paper_1605_01244_gb300.grid import grid_eval
+    N = (70, 66, 36)
+    c = wl.gaussian_coeffs(N, 20.0, seed=58)
+    g = wl.rng(59)
+    ys = [g.uniform(-0.5, 0.5, M) for M in (130, 67, 9)]
+    cd = torch.complex128 if prec == "f64" else torch.complex64
+    f = grid_eval(torch.from_numpy(c).to(cd).cuda(), *[torch.from_numpy(y).cuda() for y in ys]).cpu().numpy()
+    idx = [g.integers(0, len(y), 300) for y in ys]
+    pts = np.stack([ys[d][idx[d]] for d in range(3)], axis=1)
+    ref = oracle.forward(c, pts)
+    assert rel_l2(f[idx[0], idx[1], idx[2]].astype(np.complex128), ref) <= tol
