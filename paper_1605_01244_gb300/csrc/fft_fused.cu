@@ -87,6 +87,14 @@ struct ArithDF {
         return o;
     }
     static __device__ __forceinline__ C mul_i(const C &a) { return C{-a.ih, -a.il, a.rh, a.rl}; }
+    static __device__ __forceinline__ C conj(const C &a) { return C{a.rh, a.rl, -a.ih, -a.il}; }
+    // a grid value of the adjoint (FP64), split into float pairs
+    static __device__ __forceinline__ C from(double2 v) {
+        C o;
+        split_df(v.x, o.rh, o.rl);
+        split_df(v.y, o.ih, o.il);
+        return o;
+    }
     // a * (1 + i) / sqrt 2 and a * (-1 + i) / sqrt 2
     static __device__ __forceinline__ C mul_w8(const C &a) {
         float dh, dl, sh, sl;
@@ -127,6 +135,8 @@ struct ArithF32 {
         return C{fmaf(a.r, w.x, -a.i * w.y), fmaf(a.r, w.y, a.i * w.x)};
     }
     static __device__ __forceinline__ C mul_i(const C &a) { return C{-a.i, a.r}; }
+    static __device__ __forceinline__ C conj(const C &a) { return C{a.r, -a.i}; }
+    static __device__ __forceinline__ C from(float2 v) { return C{v.x, v.y}; }
     static __device__ __forceinline__ C mul_w8(const C &a) {
         constexpr float r2 = 0.70710678118654752440f;
         return C{(a.r - a.i) * r2, (a.r + a.i) * r2};
@@ -457,6 +467,128 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_out_kernel(const typename
     }
 }
 
+// ---- adjoint direction: forward DFT of the oversampled grid, band only -------
+// h_k = D1 D2 D3 sum_l H_l exp(-2 pi i k.l / n) for k in the band, as three
+// passes of line DFTs: along l1 (all n2 n3 lines, N1 band outputs kept),
+// along l2 (N1 n3 lines, N2 kept), along l3 (N1 N2 lines, N3 kept, then
+// deconvolved).  The forward sign comes from conjugation: the input is
+// conjugated once, the passes run the inverse-sign line DFT, and the output
+// is conjugated back.
+// deconvolved adjoint output of the FP64 family (range scaled back) / mixed
+template <typename R> struct AdjOut;
+template <> struct AdjOut<double> {
+    static __device__ __forceinline__ double2 get(const ArithDF::C &v, double d, int vs) {
+        return scale_value(make_double2(((double)v.rh + (double)v.rl) * d, ((double)v.ih + (double)v.il) * d), vs);
+    }
+};
+template <> struct AdjOut<float> {
+    static __device__ __forceinline__ float2 get(const ArithF32::C &v, float d, int) {
+        return make_float2(v.r * d, v.i * d);
+    }
+};
+
+// Pass 1: along l1 for each (l2, l3); in H[l1][l2][l3] (family type),
+// out A[i1][l2][l3] (N1 n2 n3).  A block takes LPB consecutive l3 of one l2.
+template <class A, typename R, int LOGL>
+__global__ void __launch_bounds__(A::kElems / 8) adj_first_kernel(const typename Cplx<R>::T *__restrict__ H,
+                                                                 const typename A::S *__restrict__ tw1,
+                                                                 typename A::S *__restrict__ out, FusedArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using S = typename A::S;
+    constexpr int L = 1 << LOGL, LPB = A::kElems / L;
+    constexpr int LS = L + (L >> A::kPadShift) + 1;
+    S *sm = reinterpret_cast<S *>(smem_raw);
+    S *tws = sm + LPB * LS;
+    const int nblk3 = (a.n3 + LPB - 1) / LPB;
+    const int l2 = blockIdx.x / nblk3;
+    const int l30 = (blockIdx.x - l2 * nblk3) * LPB;
+    const int nl = a.n3 - l30 < LPB ? a.n3 - l30 : LPB;
+    load_twiddles<A>(tws, tw1, L);
+    constexpr int STEP = (A::kElems / 8) / LPB;
+    const int line = threadIdx.x & (LPB - 1), r0 = threadIdx.x / LPB;
+    S *sl = sm + line * LS;
+    const int64_t plane = (int64_t)a.n2 * a.n3;
+    if (line < nl) {
+        const typename Cplx<R>::T *src = H + (int64_t)r0 * plane + (int64_t)l2 * a.n3 + l30 + line;
+        for (int l1 = r0; l1 < L; l1 += STEP, src += STEP * plane) sl[pidx<A>(l1)] = A::st(A::conj(A::from(*src)));
+    }
+    __syncthreads();
+    line_dft<A, LOGL>(sm, tws, LS, L / 2);
+    if (line < nl) {
+        S *dst = out + ((int64_t)r0 * a.n2 + l2) * a.n3 + l30 + line;
+        for (int i1 = r0; i1 < a.N1; i1 += STEP, dst += STEP * plane) *dst = sl[pidx<A>(band_pos(i1, a.N1, a.n1))];
+    }
+}
+
+// Pass 2: along l2 for each (i1, l3); in A[i1][l2][l3], out B[i1][i2][l3]
+// (N1 N2 n3).  A block takes LPB consecutive l3 of one i1.
+template <class A, int LOGL>
+__global__ void __launch_bounds__(A::kElems / 8) adj_mid_kernel(const typename A::S *__restrict__ in,
+                                                               const typename A::S *__restrict__ tw2,
+                                                               typename A::S *__restrict__ out, FusedArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using S = typename A::S;
+    constexpr int L = 1 << LOGL, LPB = A::kElems / L;
+    constexpr int LS = L + (L >> A::kPadShift) + 1;
+    S *sm = reinterpret_cast<S *>(smem_raw);
+    S *tws = sm + LPB * LS;
+    const int nblk3 = (a.n3 + LPB - 1) / LPB;
+    const int i1 = blockIdx.x / nblk3;
+    const int l30 = (blockIdx.x - i1 * nblk3) * LPB;
+    const int nl = a.n3 - l30 < LPB ? a.n3 - l30 : LPB;
+    load_twiddles<A>(tws, tw2, L);
+    constexpr int STEP = (A::kElems / 8) / LPB;
+    const int line = threadIdx.x & (LPB - 1), r0 = threadIdx.x / LPB;
+    S *sl = sm + line * LS;
+    if (line < nl) {
+        const S *src = in + (int64_t)i1 * a.n2 * a.n3 + l30 + line + (int64_t)r0 * a.n3;
+        for (int l2 = r0; l2 < L; l2 += STEP, src += (int64_t)STEP * a.n3) sl[pidx<A>(l2)] = *src;
+    }
+    __syncthreads();
+    line_dft<A, LOGL>(sm, tws, LS, L / 2);
+    if (line < nl) {
+        S *dst = out + (int64_t)i1 * a.N2 * a.n3 + l30 + line + (int64_t)r0 * a.n3;
+        for (int i2 = r0; i2 < a.N2; i2 += STEP, dst += (int64_t)STEP * a.n3)
+            *dst = sl[pidx<A>(band_pos(i2, a.N2, a.n2))];
+    }
+}
+
+// Pass 3: along l3 for each (i1, i2); in B[i1][i2][l3], out the deconvolved
+// band c[i1][i2][i3] (family type, conjugated back, range scaled back).
+template <class A, typename R, int LOGL>
+__global__ void __launch_bounds__(A::kElems / 8) adj_last_kernel(const typename A::S *__restrict__ in,
+                                                                const R *__restrict__ D1, const R *__restrict__ D2,
+                                                                const R *__restrict__ D3,
+                                                                const typename A::S *__restrict__ tw3,
+                                                                typename Cplx<R>::T *__restrict__ c, FusedArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using S = typename A::S;
+    constexpr int L = 1 << LOGL, LPB = A::kElems / L;
+    constexpr int LS = L + (L >> A::kPadShift) + 1;
+    S *sm = reinterpret_cast<S *>(smem_raw);
+    S *tws = sm + LPB * LS;
+    const int64_t nrows = (int64_t)a.N1 * a.N2;
+    const int64_t row0 = (int64_t)blockIdx.x * LPB;
+    load_twiddles<A>(tws, tw3, L);
+    for (int e = threadIdx.x; e < LPB * L; e += blockDim.x) {
+        const int line = e / L, l3 = e - line * L;
+        const int64_t row = row0 + line;
+        if (row < nrows) sm[line * LS + pidx<A>(l3)] = in[row * L + l3];
+    }
+    __syncthreads();
+    line_dft<A, LOGL>(sm, tws, LS, L / 2);
+    const int vs = -value_shift(a.vexp);
+    for (int e = threadIdx.x; e < LPB * a.N3; e += blockDim.x) {
+        const int line = (int)a.divN3.div((unsigned)e), i3 = e - line * a.N3;
+        const int64_t row = row0 + line;
+        if (row >= nrows) continue;
+        const int i1 = (int)a.divN2.div((unsigned)row), i2 = (int)(row - (int64_t)i1 * a.N2);
+        const R d = D1[i1] * D2[i2] * D3[i3];
+        const typename A::C v = A::conj(A::ld(sm[line * LS + pidx<A>(band_pos(i3, a.N3, a.n3))]));
+        c[row * a.N3 + i3] = AdjOut<R>::get(v, d, vs);
+    }
+}
+
 int ilog2(int v) {
     int r = 0;
     while ((1 << r) < v) ++r;
@@ -558,23 +690,69 @@ cudaError_t run_fused(const typename Cplx<R>::T *c, const R *D1, const R *D2, co
     return e;
 }
 
-}  // namespace
-
-bool fused_supported(const int n[3]) {
-    for (int d = 0; d < 3; ++d)
-        if (n[d] < 16 || n[d] > 2048 || (n[d] & (n[d] - 1))) return false;
-    return true;
+template <class A, typename R, int LOGL>
+cudaError_t launch_adj_first(const typename Cplx<R>::T *H, const typename A::S *tw, typename A::S *out,
+                             const FusedArgs &a, cudaStream_t st) {
+    const size_t sm = line_smem<A>(1 << LOGL);
+    cudaError_t e = cudaFuncSetAttribute(adj_first_kernel<A, R, LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    const int lpb = A::kElems >> LOGL;
+    adj_first_kernel<A, R, LOGL><<<(unsigned)(a.n2 * ((a.n3 + lpb - 1) / lpb)), A::kElems / 8, sm, st>>>(H, tw, out,
+                                                                                                         a);
+    return cudaGetLastError();
 }
 
-size_t fused_scratch_bytes(const int N[3], const int n[3], int ng, int prec) {
-    const size_t elem = prec == 64 ? 16 : 8;
-    return elem * (size_t)ng * ((size_t)N[0] * N[1] * n[2] + (size_t)N[0] * n[1] * n[2]);
+template <class A, int LOGL>
+cudaError_t launch_adj_mid(const typename A::S *in, const typename A::S *tw, typename A::S *out, const FusedArgs &a,
+                           cudaStream_t st) {
+    const size_t sm = line_smem<A>(1 << LOGL);
+    cudaError_t e =
+        cudaFuncSetAttribute(adj_mid_kernel<A, LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int lpb = A::kElems >> LOGL;
+    adj_mid_kernel<A, LOGL><<<(unsigned)(a.N1 * ((a.n3 + lpb - 1) / lpb)), A::kElems / 8, sm, st>>>(in, tw, out, a);
+    return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_fused_series(const typename Cplx<R>::T *c, const int N[3], const int n[3], const R *D1,
-                                const R *D2, const R *D3, const void *const tw[3], void *scratch,
-                                void *P, int m, int shift, int ng, const int *vexp, cudaStream_t st) {
+template <class A, typename R, int LOGL>
+cudaError_t launch_adj_last(const typename A::S *in, const R *D1, const R *D2, const R *D3, const typename A::S *tw,
+                            typename Cplx<R>::T *c, const FusedArgs &a, cudaStream_t st) {
+    const size_t sm = line_smem<A>(1 << LOGL);
+    cudaError_t e = cudaFuncSetAttribute(adj_last_kernel<A, R, LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    const int64_t rows = (int64_t)a.N1 * a.N2, lpb = A::kElems >> LOGL;
+    adj_last_kernel<A, R, LOGL><<<(unsigned)((rows + lpb - 1) / lpb), A::kElems / 8, sm, st>>>(in, D1, D2, D3, tw,
+                                                                                              c, a);
+    return cudaGetLastError();
+}
+
+template <class A, typename R>
+cudaError_t run_adjoint(const typename Cplx<R>::T *H, const R *D1, const R *D2, const R *D3, const void *const tw[3],
+                        void *scratch, typename Cplx<R>::T *c, const FusedArgs &a, cudaStream_t st) {
+    using S = typename A::S;
+    S *Abuf = (S *)scratch;                                   // N1 n2 n3
+    S *Bbuf = Abuf + (int64_t)a.N1 * a.n2 * a.n3;             // N1 N2 n3
+    cudaError_t e;
+    {
+#define GBNFFT_CALL(L) launch_adj_first<A, R, L>(H, (const S *)tw[0], Abuf, a, st)
+        e = [&]() -> cudaError_t { GBNFFT_LOGL_SWITCH(a.logn1, GBNFFT_CALL) }();
+#undef GBNFFT_CALL
+    }
+    if (e != cudaSuccess) return e;
+    {
+#define GBNFFT_CALL(L) launch_adj_mid<A, L>(Abuf, (const S *)tw[1], Bbuf, a, st)
+        e = [&]() -> cudaError_t { GBNFFT_LOGL_SWITCH(a.logn2, GBNFFT_CALL) }();
+#undef GBNFFT_CALL
+    }
+    if (e != cudaSuccess) return e;
+#define GBNFFT_CALL(L) launch_adj_last<A, R, L>(Bbuf, D1, D2, D3, (const S *)tw[2], c, a, st)
+    GBNFFT_LOGL_SWITCH(a.logn3, GBNFFT_CALL)
+#undef GBNFFT_CALL
+}
+
+FusedArgs make_args(const int N[3], const int n[3], int m, int shift, int ng, const int *vexp) {
     FusedArgs a;
     a.vexp = vexp;
     a.N1 = N[0];
@@ -591,6 +769,45 @@ cudaError_t launch_fused_series(const typename Cplx<R>::T *c, const int N[3], co
     a.ng = ng;
     a.divN2 = make_fastdiv((unsigned)N[1]);
     a.divN3 = make_fastdiv((unsigned)N[2]);
+    return a;
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_fused_adjoint(const typename Cplx<R>::T *H, const int N[3], const int n[3], const R *D1,
+                                 const R *D2, const R *D3, const void *const tw[3], void *scratch,
+                                 typename Cplx<R>::T *c, const int *vexp, cudaStream_t st) {
+    const FusedArgs a = make_args(N, n, 0, 0, 1, vexp);
+    if constexpr (sizeof(R) == 8)
+        return run_adjoint<ArithDF, R>(H, D1, D2, D3, tw, scratch, c, a, st);
+    else
+        return run_adjoint<ArithF32, R>(H, D1, D2, D3, tw, scratch, c, a, st);
+}
+
+template cudaError_t launch_fused_adjoint<double>(const double2 *, const int[3], const int[3], const double *,
+                                                  const double *, const double *, const void *const[3], void *,
+                                                  double2 *, const int *, cudaStream_t);
+template cudaError_t launch_fused_adjoint<float>(const float2 *, const int[3], const int[3], const float *,
+                                                 const float *, const float *, const void *const[3], void *,
+                                                 float2 *, const int *, cudaStream_t);
+
+bool fused_supported(const int n[3]) {
+    for (int d = 0; d < 3; ++d)
+        if (n[d] < 16 || n[d] > 2048 || (n[d] & (n[d] - 1))) return false;
+    return true;
+}
+
+size_t fused_scratch_bytes(const int N[3], const int n[3], int ng, int prec) {
+    const size_t elem = prec == 64 ? 16 : 8;
+    return elem * (size_t)ng * ((size_t)N[0] * N[1] * n[2] + (size_t)N[0] * n[1] * n[2]);
+}
+
+template <typename R>
+cudaError_t launch_fused_series(const typename Cplx<R>::T *c, const int N[3], const int n[3], const R *D1,
+                                const R *D2, const R *D3, const void *const tw[3], void *scratch,
+                                void *P, int m, int shift, int ng, const int *vexp, cudaStream_t st) {
+    const FusedArgs a = make_args(N, n, m, shift, ng, vexp);
     if constexpr (sizeof(R) == 8)
         return run_fused<ArithDF, R>(c, D1, D2, D3, tw, scratch, P, a, st);
     else

@@ -176,6 +176,14 @@ cudaError_t launch_fused_series(const typename Cplx<R>::T *c, const int N[3], co
                                 const R *D2, const R *D3, const void *const tw[3], void *scratch,
                                 void *P, int m, int shift, int ng, const int *vexp, cudaStream_t st);
 
+// Adjoint direction of the same passes: c_out[k] = D1 D2 D3 sum_l H_l
+// exp(-2 pi i k.l / n) for k in the band (FP64 family: double-float passes,
+// output scaled by 2^-s; the scratch of fused_scratch_bytes(N, n, 1, prec)).
+template <typename R>
+cudaError_t launch_fused_adjoint(const typename Cplx<R>::T *H, const int N[3], const int n[3], const R *D1,
+                                 const R *D2, const R *D3, const void *const tw[3], void *scratch,
+                                 typename Cplx<R>::T *c, const int *vexp, cudaStream_t st);
+
 // ---- range scaling (range.cu) -----------------------------------------------
 // *rank = max(*rank, value_rank of each of the count doubles at v); the caller
 // zeroes *rank first.

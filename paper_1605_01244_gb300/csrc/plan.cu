@@ -411,6 +411,10 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         // point with global atomics only (GBNFFT_SPREAD=direct)
         const char *sp = std::getenv("GBNFFT_SPREAD");
         p->spread_direct = sp && !std::strcmp(sp, "direct");
+        // GBNFFT_ADJ_FFT=cufft: the adjoint's forward FFT by cuFFT plus the
+        // deconvolution kernel instead of the fused passes
+        const char *af = std::getenv("GBNFFT_ADJ_FFT");
+        p->adj_cufft = af && !std::strcmp(af, "cufft");
         // GBNFFT_TMA_FIRST_WAIT: polls of the tile-staged gather's first
         // mbarrier wait (failure-detection test only; default: the full limit)
         const char *fw = std::getenv("GBNFFT_TMA_FIRST_WAIT");
@@ -1051,14 +1055,28 @@ template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
         e = launch_spread<R>((const C *)f, g, p->m, pv, win_table<R>(p), H, p->stream);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     rec_mark(p, rec, 1);
+    p->launches += p->M > 0 ? 1 : 0;   // the spread
+    if (p->fused && !p->adj_cufft) {
+        // forward DFT of the band and deconvolution in three line passes
+        st = ensure_fscratch(p, 1);
+        if (st != NFFT3_OK) return st;
+        const void *tw[3] = {p->tw[0], p->tw[1], p->tw[2]};
+        e = launch_fused_adjoint<R>(H, p->N, p->n, (const R *)p->D[0], (const R *)p->D[1], (const R *)p->D[2], tw,
+                                    p->fscratch, (C *)c_out, avexp, p->stream);
+        p->launches += 3;
+        rec_mark(p, rec, 2);
+        rec_mark(p, rec, 3);
+        rec_end(p, rec, 3);
+        return finish(p, cuda_status(e));
+    }
     st = exec_grid_fft(p, H, prec, CUFFT_FORWARD, 1);
     if (st != NFFT3_OK) return st;
     rec_mark(p, rec, 2);
     e = launch_deconv_gather<R>(H, g, (const R *)p->D[0], (const R *)p->D[1], (const R *)p->D[2],
                                 p->N[0], p->N[1], p->N[2], (C *)c_out, avexp, p->stream);
+    p->launches += 1;
     rec_mark(p, rec, 3);
     rec_end(p, rec, 3);
-    p->launches += p->M > 0 ? 2 : 1;
     return finish(p, cuda_status(e));
 }
 

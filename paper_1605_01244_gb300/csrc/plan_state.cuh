@@ -26,6 +26,7 @@ struct nfft3_plan_s {
     int df_weights_fp64;       // GBNFFT_DF_WEIGHTS: FP64-pipe weights (default) or df ("df")
     int gather_mode;           // GBNFFT_GATHER: 0 col (default), 1 thread, 2 native (see plan.cu)
     int spread_direct;         // GBNFFT_SPREAD=direct: one thread per point, global atomics only
+    int adj_cufft;             // GBNFFT_ADJ_FFT=cufft: adjoint transform by cuFFT + deconvolution kernel
     unsigned tma_first_wait;   // GBNFFT_TMA_FIRST_WAIT (test of the tile-staged gather's bounded wait)
     // tables and grid
     void *D[3];               // deconvolution factors, real type of the family

@@ -10,7 +10,7 @@
 // spread_tile_kernel (FP64 at m = 8, whose box and staged weights exceed
 // shared memory) has warps take points, the lanes of a warp take the (b, c)
 // node pairs of a stencil plane, and shared-memory atomics resolve the rest.
-#include "internal.cuh"
+#include "col_common.cuh"
 
 namespace gbnfft {
 namespace {
@@ -220,10 +220,15 @@ __global__ void __launch_bounds__(32 * (kTile + 2 * MM), 1) spread_tile_df_kerne
             const int b = slot / W, c = slot - b * W;
             const float2 w23 = df2_mul(wi[W + b], wi[2 * W + c]);
             float4 &node = row[(o.y + b) * B + (o.z + c)];
-            const float4 v = node;
-            const float2 re = df2_add(make_float2(v.x, v.y), df2_mul(fr, w23));
-            const float2 im = df2_add(make_float2(v.z, v.w), df2_mul(fi, w23));
-            node = make_float4(re.x, re.y, im.x, im.y);
+            // node += f w1 w23: exact product, two-sum into the high part,
+            // errors into the low part, renormalised so that the low part
+            // stays below half an ulp of the high part
+            float4 v = node;
+            df_mac(v.x, v.y, fr.x, fr.y, w23.x, w23.y);
+            df_mac(v.z, v.w, fi.x, fi.y, w23.x, w23.y);
+            df_norm(v.x, v.y);
+            df_norm(v.z, v.w);
+            node = v;
         }
     }
     __syncthreads();

@@ -535,3 +535,33 @@ def test_tiled_spread_matches_direct_and_cpu(prec, m, N, monkeypatch):
         # less accurate than the direct one
         e_tiles, e_direct = rel_l2(out["tiles"], hc), rel_l2(out["direct"], hc)
         assert e_tiles <= max(2 * e_direct, 1e-6), (e_tiles, e_direct)
+
+
+@pytest.mark.parametrize("N", [(16, 32, 8), (8, 1024, 8), (64, 64, 64)])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_fused_adjoint_transform(N, prec, monkeypatch):
+    """The adjoint's forward DFT of the band and deconvolution as three fused
+    line passes (default for power-of-two grids; double-float in the FP64
+    family) against the cuFFT transform plus deconvolution kernel
+    (GBNFFT_ADJ_FFT=cufft) and the CPU NFFT restatement, for line lengths 16
+    to 2048."""
+    from paper_1605_01244_gb300 import Plan
+    x = wl.mixed_points(1500, 0.05, seed=71)
+    g = wl.rng(72)
+    f = g.standard_normal(len(x)) + 1j * g.standard_normal(len(x))
+    out = {}
+    for mode in ("fused", "cufft"):
+        if mode == "cufft":
+            monkeypatch.setenv("GBNFFT_ADJ_FFT", "cufft")
+        else:
+            monkeypatch.delenv("GBNFFT_ADJ_FFT", raising=False)
+        plan = Plan(N, len(x), m=5, precision=prec)
+        plan.set_points(to_dev(x))
+        out[mode] = to_np(plan.adjoint(to_dev(f, CD[prec]))).astype(np.complex128)
+    hc = nfft_cpu.adjoint(f, x, N, plan.n, 5)
+    if prec == "f64":
+        assert max_rel(out["fused"], hc) <= 1e-12
+        assert max_rel(out["fused"], out["cufft"]) <= 1e-12
+    else:
+        assert rel_l2(out["fused"], hc) <= 2e-6
+        assert rel_l2(out["fused"], out["cufft"]) <= 2e-6
