@@ -410,6 +410,27 @@ def run_ours(args, rank, world, local):
         _lib.lib().nfft3_timing_enable(plan._h, 0)
         adj_stages = {nm: (st_ms[i] / st_n[i] if st_n[i] else 0.0) for i, nm in enumerate(_lib.STAGES)
                       if nm in ("spread", "fft_fwd", "deconv_adj")}
+        adj_det = None
+        if fam == "f64":
+            # deterministic mode: stable point order, fixed-point spread flushes
+            plan.set_deterministic(True)
+            plan.set_points(x)
+            plan.adjoint(f, out=h_out)
+            barrier()
+            e0.record(s)
+            for _ in range(min(args.steps, 3)):
+                plan.set_points(x)
+            e1.record(s)
+            barrier()
+            sp_det_ms = e0.elapsed_time(e1) / min(args.steps, 3)
+            e0.record(s)
+            for _ in range(min(args.steps, 3)):
+                plan.adjoint(f, out=h_out)
+            e1.record(s)
+            barrier()
+            adj_det = {"ms": e0.elapsed_time(e1) / min(args.steps, 3), "set_points_ms": sp_det_ms}
+            plan.set_deterministic(False)
+            plan.set_points(x)
         del h_out
         # accuracy on the fixed subsample (oracle on rank 0's host; computed later)
         idx = np.concatenate([wl.rng(99).choice(M // 2, SUBSAMPLE, replace=False),
@@ -460,7 +481,7 @@ def run_ours(args, rank, world, local):
                             "%.0f %% of it" % (w, w, w, l1_floor_ms, 100 * l1_floor_ms / g_ms))
         results[fam] = {
             "m": m, "ms_per_step": ms, "ms_eval_only": ms_eval, "e2e_ms": e2e_ms, "grad_ms": grad_ms,
-            "adj_ms": adj_ms, "adj_stages": adj_stages,
+            "adj_ms": adj_ms, "adj_stages": adj_stages, "adj_det": adj_det,
             "stages_ms": stages, "launches_per_step": launches.value / args.steps,
             "clocks": clocks, "roofline": roof, "f_sub": f_sub, "idx": idx,
             "h2d": M * 3 * 8 + N ** 3 * 2 * rb, "d2h": M * 2 * rb,
@@ -510,7 +531,8 @@ def run_ours(args, rank, world, local):
             "eval_only_mpoints_s": pts / (r["ms_eval_only"] * 1e-3) / 1e6,
             "gradient_mpoints_s": {k: pts / (v * 1e-3) / 1e6 for k, v in r["grad_ms"].items()},
             "adjoint": {"mpoints_s": pts / (r["adj_ms"] * 1e-3) / 1e6, "ms": r["adj_ms"],
-                        "stages_ms": r["adj_stages"]},
+                        "stages_ms": r["adj_stages"],
+                        **({"deterministic": r["adj_det"]} if r["adj_det"] else {})},
             "stages_ms": r["stages_ms"], "roofline": r["roofline"],
             "fft_share": r["stages_ms"]["fft"] / max(sum(r["stages_ms"].values()), 1e-12),
             "e2e": {"value": pts / (r["e2e_ms"] * 1e-3) / 1e6, "unit": "Mpoints/s",

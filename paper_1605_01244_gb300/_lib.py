@@ -39,6 +39,7 @@ SIGNATURES = {
     "nfft3d_eval_grad": (_I, [_P, _P, _P, _P]),
     "nfft3f_eval_grad": (_I, [_P, _P, _P, _P]),
     "nfft3d_eval_grad_noalloc": (_I, [_P, _P, _P, _P]),
+    "nfft3_set_deterministic": (_I, [_P, _I]),
     "gpe_plan_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _D, _D, _D, _P]),
     "gpe_steps": (_I, [_P, _P, _D, _I]),
     "gpe_mass_energy": (_I, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),

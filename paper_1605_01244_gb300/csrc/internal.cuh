@@ -250,10 +250,14 @@ cudaError_t launch_spread(const typename Cplx<R>::T *f, Grid3 g, int m, PointsVi
                           const WinTable<R> &w, typename Cplx<R>::T *H, cudaStream_t st);
 // Adjoint spread through shared-memory tile boxes (spread_tile.cu): one block
 // per chunk of the set_points chunk list.
+// Hq non-null (FP64 family, m <= 7): the boxes are flushed as exact
+// fixed-point sums into Hq (four int64 limbs per node, zeroed by the caller)
+// instead of FP64 atomics into H; launch_fixed_to_grid then writes H.
 template <typename R>
 cudaError_t launch_spread_tiles(const typename Cplx<R>::T *f, Grid3 g, int m, PointsView<R> pts,
                                 const WinTable<R> &w, const WinTableDF *wdf, const int4 *chunks, int nchunks,
-                                int nt2, int nt3, typename Cplx<R>::T *H, cudaStream_t st);
+                                int nt2, int nt3, typename Cplx<R>::T *H, unsigned long long *Hq, cudaStream_t st);
+cudaError_t launch_fixed_to_grid(const unsigned long long *Hq, double2 *H, int64_t total, cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_deconv_gather(const typename Cplx<R>::T *H, Grid3 g, const R *D1, const R *D2,
@@ -327,9 +331,25 @@ cudaError_t launch_gather_tma_f32(const void *tmap, const int4 *chunks, int nchu
                                   Grid3 g, int m, PointsView<float> pts, const WinTable<float> &w,
                                   float2 *f, int *status, unsigned first_wait_limit, cudaStream_t st);
 
+// Buffers of the stable (deterministic) point order: a second permutation
+// buffer (M_cap ints), per-pass digit counts and offsets
+// (stable_sort_count_ints each) and the scan's temporary.
+struct StableSort {
+    int *buf;
+    int *counts;
+    int *offsets;
+    int *scan_tmp;
+};
+size_t stable_sort_count_ints(int64_t M_cap);
+// kernels launch_points adds with a stable sort, in place of one
+int stable_sort_launches(const PointsBuild &pb);
+
+// stable: nullptr for the default order (by key; the order within a key
+// follows the count pass's atomics), else points within a key keep their
+// original order.
 template <typename R>
 cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R *s2, R *s3,
-                          cudaStream_t st);
+                          cudaStream_t st, const StableSort *stable);
 
 // Chunk list from tile_start (after launch_points); the number of chunks is
 // left in chunk_start[ntile].

@@ -43,6 +43,18 @@ void dev_free(void *&ptr) {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? NFFT3_OK : NFFT3_ERR_CUDA; }
 
+void release_deterministic(nfft3_plan p) {
+    void *v;
+    v = p->ss.buf; dev_free(v);
+    v = p->ss.counts; dev_free(v);
+    v = p->ss.offsets; dev_free(v);
+    v = p->ss.scan_tmp; dev_free(v);
+    v = p->Hq; dev_free(v);
+    p->ss = StableSort{nullptr, nullptr, nullptr, nullptr};
+    p->Hq = nullptr;
+    p->det = 0;
+}
+
 // Twiddle table exp(+2 pi i j / n_d), j in [0, n_d), from long double cos/sin:
 // double-float (cos_hi, cos_lo, sin_hi, sin_lo) for the FP64 family, float2
 // for the mixed family.
@@ -339,6 +351,7 @@ void release(nfft3_plan p) {
     v = p->pb.tile_sparse_start; dev_free(v);
     v = p->pb.batches; dev_free(v);
     v = p->pb.sparse_idx; dev_free(v);
+    release_deterministic(p);
     v = p->x_dev; dev_free(v);
     dev_free(p->c_dev);
     dev_free(p->f_dev);
@@ -632,14 +645,16 @@ int set_points_impl(nfft3_plan p, const double *x, int prec) {
     p->split_ok = 0;
     const int rec = rec_begin(p, kRecSetPoints);
     cudaError_t e;
+    const StableSort *stable = p->det ? &p->ss : nullptr;
     if (prec == 64)
         e = launch_points<double>(x, p->pb, p->key, (double *)p->s[0], (double *)p->s[1],
-                                  (double *)p->s[2], p->stream);
+                                  (double *)p->s[2], p->stream, stable);
     else
         e = launch_points<float>(x, p->pb, p->key, (float *)p->s[0], (float *)p->s[1],
-                                 (float *)p->s[2], p->stream);
+                                 (float *)p->s[2], p->stream, stable);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     p->launches += (p->M > 0 ? 4 : 1) + scan_launches(p->pb.nkey + 1);
+    if (stable) p->launches += stable_sort_launches(p->pb);
     if (launch_chunks(p->pb, p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
     p->launches += 2 + scan_launches(p->pb.ntile + 1);
     const bool split = p->pb.dense_min > 0 && p->M > 0;
@@ -1046,13 +1061,25 @@ template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
     if (st != NFFT3_OK) return st;
     PointsView<R> pv = points_view<R>(p);
     pv.vexp = avexp;
-    cudaError_t e = cudaMemsetAsync(H, 0, sizeof(C) * nn, p->stream);
-    if (e != cudaSuccess) return NFFT3_ERR_CUDA;
-    if (!p->spread_direct && p->nchunks > 0)
-        e = launch_spread_tiles<R>((const C *)f, g, p->m, pv, win_table<R>(p), prec == 64 ? &p->wtdf : nullptr,
-                                   p->pb.chunks, p->nchunks, p->pb.nt2, p->pb.nt3, H, p->stream);
-    else
-        e = launch_spread<R>((const C *)f, g, p->m, pv, win_table<R>(p), H, p->stream);
+    cudaError_t e;
+    if (p->det) {
+        // deterministic: the tile spread flushes exact fixed-point sums
+        if (prec != 64 || p->m > 7 || p->spread_direct) return NFFT3_ERR_ARG;
+        e = cudaMemsetAsync(p->Hq, 0, 4 * sizeof(unsigned long long) * nn, p->stream);
+        if (e == cudaSuccess && p->nchunks > 0)
+            e = launch_spread_tiles<R>((const C *)f, g, p->m, pv, win_table<R>(p), &p->wtdf, p->pb.chunks,
+                                       p->nchunks, p->pb.nt2, p->pb.nt3, H, p->Hq, p->stream);
+        if (e == cudaSuccess) e = launch_fixed_to_grid(p->Hq, (double2 *)H, nn, p->stream);
+        p->launches += 1;
+    } else {
+        e = cudaMemsetAsync(H, 0, sizeof(C) * nn, p->stream);
+        if (e != cudaSuccess) return NFFT3_ERR_CUDA;
+        if (!p->spread_direct && p->nchunks > 0)
+            e = launch_spread_tiles<R>((const C *)f, g, p->m, pv, win_table<R>(p), prec == 64 ? &p->wtdf : nullptr,
+                                       p->pb.chunks, p->nchunks, p->pb.nt2, p->pb.nt3, H, nullptr, p->stream);
+        else
+            e = launch_spread<R>((const C *)f, g, p->m, pv, win_table<R>(p), H, p->stream);
+    }
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     rec_mark(p, rec, 1);
     p->launches += p->M > 0 ? 1 : 0;   // the spread
@@ -1268,6 +1295,32 @@ int nfft3_sync(nfft3_plan p) {
     if (cudaStreamSynchronize(p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
     if (status & 2) return NFFT3_ERR_CUDA;   // a tile-staged gather gave up waiting for its copy
     return cudaGetLastError() == cudaSuccess ? NFFT3_OK : NFFT3_ERR_CUDA;
+}
+
+int nfft3_set_deterministic(nfft3_plan p, int on) {
+    if (!p) return NFFT3_ERR_ARG;
+    p->points_ok = 0;   // the point order changes: set_points must follow
+    if (!on) {
+        release_deterministic(p);
+        return NFFT3_OK;
+    }
+    if (p->det) return NFFT3_OK;
+    if (p->prec != 64 || p->m > 7) return NFFT3_ERR_ARG;
+    const int64_t nn = (int64_t)p->n[0] * p->n[1] * p->n[2];
+    const size_t cnt = stable_sort_count_ints(p->M_cap);
+    void *v = nullptr;
+    int st = dev_alloc(p, &v, sizeof(int) * (p->M_cap + 1));
+    p->ss.buf = (int *)v;
+    if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * cnt), p->ss.counts = (int *)v;
+    if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * cnt), p->ss.offsets = (int *)v;
+    if (st == NFFT3_OK) st = dev_alloc(p, &v, sizeof(int) * scan_tmp_ints((int64_t)cnt)), p->ss.scan_tmp = (int *)v;
+    if (st == NFFT3_OK) st = dev_alloc(p, &v, 4 * sizeof(unsigned long long) * nn), p->Hq = (unsigned long long *)v;
+    if (st != NFFT3_OK) {
+        release_deterministic(p);
+        return st;
+    }
+    p->det = 1;
+    return NFFT3_OK;
 }
 
 int nfft3_timing_enable(nfft3_plan p, int on) {

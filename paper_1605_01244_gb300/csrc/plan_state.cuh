@@ -81,6 +81,11 @@ struct nfft3_plan_s {
     double stage_ms[NFFT3_NSTAGES];
     int64_t stage_calls[NFFT3_NSTAGES];
     int64_t launches;         // kernels this library enqueued (cuFFT's own not counted)
+    // deterministic mode (nfft3_set_deterministic): stable point order and
+    // exact fixed-point flushes of the adjoint spread
+    int det;
+    gbnfft::StableSort ss;
+    unsigned long long *Hq;   // n1 n2 n3 x 4 int64 limbs
 };
 
 // Set-up of the allocation-free entry point on the plan's device (noalloc.cu):

@@ -279,6 +279,77 @@ __global__ void __launch_bounds__(256) split_fill_kernel(PointsBuild pb) {
     }
 }
 
+// ---- stable order (deterministic mode) --------------------------------------
+// An LSD radix sort of the point indices by sort key, kRadixBits per pass:
+// each pass is a stable counting sort (per-block digit histograms, a scan
+// over (digit, block), then a scatter that ranks every block's elements in
+// their order), so the result lists the points by key and, within a key, by
+// original index -- independent of scheduling.
+constexpr int kRadixBits = 8, kRadixBins = 1 << kRadixBits, kRadixThreads = 256, kRadixBlock = 4096;
+
+__device__ __forceinline__ int radix_digit(const int2 *key_rank, const int *vin, int64_t e, int shift, int &j) {
+    j = vin ? vin[e] : (int)e;
+    return (key_rank[j].x >> shift) & (kRadixBins - 1);
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const int2 *__restrict__ key_rank,
+                                                                   const int *__restrict__ vin, int64_t M,
+                                                                   int shift, int *__restrict__ counts,
+                                                                   int nblocks) {
+    __shared__ int h[kRadixBins];
+    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) h[d] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixBlock;
+    for (int i = threadIdx.x; i < kRadixBlock; i += blockDim.x) {
+        const int64_t e = base + i;
+        if (e >= M) break;
+        int j;
+        atomicAdd(&h[radix_digit(key_rank, vin, e, shift, j)], 1);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) counts[(int64_t)d * nblocks + blockIdx.x] = h[d];
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(const int2 *__restrict__ key_rank,
+                                                                      const int *__restrict__ vin,
+                                                                      int *__restrict__ vout, int64_t M, int shift,
+                                                                      const int *__restrict__ offsets, int nblocks) {
+    constexpr int NW = kRadixThreads / 32;
+    __shared__ int running[kRadixBins];
+    __shared__ int wcount[NW][kRadixBins];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) {
+        running[d] = offsets[(int64_t)d * nblocks + blockIdx.x];
+        for (int w = 0; w < NW; ++w) wcount[w][d] = 0;
+    }
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixBlock;
+    for (int r = 0; r < kRadixBlock / kRadixThreads; ++r) {
+        // element e of this round: its rank among the block's earlier elements
+        // of the same digit = the running count + the earlier warps' counts in
+        // this round + the lower lanes of its own warp with the same digit
+        const int64_t e = base + (int64_t)r * kRadixThreads + threadIdx.x;
+        const bool valid = e < M;
+        int j = 0, d = kRadixBins;   // invalid lanes match each other only
+        if (valid) d = radix_digit(key_rank, vin, e, shift, j);
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        if (valid && lane == leader) wcount[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int pos = running[d] + __popc(peers & ((1u << lane) - 1u));
+            for (int w = 0; w < warp; ++w) pos += wcount[w][d];
+            vout[pos] = j;
+        }
+        __syncthreads();
+        if (valid && lane == leader) {
+            atomicAdd(&running[d], __popc(peers));
+            wcount[warp][d] = 0;
+        }
+        __syncthreads();
+    }
+}
+
 int point_blocks(int64_t M) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -325,9 +396,41 @@ int scan_launches(int64_t n) {
     return nb == 1 ? 1 : 2 + scan_launches(nb);
 }
 
+int64_t radix_blocks(int64_t M) { return ceil_div(M > 0 ? M : 1, kRadixBlock); }
+int radix_passes(int64_t nkey) {
+    int bits = 1;
+    while (bits < 31 && ((int64_t)1 << bits) < nkey) ++bits;
+    return (bits + kRadixBits - 1) / kRadixBits;
+}
+
+// The stable permutation (sorted position -> original index) into one of the
+// two buffers; returns it in *perm_out.
+cudaError_t stable_perm(PointsBuild &pb, int *bufA, int *bufB, const StableSort &ss, int **perm_out,
+                        cudaStream_t st) {
+    const int64_t nb = radix_blocks(pb.M);
+    const int passes = radix_passes(pb.nkey);
+    const int *vin = nullptr;
+    int *vout = bufA;
+    for (int ps = 0; ps < passes; ++ps) {
+        const int shift = ps * kRadixBits;
+        radix_hist_kernel<<<(unsigned)nb, kRadixThreads, 0, st>>>(pb.key_rank, vin, pb.M, shift, ss.counts, (int)nb);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = exclusive_scan(ss.counts, ss.offsets, (int64_t)kRadixBins * nb, ss.scan_tmp, st);
+        if (e != cudaSuccess) return e;
+        radix_scatter_kernel<<<(unsigned)nb, kRadixThreads, 0, st>>>(pb.key_rank, vin, vout, pb.M, shift, ss.offsets,
+                                                                     (int)nb);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        vin = vout;
+        vout = vout == bufA ? bufB : bufA;
+    }
+    *perm_out = const_cast<int *>(vin);
+    return cudaSuccess;
+}
+
 template <typename R>
 cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R *s2, R *s3,
-                          cudaStream_t st) {
+                          cudaStream_t st, const StableSort *stable) {
     // key_count has nkey + 1 entries; the extra zero makes key_start[nkey] = M.
     cudaError_t e = cudaMemsetAsync(pb.key_count, 0, sizeof(int) * (pb.nkey + 1), st);
     if (e != cudaSuccess) return e;
@@ -344,12 +447,26 @@ cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R 
     tile_start_kernel<<<point_blocks(pb.ntile + 1), 256, 0, st>>>(pb);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (pb.M > 0) {
-        points_perm_kernel<<<point_blocks(pb.M), 256, 0, st>>>(pb, perm);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (stable) {
+            // deterministic order: by key, then by original index
+            int *sorted = nullptr;
+            if ((e = stable_perm(pb, perm, stable->buf, *stable, &sorted, st)) != cudaSuccess) return e;
+            perm = sorted;
+        } else {
+            points_perm_kernel<<<point_blocks(pb.M), 256, 0, st>>>(pb, perm);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
         points_gather_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(pb, rec, perm, key, s1, s2, s3);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+size_t stable_sort_count_ints(int64_t M_cap) { return (size_t)kRadixBins * (size_t)radix_blocks(M_cap); }
+
+int stable_sort_launches(const PointsBuild &pb) {
+    if (pb.M <= 0) return 0;
+    return radix_passes(pb.nkey) * (2 + scan_launches((int64_t)kRadixBins * radix_blocks(pb.M))) - 1;
 }
 
 cudaError_t launch_chunks(PointsBuild &pb, cudaStream_t st) {
@@ -381,9 +498,9 @@ cudaError_t launch_split_lists(PointsBuild &pb, cudaStream_t st) {
 int split_list_launches(const PointsBuild &pb) { return 2 + 2 * scan_launches(pb.ntile + 1); }
 
 template cudaError_t launch_points<double>(const double *, PointsBuild &, int4 *, double *,
-                                           double *, double *, cudaStream_t);
+                                           double *, double *, cudaStream_t, const StableSort *);
 template cudaError_t launch_points<float>(const double *, PointsBuild &, int4 *, float *, float *,
-                                          float *, cudaStream_t);
+                                          float *, cudaStream_t, const StableSort *);
 
 }  // namespace gbnfft
 

@@ -157,10 +157,55 @@ __device__ __forceinline__ double f2d_bits(float x) {
                                             ((unsigned long long)(u & 0x7FFFFFu) << 29)));
 }
 
-template <int MM>
+// ---- deterministic flush: exact fixed-point sums ----------------------------
+// A float x = M 2^(E - 150) (normal, biased exponent E) as fixed point at
+// resolution 2^-60 in two limbs, x ~ hi 2^-30 + lo 2^-60 with |lo| < 2^30,
+// bits below 2^-60 dropped (zero and subnormal floats give 0).  Box values
+// are below 2^9 in magnitude (f is scaled into [1, 2), at most kChunk points
+// with weights <= 1), so hi < 2^39 and a node's sums of at most 2^24 flushes
+// stay in int64.  Integer addition is exact and commutative, so the grid
+// does not depend on the order of the flushes.
+__device__ __forceinline__ void fixed_limbs(float x, long long &hi, long long &lo) {
+    const unsigned u = __float_as_uint(x);
+    const int E = (int)((u >> 23) & 0xFFu);
+    if (E == 0) {
+        hi = lo = 0;
+        return;
+    }
+    const unsigned long long M = (u & 0x7FFFFFu) | 0x800000u;
+    const int k = E - 90;   // x 2^60 = M 2^k
+    unsigned long long h, l;
+    if (k >= 30) {
+        h = M << (k - 30 < 40 ? k - 30 : 40);
+        l = 0;
+    } else if (k >= 0) {
+        const unsigned long long F = M << k;
+        h = F >> 30;
+        l = F & ((1ull << 30) - 1);
+    } else {
+        h = 0;
+        l = -k < 32 ? M >> -k : 0;
+    }
+    const bool neg = (u >> 31) != 0;
+    hi = neg ? -(long long)h : (long long)h;
+    lo = neg ? -(long long)l : (long long)l;
+}
+
+// add the double-float value (h + l) to the node's two limbs
+__device__ __forceinline__ void fixed_add(unsigned long long *q, float h, float l) {
+    long long a1, b1, a2, b2;
+    fixed_limbs(h, a1, b1);
+    fixed_limbs(l, a2, b2);
+    atomicAdd(q, (unsigned long long)(a1 + a2));
+    atomicAdd(q + 1, (unsigned long long)(b1 + b2));
+}
+
+// FIXED: flush into the fixed-point grid Hq (four int64 limbs per node: re
+// hi, re lo, im hi, im lo) instead of FP64 atomics into H (deterministic mode)
+template <int MM, bool FIXED>
 __global__ void __launch_bounds__(32 * (kTile + 2 * MM), 1) spread_tile_df_kernel(
     const double2 *__restrict__ f, Grid3 g, PointsView<double> pts, const __grid_constant__ PolyDF<MM> P,
-    const int4 *__restrict__ chunks, int nt2, int nt3, double2 *__restrict__ H) {
+    const int4 *__restrict__ chunks, int nt2, int nt3, double2 *__restrict__ H, unsigned long long *__restrict__ Hq) {
     constexpr int W = 2 * MM + 1, B = kTile + 2 * MM, B3 = B * B * B, D = kPolyDegDF;
     constexpr int THREADS = 32 * B, NSLOT = (W * W + 31) / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -239,9 +284,25 @@ __global__ void __launch_bounds__(32 * (kTile + 2 * MM), 1) spread_tile_df_kerne
         const int i1 = e / (B * B), i2 = (e / B) % B, i3 = e % B;
         const int64_t node = ((int64_t)wrap_node(b1 + i1, g.n1) * g.n2 + wrap_node(b2 + i2, g.n2)) * g.n3 +
                              wrap_node(b3 + i3, g.n3);
-        double *dst = reinterpret_cast<double *>(H + node);
-        atomicAdd(dst, f2d_bits(v.x) + f2d_bits(v.y));
-        atomicAdd(dst + 1, f2d_bits(v.z) + f2d_bits(v.w));
+        if (FIXED) {
+            fixed_add(Hq + 4 * node, v.x, v.y);
+            fixed_add(Hq + 4 * node + 2, v.z, v.w);
+        } else {
+            double *dst = reinterpret_cast<double *>(H + node);
+            atomicAdd(dst, f2d_bits(v.x) + f2d_bits(v.y));
+            atomicAdd(dst + 1, f2d_bits(v.z) + f2d_bits(v.w));
+        }
+    }
+}
+
+// H[node] = the fixed-point limbs as FP64 (deterministic mode)
+__global__ void fixed_to_grid_kernel(const unsigned long long *__restrict__ Hq, double2 *__restrict__ H,
+                                     int64_t total) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const long long *q = reinterpret_cast<const long long *>(Hq + 4 * e);
+        H[e] = make_double2((double)q[0] * 0x1p-30 + (double)q[1] * 0x1p-60,
+                            (double)q[2] * 0x1p-30 + (double)q[3] * 0x1p-60);
     }
 }
 
@@ -334,9 +395,10 @@ __global__ void __launch_bounds__(32 * (kTile + 2 * MM)) spread_tile_f32_kernel(
 template <typename R, int MM>
 cudaError_t spread_tile_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsView<R> pts, const WinTable<R> &w,
                                  const WinTableDF *wdf, const int4 *chunks, int nchunks, int nt2, int nt3,
-                                 typename Cplx<R>::T *H, cudaStream_t st) {
+                                 typename Cplx<R>::T *H, unsigned long long *Hq, cudaStream_t st) {
     constexpr int B = kTile + 2 * MM;
     if constexpr (sizeof(R) == 4) {
+        if (Hq) return cudaErrorInvalidValue;   // deterministic mode: FP64 family only
         constexpr size_t smem_f = spread_f32_smem<MM>();
         auto kern = spread_tile_f32_kernel<MM>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f);
@@ -347,11 +409,12 @@ cudaError_t spread_tile_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsVi
         // fit one SM's shared memory (m <= 7)
         constexpr size_t smem_df = spread_df_smem<MM>();
         if (!wdf) return cudaErrorInvalidValue;
-        auto kern = spread_tile_df_kernel<MM>;
+        auto kern = Hq ? spread_tile_df_kernel<MM, true> : spread_tile_df_kernel<MM, false>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
         if (e != cudaSuccess) return e;
-        kern<<<(unsigned)nchunks, 32 * B, smem_df, st>>>(f, g, pts, make_poly_df<MM>(*wdf), chunks, nt2, nt3, H);
+        kern<<<(unsigned)nchunks, 32 * B, smem_df, st>>>(f, g, pts, make_poly_df<MM>(*wdf), chunks, nt2, nt3, H, Hq);
     } else {
+        if (Hq) return cudaErrorInvalidValue;   // deterministic mode: not at this m
         // FP64 at m = 8: the box alone takes most of an SM's shared memory;
         // FP64 shared-memory atomics, 512 threads
         const size_t smem = 2 * sizeof(R) * (size_t)B * B * B;
@@ -368,26 +431,35 @@ cudaError_t spread_tile_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsVi
 template <typename R>
 cudaError_t launch_spread_tiles(const typename Cplx<R>::T *f, Grid3 g, int m, PointsView<R> pts,
                                 const WinTable<R> &w, const WinTableDF *wdf, const int4 *chunks, int nchunks,
-                                int nt2, int nt3, typename Cplx<R>::T *H, cudaStream_t st) {
+                                int nt2, int nt3, typename Cplx<R>::T *H, unsigned long long *Hq, cudaStream_t st) {
     if (nchunks <= 0) return cudaSuccess;
     switch (m) {
-        case 1: return spread_tile_dispatch<R, 1>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
-        case 2: return spread_tile_dispatch<R, 2>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
-        case 3: return spread_tile_dispatch<R, 3>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
-        case 4: return spread_tile_dispatch<R, 4>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
-        case 5: return spread_tile_dispatch<R, 5>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
-        case 6: return spread_tile_dispatch<R, 6>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
-        case 7: return spread_tile_dispatch<R, 7>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
-        case 8: return spread_tile_dispatch<R, 8>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, st);
+        case 1: return spread_tile_dispatch<R, 1>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 2: return spread_tile_dispatch<R, 2>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 3: return spread_tile_dispatch<R, 3>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 4: return spread_tile_dispatch<R, 4>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 5: return spread_tile_dispatch<R, 5>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 6: return spread_tile_dispatch<R, 6>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 7: return spread_tile_dispatch<R, 7>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 8: return spread_tile_dispatch<R, 8>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template cudaError_t launch_spread_tiles<double>(const double2 *, Grid3, int, PointsView<double>,
                                                  const WinTable<double> &, const WinTableDF *, const int4 *, int,
-                                                 int, int, double2 *, cudaStream_t);
+                                                 int, int, double2 *, unsigned long long *, cudaStream_t);
 template cudaError_t launch_spread_tiles<float>(const float2 *, Grid3, int, PointsView<float>,
                                                 const WinTable<float> &, const WinTableDF *, const int4 *, int,
-                                                int, int, float2 *, cudaStream_t);
+                                                int, int, float2 *, unsigned long long *, cudaStream_t);
+
+cudaError_t launch_fixed_to_grid(const unsigned long long *Hq, double2 *H, int64_t total, cudaStream_t st) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (total + 255) / 256, cap = (int64_t)sms * 16;
+    fixed_to_grid_kernel<<<(unsigned)(want < cap ? (want < 1 ? 1 : want) : cap), 256, 0, st>>>(Hq, H, total);
+    return cudaGetLastError();
+}
 
 }  // namespace gbnfft

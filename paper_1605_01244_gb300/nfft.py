@@ -182,6 +182,11 @@ class Plan:
                    self._fn("_eval_host")(self._h, _ptr(x_host), _ptr(c_host), _ptr(f_host)))
         return f_host
 
+    def set_deterministic(self, on: bool = True):
+        """Bitwise reproducible adjoints (FP64 plans, m <= 7): stable point
+        order and exact fixed-point spread flushes.  set_points must follow."""
+        _lib.call("nfft3_set_deterministic", self._h, int(bool(on)))
+
     def sync(self):
         _lib.call("nfft3_sync", self._h)
 
