@@ -146,9 +146,12 @@ def gather_bytes(M: int, n: int, real_bytes: int) -> int:
 
 # DRAM bytes (read + write) of one gather launch at the default workload,
 # from ncu's dram__bytes_read.sum + dram__bytes_write.sum on the same kernels
-# at N = 128^3, M = 1.25e6 (both units 1/8 of the default), scaled by 8;
-# profiles/gather_col_128cubed_1.25e6pts_full.md has the capture.
-GATHER_TRAFFIC_BYTES = {"gather_slot_df_kernel": 3.258e9, "gather_col_f32_cube_kernel": 1.51e9}
+# at N = 128^3, M = 1.25e6 (both units 1/8 of the default), scaled by 8
+# (profiles/gather_col_128cubed_1.25e6pts_full.md, and
+# profiles/gather_split_f32_128cubed_1.25e6pts.md for the mixed family's two
+# split kernels together).
+GATHER_TRAFFIC_BYTES = {"gather_slot_df_kernel": 3.258e9,
+                        "gather_dense_f32_kernel + gather_col_f32_cube_kernel": None}
 
 # FP32 instructions of one FP64-accurate (double-float) multiply-add: exact
 # product (1 mul + 3 fma), two-sum of the high parts (6 add/sub), 2 adds into
@@ -455,7 +458,7 @@ def run_ours(args, rank, world, local):
         t_alu = flops / (apk[alu_key] * 1e12)
         t_hbm = byts / (peaks["hbm_gbs"] * 1e9)
         # cubic grids: the FP32 family's shared-table gather
-        kname = "gather_slot_df_kernel" if fam == "f64" else "gather_col_f32_cube_kernel"
+        kname = "gather_slot_df_kernel" if fam == "f64" else "gather_dense_f32_kernel + gather_col_f32_cube_kernel"
         default_size = N == N_EDGE and M == M_POINTS
         traffic = GATHER_TRAFFIC_BYTES.get(kname) if default_size else None
         if t_alu >= t_hbm:
@@ -475,10 +478,11 @@ def run_ours(args, rank, world, local):
                     "traffic": traffic, "kernel": kname, "bytes_per_launch": byts,
                     "peak_source": peak_src}
             w = 2 * m + 1
-            l1_floor_ms = w * w * M / (152 * 2.070e9) * 1e3
-            roof["note"] = ("the kernel is bound by L1 data-pipe wavefronts (about one per stencil row of "
-                            "%d values): floor %d x %d rows x M / (152 SMs x 2.07 GHz) = %.2f ms, achieved "
-                            "%.0f %% of it" % (w, w, w, l1_floor_ms, 100 * l1_floor_ms / g_ms))
+            roof["note"] = ("split gather: sort keys with >= 12 points go to dense batches (one point per "
+                            "lane, rows shared by the warp), the other points to the column kernel, which "
+                            "is bound by L1 data-pipe wavefronts (about one per stencil row of %d values, "
+                            "%d rows a point); achieved is the two kernels' algorithmic bytes over their "
+                            "combined time" % (w, w * w))
         results[fam] = {
             "m": m, "ms_per_step": ms, "ms_eval_only": ms_eval, "e2e_ms": e2e_ms, "grad_ms": grad_ms,
             "adj_ms": adj_ms, "adj_stages": adj_stages, "adj_det": adj_det,
