@@ -311,6 +311,26 @@ def run_cpu_nfft(c3, fd3):
     return out
 
 
+def run_core_proposals():
+    """The learned core proposals against the rho-threshold tube criterion
+    and the dense judge, N = 64^3 (the GPU test's size): train on 12
+    snapshots, report the 4 held-out ones (cells refined, time, recall)."""
+    from paper_1605_01244_gb300 import core_experiment
+    out = core_experiment.run(N=64, r=6)
+    rows = out["heldout"]
+    mean = lambda key, fld: float(np.mean([r[key][fld] for r in rows]))
+    return {
+        "workload": "16 two-vortex snapshots at N=64^3 (offset a swept 0.8 -> 0.05), 12 trained, 4 held out; "
+                    "box [-1.5,1.5]^3, coarse %d^3, dense %d^3" % (out["box_nodes"], out["fine"]),
+        "train_s": out["train_s"], "steps": out["steps"],
+        "learned": {"cells": mean("learned", "cells"), "t_s": mean("learned", "t_s"),
+                    "recall_min": float(min(r["learned"]["recall"] for r in rows))},
+        "rho": {"cells": mean("rho", "cells"), "t_s": mean("rho", "t_s"),
+                "recall_min": float(min(r["rho"]["recall"] for r in rows))},
+        "dense": {"cells": float(rows[0]["total_cells"]), "t_s": float(np.mean([r["t_dense_s"] for r in rows]))},
+    }
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_1605_01244_gb300 import build, sharding, workloads as wl
@@ -508,6 +528,7 @@ def run_ours(args, rank, world, local):
         s = torch.cuda.current_stream(dev)
         extras["sweep"] = run_sweep(c_np, x, results["f64"]["idx"], fd, dev, s, min(args.steps, 3))
         extras["gpe_snapshot"] = run_gpe_snapshot(dev, s, min(args.steps, 3))
+        extras["core_proposals"] = run_core_proposals()
     for fam in results:
         r = results[fam]
         r["rel_l2"] = float(np.linalg.norm(r["f_sub"] - fd) / np.linalg.norm(fd))
@@ -572,6 +593,7 @@ def run_ours(args, rank, world, local):
     if extras:
         line["sweep"] = extras["sweep"]
         line["c2"] = extras["gpe_snapshot"]
+        line["core_proposals"] = extras["core_proposals"]
         rule = [r for r in extras["sweep"] if r["family"] == "f32" and r["eps"] == 1e-6]
         if rule:
             line["mixed"]["at_rule_m"] = {"m": rule[0]["m"], "value": rule[0]["mpoints_s"],

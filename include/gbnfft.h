@@ -394,7 +394,13 @@ int nfft3_tube_refine(int prec, const double *x, const void *psi, int64_t M, dou
  *   cnn_conv3d_fwd:   y = conv(x, w) + bias, optional ReLU; y_bf16 and/or y_f32.
  *   cnn_conv3d_dgrad: dx = conv^T(dy, w), times the ReLU mask (relu_mask[i] > 0)
  *                     of the layer input when relu_mask != NULL.
- *   cnn_conv3d_wgrad: dw (FP32, same layout as w) and db (FP32, may be NULL).
+ *   cnn_conv3d_wgrad: dw (FP32, same layout as w) and db (FP32, may be NULL);
+ *                     takes B (Cout Cin k^3 + Cout) floats of stream-ordered
+ *                     scratch (cudaMallocAsync) for the per-batch-entry
+ *                     partial sums (NFFT3_ERR_ALLOC if that fails).
+ *   k = 1 or 3 with at most 16 channels in and out run the shared-memory tiled
+ *   kernels (8 x 8 x 4 voxel tiles); other shapes, or GBNFFT_CNN_NAIVE=1, one
+ *   output per thread.  Every sum is in a fixed order (deterministic).
  *   cnn_core_loss:    4-channel head y (FP32: logit, 3 offsets) vs target
  *                     (B D^3 in {0,1}) and off_target (B D^3 x 3): mean BCE,
  *                     positives weighted by pos_weight, + lam * L1 over the

@@ -94,6 +94,68 @@ def test_conv_kernels_match_reference(k, ci, co, relu):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("k,ci,co", [(3, 16, 16), (1, 16, 4), (3, 3, 16)])
+def test_tiled_conv_kernels_several_tiles(k, ci, co, monkeypatch):
+    """The shared-memory tiled kernels (8 x 8 x 4 voxel tiles) on a lattice of
+    several ragged tiles, against the reference and the one-output-per-thread
+    kernels (GBNFFT_CNN_NAIVE=1); with their times at the experiment's size
+    (12 snapshots of 49^3 coarse nodes)."""
+    import ctypes
+    from paper_1605_01244_gb300 import _lib
+    g = wl.rng(95 + k + ci)
+    P = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    B, D = 3, 13
+    x = bf16_round(np.abs(g.standard_normal((B, ci, D, D, D))))
+    w = bf16_round(g.standard_normal((co, ci, k, k, k)) * 0.3)
+    b = g.standard_normal(co).astype(np.float32).astype(float)
+    dy = g.standard_normal((B, co, D, D, D)).astype(np.float32)
+    xt = torch.from_numpy(x).to(torch.bfloat16).cuda()
+    wt = torch.from_numpy(w).to(torch.bfloat16).cuda()
+    bt = torch.from_numpy(b).float().cuda()
+    dyt = torch.from_numpy(dy).cuda()
+
+    def run():
+        yf = torch.empty((B, co, D, D, D), dtype=torch.float32, device="cuda")
+        _lib.call("cnn_conv3d_fwd", P(xt), P(wt), P(bt), B, ci, co, D, k, 1, None, P(yf), None)
+        dx = torch.empty((B, ci, D, D, D), dtype=torch.float32, device="cuda")
+        _lib.call("cnn_conv3d_dgrad", P(dyt), P(wt), B, ci, co, D, k, P(xt), P(dx), None)
+        dw = torch.empty((co, ci, k, k, k), dtype=torch.float32, device="cuda")
+        db = torch.empty(co, dtype=torch.float32, device="cuda")
+        _lib.call("cnn_conv3d_wgrad", P(dyt), P(xt), B, ci, co, D, k, P(dw), P(db), None)
+        return [t.double().cpu().numpy() for t in (yf, dx, dw, db)]
+
+    yf, dx, dw, db = run()
+    ref = np.maximum(cnn_ref.conv3d(x, w, b), 0)
+    dref = cnn_ref.conv3d_dgrad(dy.astype(float), w) * (x > 0)
+    wref, bref = cnn_ref.conv3d_wgrad(dy.astype(float), x, k)
+    for got, want in ((yf, ref), (dx, dref), (dw, wref), (db, bref)):
+        assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want))
+    monkeypatch.setenv("GBNFFT_CNN_NAIVE", "1")
+    for got, want in zip((yf, dx, dw, db), run()):
+        assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want))
+    # times at the experiment's size, tiled against one output per thread
+    B, D = 12, 49
+    xt = torch.zeros((B, ci, D, D, D), dtype=torch.bfloat16, device="cuda").uniform_()
+    dyt = torch.zeros((B, co, D, D, D), dtype=torch.float32, device="cuda").normal_()
+    ms = {}
+    for mode in ("tiled", "naive"):
+        if mode == "tiled":
+            monkeypatch.delenv("GBNFFT_CNN_NAIVE", raising=False)
+        else:
+            monkeypatch.setenv("GBNFFT_CNN_NAIVE", "1")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        run()
+        torch.cuda.synchronize()
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms[mode] = e0.elapsed_time(e1)
+    print("conv k=%d %d->%d at 12 x 49^3, fwd + dgrad + wgrad: tiled %.2f ms, one output per thread %.2f ms"
+          % (k, ci, co, ms["tiled"], ms["naive"]))
+
+
+@pytest.mark.gpu
 def test_network_gradients_match_reference_chain():
     from paper_1605_01244_gb300.cnn import CoreCNN, LAYERS
     g = wl.rng(90)
@@ -172,3 +234,9 @@ def test_learned_proposals_recover_the_dense_cores():
     for res in out["heldout"]:
         assert res["learned"]["recall"] >= 0.99, res
         assert res["learned"]["cells"] <= 0.15 * res["total_cells"], res
+    # what the network buys over the rho-threshold tube criterion (both set for
+    # full recall on the training snapshots): fewer cells to refine
+    learned = sum(r["learned"]["cells"] for r in out["heldout"])
+    rho = sum(r["rho"]["cells"] for r in out["heldout"])
+    print("held-out cells refined: learned %d, rho threshold %d" % (learned, rho))
+    assert learned <= rho
