@@ -227,13 +227,34 @@ def run_sweep(c_np, x, idx, fd, dev, s, steps):
     return out
 
 
-def run_gpe_snapshot(dev, s, steps):
+class CpuLeg:
+    """The CPU-baseline leg: the only part of this file that runs the oracle
+    (oracle/, test infrastructure) -- the FP64 direct sum and the plain CPU
+    NFFT on the host cores, rank 0 only, outside every timed GPU region.  Its
+    direct sums on the fixed subsamples are also the references of the
+    accuracy columns (rel_l2_vs_oracle, inf_err_vs_oracle)."""
+
+    def __init__(self):
+        import oracle
+        self.oracle = oracle
+
+    def direct(self, c, x):
+        return self.oracle.forward(c, x)
+
+    def direct_timed(self, c, x, label):
+        t0 = time.perf_counter()
+        self.oracle.forward(c, x)
+        dt = time.perf_counter() - t0
+        return {"value": len(x) / dt / 1e6, "unit": "Mpoints/s", "cores": self.oracle.num_threads(),
+                "kind": "oracle", "sample": "%s (%.1f s)" % (label, dt)}
+
+
+def run_gpe_snapshot(dev, s, steps, leg):
     """The GPE-snapshot workload: N = 128^3 two-vortex coefficients, 100^3
     lattice points in the physical box [-0.025, 0.025]^3 plus 10^6 uniform
     points; Mpoints/s of set_points + eval for both families and the errors on
     2000 sampled points (1000 of each population) against the direct sum."""
     import torch
-    import oracle
     from paper_1605_01244_gb300 import workloads as wl
     from paper_1605_01244_gb300.nfft import Plan
     c_np, x_np = wl.gpe_snapshot()
@@ -256,7 +277,7 @@ def run_gpe_snapshot(dev, s, steps):
         res[fam] = {"m": m, "mpoints_s": M / (ms * 1e-3) / 1e6, "ms": ms}
         plan.close()
         del c, f
-    fd = oracle.forward(c_np, x_np[idx])
+    fd = leg.direct(c_np, x_np[idx])
     for fam, fs in fsubs.items():
         res[fam]["rel_l2"] = float(np.linalg.norm(fs - fd) / np.linalg.norm(fd))
     del x
@@ -275,12 +296,12 @@ def cpu_model() -> str:
     return "unknown"
 
 
-def run_cpu_nfft(c3, fd3):
+def run_cpu_nfft(c3, fd3, leg):
     """The plain CPU NFFT (FP64, m = 6, sigma = 2; OpenMP C steps around
     scipy's FFT) on the host cores: configs 1-3 in full on all cores, and on
     one core with the window gather timed on at most 200,000 points and scaled
     to the full point count (deconvolution and FFT always on the full grid)."""
-    from oracle import cpu_nfft
+    from oracle import cpu_nfft   # part of the CPU-baseline leg (called only through it)
     from paper_1605_01244_gb300 import workloads as wl
     cores = cpu_nfft.host_cores()
     c1, x1 = wl.small_random()
@@ -374,18 +395,16 @@ def run_ours(args, rank, world, local):
         _lib.lib().nfft3_timing_enable(plan._h, 1)
         _lib.lib().nfft3_timing_read(plan._h, None, None, None, 1)
         sampler = ClockSampler(local)
-        sampler.start()
         s = torch.cuda.current_stream(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        e0.record(s)
-        for _ in range(args.steps):
+
+        def step():
             plan.set_points(x)
             plan.eval(c, out=f)
-        e1.record(s)
-        barrier()
+
+        sampler.start()
+        ms = sharding.timed_steps(step, args.steps, s, dev)   # barrier + sync both sides, max over ranks
         clocks = sampler.stop()
-        ms = e0.elapsed_time(e1) / args.steps
         import ctypes
         st_ms = (ctypes.c_double * len(_lib.STAGES))()
         st_n = (ctypes.c_int64 * len(_lib.STAGES))()
@@ -394,7 +413,6 @@ def run_ours(args, rank, world, local):
         _lib.lib().nfft3_timing_enable(plan._h, 0)
         stages = {nm: (st_ms[i] / st_n[i] if st_n[i] else 0.0) for i, nm in enumerate(_lib.STAGES)
                   if nm in ("set_points", "deconv", "fft", "split", "gather")}
-        ms = sharding.max_over_ranks(ms, dev)
         # eval-only throughput (points already set)
         barrier()
         e0.record(s)
@@ -521,13 +539,13 @@ def run_ours(args, rank, world, local):
             dist.destroy_process_group()
         return
 
-    import oracle
-    fd = oracle.forward(c_np, x_np[results["f64"]["idx"]])
+    leg = CpuLeg()
+    fd = leg.direct(c_np, x_np[results["f64"]["idx"]])
     extras = {}
     if world == 1 and not args.no_extras:
         s = torch.cuda.current_stream(dev)
         extras["sweep"] = run_sweep(c_np, x, results["f64"]["idx"], fd, dev, s, min(args.steps, 3))
-        extras["gpe_snapshot"] = run_gpe_snapshot(dev, s, min(args.steps, 3))
+        extras["gpe_snapshot"] = run_gpe_snapshot(dev, s, min(args.steps, 3), leg)
         extras["core_proposals"] = run_core_proposals()
     for fam in results:
         r = results[fam]
@@ -537,14 +555,10 @@ def run_ours(args, rank, world, local):
     cpu = None
     if not args.no_cpu_baseline:
         S = 8192          # about 10 s of direct summation on 16 Arm cores at N = 256^3
-        sub = x_np[:S]
-        t0 = time.perf_counter()
-        oracle.forward(c_np, sub)
-        dt = time.perf_counter() - t0
-        cpu = {"value": S / dt / 1e6, "unit": "Mpoints/s", "cores": oracle.num_threads(),
-               "kind": "oracle", "sample": "%d uniform points of the workload, FP64 direct sum at N=256^3 (%.1f s)" % (S, dt)}
+        cpu = leg.direct_timed(c_np, x_np[:S], "%d uniform points of the workload, FP64 direct sum at N=%d^3"
+                               % (S, N))
         if world == 1 and not args.no_extras and N == N_EDGE:
-            cpu["cpu_nfft"] = run_cpu_nfft((c_np, x_np, results["f64"]["idx"]), fd)
+            cpu["cpu_nfft"] = run_cpu_nfft((c_np, x_np, results["f64"]["idx"]), fd, leg)
 
     def fam_line(fam):
         r = results[fam]

@@ -138,6 +138,19 @@ int nfft3d_eval_grad(nfft3_plan p, const double *c, double *f, double *grad);
 int nfft3f_eval_grad(nfft3_plan p, const float *c, float *f, float *grad);
 
 /*
+ * Chain rule for the point coordinates, the backward pass of f = A(x) c in x:
+ *   gx[3j+d] = Re(conj(G_j) grad[3j+d]) = Re G_j Re grad[3j+d] + Im G_j Im grad[3j+d],
+ * with G_j = dL/d(Re f_j) + i dL/d(Im f_j) (M complex, interleaved, the
+ * plan's precision) and grad the 3M complex gradient of nfft3*_eval_grad at
+ * the same points (torus units, Sec. 2 / eq. (Lambda)).  gx: 3M doubles,
+ * written.  All three are device pointers owned by the caller; the kernel
+ * runs on the plan's stream (computed in FP64 for both families).
+ * NFFT3_ERR_ARG: a NULL pointer with M > 0, or a precision mismatch.
+ */
+int nfft3d_chain_x(nfft3_plan p, const double *G, const double *grad, double *gx);
+int nfft3f_chain_x(nfft3_plan p, const float *G, const float *grad, double *gx);
+
+/*
  * f and grad as nfft3*_eval_grad, by differentiating the window instead of
  * the series: one oversampled transform of c, then
  *   grad_d f_j = sum_l g_l n_d phi'(u_d - l_d) prod_{e != d} phi(u_e - l_e),

@@ -9,7 +9,7 @@ complex tensors):
   sums to Re/Im of sum_j conj(A_jk) G_j;
 * dL/dx_{j,d} = Re(conj(G_j) d_d f_j), with d_d f_j = sum_k 2 pi i k_d c_k
   e^{2 pi i k.x_j} from ``nfft3*_eval_grad`` (paper eq. (Lambda), torus
-  units).
+  units), contracted with G by ``nfft3*_chain_x``.
 
 All arithmetic is in the CUDA library; this module only sequences the calls.
 """
@@ -50,7 +50,7 @@ class NFFTEval(torch.autograd.Function):
             grad_c = plan.adjoint(G)
         if ctx.needs_input_grad[1]:
             _, d = plan.eval_grad(c, want_f=False)          # d[j, dim] = d f_j / d x_dim
-            grad_x = (G.conj().unsqueeze(1) * d).real.to(torch.float64)
+            grad_x = plan.chain_x(G, d)                      # Re(conj(G_j) d[j, dim])
         return grad_c, grad_x, None
 
 

@@ -188,6 +188,9 @@ cudaError_t launch_fused_adjoint(const typename Cplx<R>::T *H, const int N[3], c
 // *rank = max(*rank, value_rank of each of the count doubles at v); the caller
 // zeroes *rank first.
 cudaError_t launch_value_rank(const double *v, int64_t count, int *rank, cudaStream_t st);
+// gx[3 j + d] = Re(conj(G_j) grad[3 j + d]) for j < M (chain.cu).
+template <typename R>
+cudaError_t launch_chain_x(const R *G, const R *grad, double *gx, int64_t M, cudaStream_t st);
 
 // ---- complex matrix products (cgemm.cu) -------------------------------------
 // C[b] = A[b] B[b] for b < batch (strides sA, sB, sC elements), A (M x K),

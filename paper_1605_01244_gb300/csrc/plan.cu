@@ -909,6 +909,16 @@ template <typename R> int eval_grad_impl(nfft3_plan p, const R *c, R *f, R *grad
     return finish(p, cuda_status(e));
 }
 
+template <typename R> int chain_x_impl(nfft3_plan p, const R *G, const R *grad, double *gx) {
+    constexpr int prec = sizeof(R) == 8 ? 64 : 32;
+    if (!p || p->prec != prec) return NFFT3_ERR_ARG;
+    if (p->M == 0) return NFFT3_OK;
+    if (!G || !grad || !gx) return NFFT3_ERR_ARG;
+    const cudaError_t e = launch_chain_x<R>(G, grad, gx, p->M, p->stream);
+    p->launches += 1;
+    return finish(p, cuda_status(e));
+}
+
 // Deconvolve + FFT + pad the series c into the plan's padded grid(s) and keep
 // them: afterwards eval_stored / eval_grad_stored gather at whatever points
 // are set, without repeating the FFT (column gather mode only).
@@ -1198,6 +1208,13 @@ int nfft3d_eval_grad(nfft3_plan p, const double *c, double *f, double *grad) {
 }
 int nfft3f_eval_grad(nfft3_plan p, const float *c, float *f, float *grad) {
     return eval_grad_impl<float>(p, c, f, grad);
+}
+
+int nfft3d_chain_x(nfft3_plan p, const double *G, const double *grad, double *gx) {
+    return chain_x_impl<double>(p, G, grad, gx);
+}
+int nfft3f_chain_x(nfft3_plan p, const float *G, const float *grad, double *gx) {
+    return chain_x_impl<float>(p, G, grad, gx);
 }
 
 int nfft3d_eval_grad_window(nfft3_plan p, const double *c, double *f, double *grad) {

@@ -117,6 +117,15 @@ class Plan:
                    self._fn("_eval_grad")(self._h, _ptr(c), _ptr(f), _ptr(g)))
         return f, g
 
+    def chain_x(self, G: torch.Tensor, grad: torch.Tensor) -> torch.Tensor:
+        """(M, 3) float64 dL/dx with dL/dx_{j,d} = Re(conj(G_j) grad[j, d]):
+        G the upstream gradient of f, grad from :meth:`eval_grad`."""
+        self._cuda(G, self.cdtype, (self.M,), "G")
+        self._cuda(grad, self.cdtype, (self.M, 3), "grad")
+        gx = torch.empty((self.M, 3), dtype=torch.float64, device=self.device)
+        _lib.check(self.prefix + "_chain_x", self._fn("_chain_x")(self._h, _ptr(G), _ptr(grad), _ptr(gx)))
+        return gx
+
     def adjoint(self, f: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         """h_k = sum_j f_j exp(-2 pi i k.x_j); f: (M,) complex CUDA tensor."""
         self._cuda(f, self.cdtype, (self.M,), "f")

@@ -87,6 +87,8 @@ def test_null_handles(lib):
     assert lib.nfft3f_adjoint(None, None, None) == _lib.NFFT3_ERR_ARG
     assert lib.nfft3d_set_points(None, None) == _lib.NFFT3_ERR_ARG
     assert lib.nfft3_sync(None) == _lib.NFFT3_ERR_ARG
+    assert lib.nfft3d_chain_x(None, None, None, None) == _lib.NFFT3_ERR_ARG
+    assert lib.nfft3f_chain_x(None, None, None, None) == _lib.NFFT3_ERR_ARG
 
 
 def test_reduce_coords_rejects_bad_arguments(lib):

@@ -88,6 +88,27 @@ def test_nfft_eval_backward_matches_oracle(prec, m, tol):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_chain_x_elementwise(prec):
+    """nfft3*_chain_x against Re(conj(G) d) formed on the host in FP64, on a
+    ragged point count (several blocks and a tail), and M = 0."""
+    from paper_1605_01244_gb300 import Plan
+    cd = torch.complex128 if prec == "f64" else torch.complex64
+    M = 3 * 256 * 7 + 13
+    g = wl.rng(50)
+    G = torch.from_numpy(g.standard_normal(M) + 1j * g.standard_normal(M)).to(cd)
+    d = torch.from_numpy(g.standard_normal((M, 3)) + 1j * g.standard_normal((M, 3))).to(cd)
+    plan = Plan((8, 8, 8), M, m=3, precision=prec)
+    got = plan.chain_x(G.cuda(), d.cuda()).cpu().numpy()
+    Gn, dn = G.numpy().astype(np.complex128), d.numpy().astype(np.complex128)
+    want = Gn.real[:, None] * dn.real + Gn.imag[:, None] * dn.imag
+    assert np.max(np.abs(got - want)) <= 1e-15 * np.max(np.abs(want))
+    empty = Plan((8, 8, 8), 0, m=3, precision=prec)
+    assert empty.chain_x(torch.empty(0, dtype=cd, device="cuda"),
+                         torch.empty((0, 3), dtype=cd, device="cuda")).shape == (0, 3)
+
+
+@pytest.mark.gpu
 def test_nfft_eval_x_gradient_finite_differences():
     """Central differences (h = 1e-6) of L(x) = Re(sum conj(G) f(x)) on the FP64 CUDA path."""
     from paper_1605_01244_gb300 import Plan
