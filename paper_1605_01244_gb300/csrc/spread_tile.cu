@@ -113,10 +113,15 @@ __global__ void __launch_bounds__(THREADS, 1) spread_tile_kernel(const typename 
 // its box in double-float (hi + lo floats) on the FP32 pipe.  Phase 1: the
 // block evaluates the tap weights of all the chunk's points by double-float
 // Horner (the plan's hi + lo coefficient table, copied to shared memory) and
-// stages them as float pairs.  Phase 2: warp p owns box plane p (B warps) and walks
-// every point of the chunk, adding the point's taps that fall in its plane;
-// no other warp touches that plane and the lanes of a warp take distinct
-// (b, c) nodes, so the node updates need no atomics.
+// stages them as float pairs.  Phase 2: the B warps own disjoint node sets
+// and each walks every point of the chunk, adding the point's taps that fall
+// in its set; the lanes of a warp take distinct nodes, so the node updates
+// need no atomics.  Warp (q, h) owns the rows of parity h in the planes q and
+// q + B/2.  A point's 2m+1 stencil planes start at one of the tile's kTile
+// first planes, so the middle planes receive every point and the outer ones
+// few: one plane per warp left most warps idle while the middle ones worked.
+// Pairing plane q with plane q + B/2 evens the planes' loads (within about
+// 10 %), and splitting rows by parity keeps the warp count at B.
 __device__ __forceinline__ float2 df2_mul(float2 a, float2 b) {
     const float p = __fmul_rn(a.x, b.x);
     float e = __fmaf_rn(a.x, b.x, -p);
@@ -207,7 +212,9 @@ __global__ void __launch_bounds__(32 * (kTile + 2 * MM), 1) spread_tile_df_kerne
     const double2 *__restrict__ f, Grid3 g, PointsView<double> pts, const __grid_constant__ PolyDF<MM> P,
     const int4 *__restrict__ chunks, int nt2, int nt3, double2 *__restrict__ H, unsigned long long *__restrict__ Hq) {
     constexpr int W = 2 * MM + 1, B = kTile + 2 * MM, B3 = B * B * B, D = kPolyDegDF;
-    constexpr int THREADS = 32 * B, NSLOT = (W * W + 31) / 32;
+    // NR: stencil rows of one parity (at most); NS2: lane slots covering them
+    constexpr int THREADS = 32 * B, NR = (W + 1) / 2, NS2 = (NR * W + 31) / 32;
+    static_assert(B % 2 == 0, "plane pairs q, q + B/2");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *box = reinterpret_cast<float4 *>(smem_raw);                 // (re hi, re lo, im hi, im lo)
     float2 *wts = reinterpret_cast<float2 *>(box + B3);                   // [point][d][tap]
@@ -247,33 +254,50 @@ __global__ void __launch_bounds__(32 * (kTile + 2 * MM), 1) spread_tile_df_kerne
                            tile_centre(key.z, MM, g.n3) - kTile * tt3, 0);
     }
     __syncthreads();
-    // phase 2
-    const int lane = threadIdx.x & 31, plane = threadIdx.x >> 5;
+    // phase 2: warp (q, h) owns box planes q and q + B/2, rows of parity h
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, h = wid & 1, q0 = wid >> 1;
+    int rr[NS2], cc[NS2];
+#pragma unroll
+    for (int k = 0; k < NS2; ++k) {
+        const int sl = lane + 32 * k;
+        rr[k] = sl < NR * W ? sl / W : W;   // W: no node (b >= W below)
+        cc[k] = sl < NR * W ? sl - (sl / W) * W : 0;
+    }
     for (int i = 0; i < ch.z; ++i) {
         const int4 o = osm[i];
-        const int a = plane - o.x;
-        if (a < 0 || a >= W) continue;
+        const int b0 = (h - o.y) & 1;   // first stencil row whose box row has parity h
         const float2 *wi = wts + i * 3 * W;
         const float4 fv = fsm[i];
-        const float2 w1 = wi[a];
-        const float2 fr = df2_mul(make_float2(fv.x, fv.y), w1), fi = df2_mul(make_float2(fv.z, fv.w), w1);
-        float4 *row = box + plane * B * B;
 #pragma unroll
-        for (int k = 0; k < NSLOT; ++k) {
-            const int slot = lane + 32 * k;
-            if (slot >= W * W) continue;
-            const int b = slot / W, c = slot - b * W;
-            const float2 w23 = df2_mul(wi[W + b], wi[2 * W + c]);
-            float4 &node = row[(o.y + b) * B + (o.z + c)];
-            // node += f w1 w23: exact product, two-sum into the high part,
-            // errors into the low part, renormalised so that the low part
-            // stays below half an ulp of the high part
-            float4 v = node;
-            df_mac(v.x, v.y, fr.x, fr.y, w23.x, w23.y);
-            df_mac(v.z, v.w, fi.x, fi.y, w23.x, w23.y);
-            df_norm(v.x, v.y);
-            df_norm(v.z, v.w);
-            node = v;
+        for (int pp = 0; pp < 2; ++pp) {
+            const int plane = q0 + pp * (B / 2);
+            const int a = plane - o.x;
+            if (a < 0 || a >= W) continue;
+            const float2 w1 = wi[a];
+            const float2 fr = df2_mul(make_float2(fv.x, fv.y), w1), fi = df2_mul(make_float2(fv.z, fv.w), w1);
+            float4 *pl = box + plane * B * B;
+#pragma unroll
+            for (int k = 0; k < NS2; ++k) {
+                const int b = b0 + 2 * rr[k], c = cc[k];
+                if (b >= W) continue;
+                // w2 w3 as an unnormalised pair (product, its error): the
+                // multiply-add below only needs |low| within a few ulps
+                const float2 u = wi[W + b], v3 = wi[2 * W + c];
+                const float wp = __fmul_rn(u.x, v3.x);
+                float we = __fmaf_rn(u.x, v3.x, -wp);
+                we = __fmaf_rn(u.x, v3.y, we);
+                we = __fmaf_rn(u.y, v3.x, we);
+                float4 &node = pl[(o.y + b) * B + (o.z + c)];
+                // node += f w1 w2 w3: exact product, two-sum into the high part,
+                // errors into the low part, renormalised so that the low part
+                // stays below half an ulp of the high part
+                float4 nv = node;
+                df_mac(nv.x, nv.y, fr.x, fr.y, wp, we);
+                df_mac(nv.z, nv.w, fi.x, fi.y, wp, we);
+                df_norm(nv.x, nv.y);
+                df_norm(nv.z, nv.w);
+                node = nv;
+            }
         }
     }
     __syncthreads();
@@ -308,8 +332,9 @@ __global__ void fixed_to_grid_kernel(const unsigned long long *__restrict__ Hq, 
 
 // ---- mixed family: plane-owned FP32 box, no atomics in shared memory ------
 // Same scheme as spread_tile_df_kernel in FP32: the block stages the chunk's
-// tap weights (FP32 Horner), then warp p owns box plane p and adds every
-// point's taps in that plane with plain shared-memory updates.
+// tap weights (FP32 Horner), then warp (q, h) owns the rows of parity h in
+// box planes q and q + B/2 and adds every point's taps there with plain
+// shared-memory updates.
 template <int MM> constexpr size_t spread_f32_smem() {
     constexpr int W = 2 * MM + 1, B = kTile + 2 * MM;
     return sizeof(float2) * (size_t)B * B * B + sizeof(float) * (size_t)kChunk * 3 * W +
@@ -321,7 +346,8 @@ __global__ void __launch_bounds__(32 * (kTile + 2 * MM)) spread_tile_f32_kernel(
     const float2 *__restrict__ f, Grid3 g, PointsView<float> pts, const __grid_constant__ Poly<float, MM> P,
     const int4 *__restrict__ chunks, int nt2, int nt3, float2 *__restrict__ H) {
     constexpr int W = 2 * MM + 1, B = kTile + 2 * MM, B3 = B * B * B, D = PolyDeg<float>::value;
-    constexpr int THREADS = 32 * B, NSLOT = (W * W + 31) / 32;
+    constexpr int THREADS = 32 * B, NR = (W + 1) / 2, NS2 = (NR * W + 31) / 32;
+    static_assert(B % 2 == 0, "plane pairs q, q + B/2");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *box = reinterpret_cast<float2 *>(smem_raw);                  // (re, im) per node
     float *wts = reinterpret_cast<float *>(box + B3);                     // [point][d][tap]
@@ -356,26 +382,37 @@ __global__ void __launch_bounds__(32 * (kTile + 2 * MM)) spread_tile_f32_kernel(
                            tile_centre(key.z, MM, g.n3) - kTile * tt3, 0);
     }
     __syncthreads();
-    // phase 2
-    const int lane = threadIdx.x & 31, plane = threadIdx.x >> 5;
+    // phase 2: warp (q, h) owns box planes q and q + B/2, rows of parity h
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, h = wid & 1, q0 = wid >> 1;
+    int rr[NS2], cc[NS2];
+#pragma unroll
+    for (int k = 0; k < NS2; ++k) {
+        const int sl = lane + 32 * k;
+        rr[k] = sl < NR * W ? sl / W : W;   // W: no node (b >= W below)
+        cc[k] = sl < NR * W ? sl - (sl / W) * W : 0;
+    }
     for (int i = 0; i < ch.z; ++i) {
         const int4 o = osm[i];
-        const int a = plane - o.x;
-        if (a < 0 || a >= W) continue;
+        const int b0 = (h - o.y) & 1;   // first stencil row whose box row has parity h
         const float *wi = wts + i * 3 * W;
         const float2 fv = fsm[i];
-        const float w1 = wi[a];
-        const float fr = fv.x * w1, fi = fv.y * w1;
-        float2 *row = box + plane * B * B;
 #pragma unroll
-        for (int k = 0; k < NSLOT; ++k) {
-            const int slot = lane + 32 * k;
-            if (slot >= W * W) continue;
-            const int b = slot / W, c = slot - b * W;
-            const float w23 = wi[W + b] * wi[2 * W + c];
-            float2 &node = row[(o.y + b) * B + (o.z + c)];
-            const float2 v = node;
-            node = make_float2(fmaf(fr, w23, v.x), fmaf(fi, w23, v.y));
+        for (int pp = 0; pp < 2; ++pp) {
+            const int plane = q0 + pp * (B / 2);
+            const int a = plane - o.x;
+            if (a < 0 || a >= W) continue;
+            const float w1 = wi[a];
+            const float fr = fv.x * w1, fi = fv.y * w1;
+            float2 *pl = box + plane * B * B;
+#pragma unroll
+            for (int k = 0; k < NS2; ++k) {
+                const int b = b0 + 2 * rr[k], c = cc[k];
+                if (b >= W) continue;
+                const float w23 = wi[W + b] * wi[2 * W + c];
+                float2 &node = pl[(o.y + b) * B + (o.z + c)];
+                const float2 v = node;
+                node = make_float2(fmaf(fr, w23, v.x), fmaf(fi, w23, v.y));
+            }
         }
     }
     __syncthreads();
