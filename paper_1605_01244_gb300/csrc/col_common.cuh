@@ -12,6 +12,76 @@ template <int W> struct GroupSize {
     static constexpr int value = W <= 2 ? 2 : W <= 4 ? 4 : W <= 8 ? 8 : W <= 16 ? 16 : 32;
 };
 
+// ---- packed pairs of floats (f32x2) -----------------------------------------
+// Two FP32 values in one 64-bit register, operated on by a single add, sub,
+// mul or fma instruction (PTX .f32x2, sm_100 and later; IEEE round to
+// nearest, subnormals kept, like the scalar intrinsics).  The FP64 family's
+// double-float arithmetic on complex values treats the real and imaginary
+// parts as one pair, which halves its instruction count.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 x2_pack(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void x2_unpack(f32x2 v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_sub(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// v XOR z with z = 0 supplied at run time (a kernel argument): the same
+// bits, but a value the code generator cannot trace back to the instruction
+// that made it.  Measured on sm_103a: a packed product fed straight into a
+// packed add was fused into one multiply-add (a single rounding), and
+// fma(x, y, -(x y)) was folded to zero, although both break the explicitly
+// rounded operations' semantics; passing the product through this exclusive
+// or keeps each operation as written (checked bit for bit against the scalar
+// df_mac and df_norm below).
+__device__ __forceinline__ f32x2 x2_opaque(f32x2 v, f32x2 z) {
+    f32x2 r;
+    asm("xor.b64 %0, %1, %2;" : "=l"(r) : "l"(v), "l"(z));
+    return r;
+}
+// (sh, sl) += (xh, xl) (yh, yl) on both halves of the pairs: the operations
+// of df_mac below, in the same order (so the same results), packed; z: a
+// run-time zero (x2_opaque)
+__device__ __forceinline__ void x2_df_mac(f32x2 &sh, f32x2 &sl, f32x2 xh, f32x2 xl, f32x2 yh, f32x2 yl,
+                                          f32x2 z) {
+    const f32x2 p = x2_opaque(x2_mul(xh, yh), z);
+    f32x2 e = x2_fma(xh, yh, x2_sub(0ull, p));
+    e = x2_fma(xh, yl, e);
+    e = x2_fma(xl, yh, e);
+    const f32x2 s = x2_add(sh, p);
+    const f32x2 bb = x2_sub(s, sh);
+    const f32x2 err = x2_add(x2_sub(sh, x2_sub(s, bb)), x2_sub(p, bb));
+    sl = x2_add(sl, x2_add(err, e));
+    sh = s;
+}
+// df_norm on both halves
+__device__ __forceinline__ void x2_df_norm(f32x2 &sh, f32x2 &sl) {
+    const f32x2 s = x2_add(sh, sl);
+    sl = x2_sub(sl, x2_sub(s, sh));
+    sh = s;
+}
+
 // ---- double-float helpers (same arithmetic as gather_df.cu) ------------------
 __device__ __forceinline__ void df_mac(float &ah, float &al, float xh, float xl, float yh,
                                        float yl) {

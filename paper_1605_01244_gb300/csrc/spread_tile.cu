@@ -5,11 +5,9 @@
 // (kTile + 2m)^3 nodes starting m nodes before the tile, so the block
 // accumulates them there and then adds the box to the oversampled grid once
 // (global atomics, node indices wrapped mod n).
-// spread_tile_df_kernel (FP64, m <= 7) and spread_tile_f32_kernel (mixed)
-// give each warp one plane of the box, so no node update needs an atomic;
-// spread_tile_kernel (FP64 at m = 8, whose box and staged weights exceed
-// shared memory) has warps take points, the lanes of a warp take the (b, c)
-// node pairs of a stencil plane, and shared-memory atomics resolve the rest.
+// spread_tile_df_kernel (FP64, double-float) and spread_tile_f32_kernel
+// (mixed) give each warp its own set of box nodes (rows of one parity in two
+// planes), so no node update needs an atomic.
 #include "col_common.cuh"
 
 namespace gbnfft {
@@ -27,83 +25,15 @@ __device__ __forceinline__ int wrap_node(int v, int n) {
     return v < 0 ? v + n : v;
 }
 
-template <typename R, int MM, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1) spread_tile_kernel(const typename Cplx<R>::T *__restrict__ f, Grid3 g,
-                                                              PointsView<R> pts,
-                                                              const __grid_constant__ Poly<R, MM> P,
-                                                              const int4 *__restrict__ chunks, int nt2, int nt3,
-                                                              typename Cplx<R>::T *__restrict__ H) {
-    using C = typename Cplx<R>::T;
-    constexpr int W = 2 * MM + 1, B = kTile + 2 * MM, B3 = B * B * B, D = PolyDeg<R>::value;
-    constexpr int NSLOT = (W * W + 31) / 32;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *box_re = reinterpret_cast<R *>(smem_raw);   // box node (i1, i2, i3) at (i1 B + i2) B + i3
-    R *box_im = box_re + B3;
-    const int4 ch = chunks[blockIdx.x];
-    const int t = ch.x;
-    const int tt3 = t % nt3, tt2 = (t / nt3) % nt2, tt1 = t / (nt3 * nt2);
-    for (int e = threadIdx.x; e < B3; e += THREADS) box_re[e] = box_im[e] = (R)0;
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31;
-    const int tap = lane < W ? lane : 0;
-    for (int i = threadIdx.x >> 5; i < ch.z; i += THREADS / 32) {
-        const int64_t j = (int64_t)ch.y + i;
-        const int4 key = pts.key[j];
-        const C fv = scale_value(f[key.w], value_shift(pts.vexp));
-        // lane a < W: the weight of tap a in each dimension (Horner in t = 2s - 1)
-        R w[3];
-        {
-            const R s[3] = {pts.s1[j], pts.s2[j], pts.s3[j]};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const R tv = (R)2 * s[d] - (R)1;
-                R v = P.c[d][tap][D];
-#pragma unroll
-                for (int k = D - 1; k >= 0; --k) v = fma(v, tv, P.c[d][tap][k]);
-                w[d] = v;
-            }
-        }
-        // stencil node a of dimension d sits at box index o_d + a
-        const int o1 = tile_centre(key.x, MM, g.n1) - kTile * tt1;
-        const int o2 = tile_centre(key.y, MM, g.n2) - kTile * tt2;
-        const int o3 = tile_centre(key.z, MM, g.n3) - kTile * tt3;
-        R fr[NSLOT], fi[NSLOT];
-        int off[NSLOT];
-#pragma unroll
-        for (int k = 0; k < NSLOT; ++k) {
-            const int slot = lane + 32 * k;
-            const bool in = slot < W * W;
-            const int b = in ? slot / W : 0, c = in ? slot - (slot / W) * W : 0;
-            const R w23 = __shfl_sync(0xffffffffu, w[1], b) * __shfl_sync(0xffffffffu, w[2], c);
-            fr[k] = in ? fv.x * w23 : (R)0;
-            fi[k] = in ? fv.y * w23 : (R)0;
-            off[k] = in ? (o2 + b) * B + (o3 + c) : -1;
-        }
-#pragma unroll 1
-        for (int a = 0; a < W; ++a) {
-            const R w1 = __shfl_sync(0xffffffffu, w[0], a);
-            const int base = (o1 + a) * B * B;
-#pragma unroll
-            for (int k = 0; k < NSLOT; ++k) {
-                if (off[k] < 0) continue;
-                atomicAdd(box_re + base + off[k], fr[k] * w1);
-                atomicAdd(box_im + base + off[k], fi[k] * w1);
-            }
-        }
-    }
-    __syncthreads();
-    // the box starts m nodes before the tile in every dimension
-    const int b1 = kTile * tt1 - MM, b2 = kTile * tt2 - MM, b3 = kTile * tt3 - MM;
-    for (int e = threadIdx.x; e < B3; e += THREADS) {
-        const R re = box_re[e], im = box_im[e];
-        if (re == (R)0 && im == (R)0) continue;
-        const int i1 = e / (B * B), i2 = (e / B) % B, i3 = e % B;
-        const int64_t node = ((int64_t)wrap_node(b1 + i1, g.n1) * g.n2 + wrap_node(b2 + i2, g.n2)) * g.n3 +
-                             wrap_node(b3 + i3, g.n3);
-        R *dst = reinterpret_cast<R *>(H + node);
-        atomicAdd(dst, re);
-        atomicAdd(dst + 1, im);
+// wrap[d B + i] = the grid index (mod n_d) of box index i in dimension d; the
+// box of tile (tt1, tt2, tt3) starts MM nodes before the tile.  The caller
+// synchronises before the first read.
+template <int B, int MM>
+__device__ __forceinline__ void fill_wrap(int *wrap, int tt1, int tt2, int tt3, Grid3 g) {
+    for (int e = threadIdx.x; e < 3 * B; e += blockDim.x) {
+        const int d = e / B, i = e - d * B;
+        const int tt = d == 0 ? tt1 : d == 1 ? tt2 : tt3, n = d == 0 ? g.n1 : d == 1 ? g.n2 : g.n3;
+        wrap[e] = wrap_node(kTile * tt - MM + i, n);
     }
 }
 
@@ -143,23 +73,62 @@ __device__ __forceinline__ float2 df2_split(double v) {
     return make_float2(h, __double2float_rn(v - (double)h));
 }
 
-// shared memory of the double-float spread: the box (float4 a node) and the
-// staged weights, values and box offsets of up to kChunk points
+// Each chunk is served by two blocks, one per half of its box (planes
+// [0, B/2) and [B/2, B)): a half box and the chunk's staged weights fit twice
+// in one SM's shared memory, so two blocks overlap one another's loads,
+// barriers and flushes.  Warp (q, h) of a half owns the rows of parity h in
+// the half's planes q and B/2 - 1 - q: a point's stencil planes start at one
+// of the tile's first kTile planes, so the planes near the middle of the box
+// receive every point and the outer ones few, and pairing an outer plane
+// with an inner one evens the warps' loads.
+template <int MM> struct SpreadDF {
+    static constexpr int W = 2 * MM + 1, B = kTile + 2 * MM, HB = B / 2;   // HB: planes per half
+    static constexpr int NPAIR = (HB + 1) / 2, THREADS = 64 * NPAIR;
+    // NR: stencil rows of one parity (at most); NS2: lane slots covering them
+    static constexpr int NR = (W + 1) / 2, NS2 = (NR * W + 31) / 32;
+    static_assert(B % 2 == 0, "two halves of B / 2 planes");
+};
+
+// shared memory of the double-float spread: the half box (float4 a node, and
+// a spare node for lane slots outside the stencil), the staged weights,
+// values and box offsets of up to kChunk points, the tap polynomials and the
+// wrapped grid indices of the box
 template <int MM> constexpr size_t spread_df_smem() {
-    constexpr int W = 2 * MM + 1, B = kTile + 2 * MM;
-    return sizeof(float4) * (size_t)B * B * B + sizeof(float2) * (size_t)kChunk * 3 * W +
-           sizeof(float4) * (size_t)kChunk + sizeof(int4) * (size_t)kChunk + sizeof(PolyDF<MM>);
+    using S = SpreadDF<MM>;
+    return sizeof(float4) * ((size_t)S::HB * S::B * S::B + 1) + sizeof(float2) * (size_t)kChunk * 3 * S::W +
+           sizeof(float4) * (size_t)kChunk + sizeof(int4) * (size_t)kChunk + sizeof(PolyDF<MM>) +
+           sizeof(int) * 3 * S::B;
 }
 
-// exact float -> double from the bits (no FP64 conversion instruction) for
-// normal floats; zeros, subnormals and non-finite values take the conversion
-__device__ __forceinline__ double f2d_bits(float x) {
-    const unsigned u = __float_as_uint(x);
-    const unsigned ex = (u >> 23) & 0xFFu;
-    if (ex == 0u || ex == 0xFFu) return (double)x;
-    return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
-                                            ((unsigned long long)(ex + 896u) << 52) |
-                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+// (double)h + (double)l of a normalised double-float pair (|l| <= ulp(h) / 2)
+// with integer instructions (GB300's FP64 pipe is 1/64 of its FP32 rate):
+// h's 24-bit significand T sits at bit 52 of an integer, l's is added at its
+// binary point (bits of l below 2^-29 ulp(h) truncated), and T is brought
+// back to [2^52, 2^53) by at most one shift -- within 2^-51 of the sum.
+// Subnormal and non-finite h, and a pair that is not normalised, take the
+// FP64 addition.
+__device__ __forceinline__ double df_pair_to_double(float h, float l) {
+    const unsigned uh = __float_as_uint(h), ul = __float_as_uint(l);
+    const int eh = (int)((uh >> 23) & 0xFFu), el = (int)((ul >> 23) & 0xFFu);
+    const int sh = el - eh + 29;   // l = ml 2^sh in units of 2^(eh - 179), h = T in those units
+    if ((uh & 0x7FFFFFFFu) == 0u) return 0.0;   // h = 0: l = 0 in a normalised pair
+    if (eh == 0 || eh == 0xFF || el == 0xFF || (el != 0 && sh > 5)) return (double)h + (double)l;
+    long long T = (long long)((uh & 0x7FFFFFu) | 0x800000u) << 29;
+    if (el != 0) {
+        const long long ml = (long long)((ul & 0x7FFFFFu) | 0x800000u);
+        const long long L = sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> -sh) : 0);
+        T += ((uh ^ ul) >> 31) ? -L : L;
+    }
+    unsigned long long E = (unsigned long long)(eh + 896);   // T in [2^52, 2^53): exponent eh - 127
+    if (T >= (1ll << 53)) {
+        T >>= 1;
+        ++E;
+    } else if (T < (1ll << 52)) {
+        T <<= 1;
+        --E;
+    }
+    return __longlong_as_double((long long)(((unsigned long long)(uh & 0x80000000u) << 32) | (E << 52) |
+                                            ((unsigned long long)T & ((1ull << 52) - 1))));
 }
 
 // ---- deterministic flush: exact fixed-point sums ----------------------------
@@ -206,25 +175,29 @@ __device__ __forceinline__ void fixed_add(unsigned long long *q, float h, float 
 }
 
 // FIXED: flush into the fixed-point grid Hq (four int64 limbs per node: re
-// hi, re lo, im hi, im lo) instead of FP64 atomics into H (deterministic mode)
+// hi, re lo, im hi, im lo) instead of FP64 atomics into H (deterministic
+// mode).  zero: a run-time zero for the packed arithmetic (x2_opaque).
 template <int MM, bool FIXED>
-__global__ void __launch_bounds__(32 * (kTile + 2 * MM), 1) spread_tile_df_kernel(
+__global__ void __launch_bounds__(SpreadDF<MM>::THREADS) spread_tile_df_kernel(
     const double2 *__restrict__ f, Grid3 g, PointsView<double> pts, const __grid_constant__ PolyDF<MM> P,
-    const int4 *__restrict__ chunks, int nt2, int nt3, double2 *__restrict__ H, unsigned long long *__restrict__ Hq) {
-    constexpr int W = 2 * MM + 1, B = kTile + 2 * MM, B3 = B * B * B, D = kPolyDegDF;
-    // NR: stencil rows of one parity (at most); NS2: lane slots covering them
-    constexpr int THREADS = 32 * B, NR = (W + 1) / 2, NS2 = (NR * W + 31) / 32;
-    static_assert(B % 2 == 0, "plane pairs q, q + B/2");
+    const int4 *__restrict__ chunks, int nt2, int nt3, double2 *__restrict__ H, unsigned long long *__restrict__ Hq,
+    f32x2 zero) {
+    using S = SpreadDF<MM>;
+    constexpr int W = S::W, B = S::B, HB = S::HB, HB3 = HB * B * B, D = kPolyDegDF;
+    constexpr int THREADS = S::THREADS, NR = S::NR, NS2 = S::NS2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4 *box = reinterpret_cast<float4 *>(smem_raw);                 // (re hi, re lo, im hi, im lo)
-    float2 *wts = reinterpret_cast<float2 *>(box + B3);                   // [point][d][tap]
-    float4 *fsm = reinterpret_cast<float4 *>(wts + kChunk * 3 * W);      // f_j as (re hi, re lo, im hi, im lo)
+    float4 *box = reinterpret_cast<float4 *>(smem_raw);                 // (re hi, im hi, re lo, im lo); + 1 spare
+    float2 *wts = reinterpret_cast<float2 *>(box + HB3 + 1);              // [point][d][tap]
+    float4 *fsm = reinterpret_cast<float4 *>(wts + kChunk * 3 * W);      // f_j as (re hi, im hi, re lo, im lo)
     int4 *osm = reinterpret_cast<int4 *>(fsm + kChunk);                  // box index of the first node
     PolyDF<MM> *tab = reinterpret_cast<PolyDF<MM> *>(osm + kChunk);       // double-float tap polynomials
-    const int4 ch = chunks[blockIdx.x];
+    int *wrap = reinterpret_cast<int *>(tab + 1);                         // grid index of box index i, per dimension
+    const int part = blockIdx.x & 1;                                      // planes [part HB, part HB + HB)
+    const int4 ch = chunks[blockIdx.x >> 1];
     const int t = ch.x;
     const int tt3 = t % nt3, tt2 = (t / nt3) % nt2, tt1 = t / (nt3 * nt2);
-    for (int e = threadIdx.x; e < B3; e += THREADS) box[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = threadIdx.x; e < HB3; e += THREADS) box[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    fill_wrap<B, MM>(wrap, tt1, tt2, tt3, g);
     {
         const float *src = &P.ch[0][0][0];
         float *dst = &tab->ch[0][0][0];
@@ -249,72 +222,98 @@ __global__ void __launch_bounds__(32 * (kTile + 2 * MM), 1) spread_tile_df_kerne
         // FP64 family: f enters scaled by 2^s, so the float pairs keep its range
         const double2 fv = scale_value(f[key.w], value_shift(pts.vexp));
         const float2 re = df2_split(fv.x), im = df2_split(fv.y);
-        fsm[i] = make_float4(re.x, re.y, im.x, im.y);
-        osm[i] = make_int4(tile_centre(key.x, MM, g.n1) - kTile * tt1, tile_centre(key.y, MM, g.n2) - kTile * tt2,
-                           tile_centre(key.z, MM, g.n3) - kTile * tt3, 0);
+        fsm[i] = make_float4(re.x, im.x, re.y, im.y);
+        // box plane index of the stencil's first node, relative to this half
+        osm[i] = make_int4(tile_centre(key.x, MM, g.n1) - kTile * tt1 - part * HB,
+                           tile_centre(key.y, MM, g.n2) - kTile * tt2, tile_centre(key.z, MM, g.n3) - kTile * tt3, 0);
     }
     __syncthreads();
-    // phase 2: warp (q, h) owns box planes q and q + B/2, rows of parity h
+    // phase 2: warp (q, h) owns local planes q and HB - 1 - q (one plane when
+    // they coincide), rows of parity h.  Lane slot k covers stencil row
+    // b = b0 + 2 r and column c (b0: the point's first row of parity h);
+    // slots past the stencil update the spare node box[HB3], so the loop has
+    // no branches.  Complex values are packed pairs: hi = (re hi, im hi),
+    // lo = (re lo, im lo).
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, h = wid & 1, q0 = wid >> 1;
-    int rr[NS2], cc[NS2];
+    const int plane_of[2] = {q0, HB - 1 - q0};
+    const bool second = HB - 1 - q0 != q0;
+    constexpr int kFar = 1 << 20;   // an offset that sends the slot to the spare node
+    int roff[2][NS2], w2o[2][NS2], w3o[NS2];
 #pragma unroll
     for (int k = 0; k < NS2; ++k) {
         const int sl = lane + 32 * k;
-        rr[k] = sl < NR * W ? sl / W : W;   // W: no node (b >= W below)
-        cc[k] = sl < NR * W ? sl - (sl / W) * W : 0;
+        const int r = sl < NR * W ? sl / W : 0, c = sl < NR * W ? sl - (sl / W) * W : 0;
+#pragma unroll
+        for (int b0 = 0; b0 < 2; ++b0) {
+            const int b = b0 + 2 * r;
+            const bool ok = sl < NR * W && b < W;
+            roff[b0][k] = ok ? b * B + c : kFar;
+            w2o[b0][k] = ok ? W + b : W;
+        }
+        w3o[k] = 2 * W + c;
     }
+    ulonglong2 *boxp = reinterpret_cast<ulonglong2 *>(box);
     for (int i = 0; i < ch.z; ++i) {
         const int4 o = osm[i];
         const int b0 = (h - o.y) & 1;   // first stencil row whose box row has parity h
         const float2 *wi = wts + i * 3 * W;
-        const float4 fv = fsm[i];
+        const ulonglong2 fv = reinterpret_cast<const ulonglong2 *>(fsm)[i];
+        // the point's nodes in this warp's set are distinct: all are loaded
+        // before any is stored, so their updates overlap
+        int idx[2][NS2];
+        ulonglong2 nv[2][NS2];
 #pragma unroll
         for (int pp = 0; pp < 2; ++pp) {
-            const int plane = q0 + pp * (B / 2);
-            const int a = plane - o.x;
-            if (a < 0 || a >= W) continue;
-            const float2 w1 = wi[a];
-            const float2 fr = df2_mul(make_float2(fv.x, fv.y), w1), fi = df2_mul(make_float2(fv.z, fv.w), w1);
-            float4 *pl = box + plane * B * B;
+            const int plane = plane_of[pp], a = plane - o.x;
+            const bool on = (pp == 0 || second) && a >= 0 && a < W;
+            const int base = (plane * B + o.y) * B + o.z;
 #pragma unroll
             for (int k = 0; k < NS2; ++k) {
-                const int b = b0 + 2 * rr[k], c = cc[k];
-                if (b >= W) continue;
+                idx[pp][k] = min(base + (b0 ? roff[1][k] : roff[0][k]), HB3);
+                if (on) nv[pp][k] = boxp[idx[pp][k]];
+            }
+        }
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp) {
+            const int a = plane_of[pp] - o.x;
+            if ((pp == 1 && !second) || a < 0 || a >= W) continue;
+            // F = f w1 as packed double-float pairs
+            const float2 w1 = wi[a];
+            f32x2 fh = 0ull, fl = 0ull;
+            x2_df_mac(fh, fl, fv.x, fv.y, x2_pack(w1.x, w1.x), x2_pack(w1.y, w1.y), zero);
+            x2_df_norm(fh, fl);
+#pragma unroll
+            for (int k = 0; k < NS2; ++k) {
                 // w2 w3 as an unnormalised pair (product, its error): the
                 // multiply-add below only needs |low| within a few ulps
-                const float2 u = wi[W + b], v3 = wi[2 * W + c];
+                const float2 u = wi[b0 ? w2o[1][k] : w2o[0][k]], v3 = wi[w3o[k]];
                 const float wp = __fmul_rn(u.x, v3.x);
                 float we = __fmaf_rn(u.x, v3.x, -wp);
                 we = __fmaf_rn(u.x, v3.y, we);
                 we = __fmaf_rn(u.y, v3.x, we);
-                float4 &node = pl[(o.y + b) * B + (o.z + c)];
-                // node += f w1 w2 w3: exact product, two-sum into the high part,
+                // node += F w2 w3: exact product, two-sum into the high part,
                 // errors into the low part, renormalised so that the low part
                 // stays below half an ulp of the high part
-                float4 nv = node;
-                df_mac(nv.x, nv.y, fr.x, fr.y, wp, we);
-                df_mac(nv.z, nv.w, fi.x, fi.y, wp, we);
-                df_norm(nv.x, nv.y);
-                df_norm(nv.z, nv.w);
-                node = nv;
+                ulonglong2 v = nv[pp][k];
+                x2_df_mac(v.x, v.y, fh, fl, x2_pack(wp, wp), x2_pack(we, we), zero);
+                x2_df_norm(v.x, v.y);
+                boxp[idx[pp][k]] = v;
             }
         }
     }
     __syncthreads();
-    const int b1 = kTile * tt1 - MM, b2 = kTile * tt2 - MM, b3 = kTile * tt3 - MM;
-    for (int e = threadIdx.x; e < B3; e += THREADS) {
-        const float4 v = box[e];
-        if (v.x == 0.f && v.z == 0.f) continue;
-        const int i1 = e / (B * B), i2 = (e / B) % B, i3 = e % B;
-        const int64_t node = ((int64_t)wrap_node(b1 + i1, g.n1) * g.n2 + wrap_node(b2 + i2, g.n2)) * g.n3 +
-                             wrap_node(b3 + i3, g.n3);
+    for (int e = threadIdx.x; e < HB3; e += THREADS) {
+        const float4 v = box[e];   // (re hi, im hi, re lo, im lo)
+        if (v.x == 0.f && v.y == 0.f) continue;
+        const int i1 = e / (B * B) + part * HB, i2 = (e / B) % B, i3 = e % B;
+        const int64_t node = ((int64_t)wrap[i1] * g.n2 + wrap[B + i2]) * g.n3 + wrap[2 * B + i3];
         if (FIXED) {
-            fixed_add(Hq + 4 * node, v.x, v.y);
-            fixed_add(Hq + 4 * node + 2, v.z, v.w);
+            fixed_add(Hq + 4 * node, v.x, v.z);
+            fixed_add(Hq + 4 * node + 2, v.y, v.w);
         } else {
             double *dst = reinterpret_cast<double *>(H + node);
-            atomicAdd(dst, f2d_bits(v.x) + f2d_bits(v.y));
-            atomicAdd(dst + 1, f2d_bits(v.z) + f2d_bits(v.w));
+            atomicAdd(dst, df_pair_to_double(v.x, v.z));
+            atomicAdd(dst + 1, df_pair_to_double(v.y, v.w));
         }
     }
 }
@@ -338,7 +337,8 @@ __global__ void fixed_to_grid_kernel(const unsigned long long *__restrict__ Hq, 
 template <int MM> constexpr size_t spread_f32_smem() {
     constexpr int W = 2 * MM + 1, B = kTile + 2 * MM;
     return sizeof(float2) * (size_t)B * B * B + sizeof(float) * (size_t)kChunk * 3 * W +
-           sizeof(float2) * (size_t)kChunk + sizeof(int4) * (size_t)kChunk + sizeof(Poly<float, MM>);
+           sizeof(float2) * (size_t)kChunk + sizeof(int4) * (size_t)kChunk + sizeof(Poly<float, MM>) +
+           sizeof(int) * 3 * B;
 }
 
 template <int MM>
@@ -354,10 +354,12 @@ __global__ void __launch_bounds__(32 * (kTile + 2 * MM)) spread_tile_f32_kernel(
     float2 *fsm = reinterpret_cast<float2 *>(wts + kChunk * 3 * W);      // f_j
     int4 *osm = reinterpret_cast<int4 *>(fsm + kChunk);                  // box index of the first node
     Poly<float, MM> *tab = reinterpret_cast<Poly<float, MM> *>(osm + kChunk);
+    int *wrap = reinterpret_cast<int *>(tab + 1);                         // grid index of box index i, per dimension
     const int4 ch = chunks[blockIdx.x];
     const int t = ch.x;
     const int tt3 = t % nt3, tt2 = (t / nt3) % nt2, tt1 = t / (nt3 * nt2);
     for (int e = threadIdx.x; e < B3; e += THREADS) box[e] = make_float2(0.f, 0.f);
+    fill_wrap<B, MM>(wrap, tt1, tt2, tt3, g);
     {
         const float *src = &P.c[0][0][0];
         float *dst = &tab->c[0][0][0];
@@ -396,33 +398,41 @@ __global__ void __launch_bounds__(32 * (kTile + 2 * MM)) spread_tile_f32_kernel(
         const int b0 = (h - o.y) & 1;   // first stencil row whose box row has parity h
         const float *wi = wts + i * 3 * W;
         const float2 fv = fsm[i];
+        // distinct nodes: all loaded before any is stored
+        int idx[2][NS2];
+        float2 nv[2][NS2];
 #pragma unroll
         for (int pp = 0; pp < 2; ++pp) {
-            const int plane = q0 + pp * (B / 2);
-            const int a = plane - o.x;
+            const int plane = q0 + pp * (B / 2), a = plane - o.x;
+            const bool on = a >= 0 && a < W;
+#pragma unroll
+            for (int k = 0; k < NS2; ++k) {
+                const int b = b0 + 2 * rr[k];
+                idx[pp][k] = (on && b < W) ? (plane * B + o.y + b) * B + o.z + cc[k] : -1;
+                if (idx[pp][k] >= 0) nv[pp][k] = box[idx[pp][k]];
+            }
+        }
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp) {
+            const int a = q0 + pp * (B / 2) - o.x;
             if (a < 0 || a >= W) continue;
             const float w1 = wi[a];
             const float fr = fv.x * w1, fi = fv.y * w1;
-            float2 *pl = box + plane * B * B;
 #pragma unroll
             for (int k = 0; k < NS2; ++k) {
-                const int b = b0 + 2 * rr[k], c = cc[k];
-                if (b >= W) continue;
-                const float w23 = wi[W + b] * wi[2 * W + c];
-                float2 &node = pl[(o.y + b) * B + (o.z + c)];
-                const float2 v = node;
-                node = make_float2(fmaf(fr, w23, v.x), fmaf(fi, w23, v.y));
+                if (idx[pp][k] < 0) continue;
+                const float w23 = wi[W + b0 + 2 * rr[k]] * wi[2 * W + cc[k]];
+                const float2 v = nv[pp][k];
+                box[idx[pp][k]] = make_float2(fmaf(fr, w23, v.x), fmaf(fi, w23, v.y));
             }
         }
     }
     __syncthreads();
-    const int b1 = kTile * tt1 - MM, b2 = kTile * tt2 - MM, b3 = kTile * tt3 - MM;
     for (int e = threadIdx.x; e < B3; e += THREADS) {
         const float2 v = box[e];
         if (v.x == 0.f && v.y == 0.f) continue;
         const int i1 = e / (B * B), i2 = (e / B) % B, i3 = e % B;
-        const int64_t node = ((int64_t)wrap_node(b1 + i1, g.n1) * g.n2 + wrap_node(b2 + i2, g.n2)) * g.n3 +
-                             wrap_node(b3 + i3, g.n3);
+        const int64_t node = ((int64_t)wrap[i1] * g.n2 + wrap[B + i2]) * g.n3 + wrap[2 * B + i3];
         float *dst = reinterpret_cast<float *>(H + node);
         atomicAdd(dst, v.x);
         atomicAdd(dst + 1, v.y);
@@ -441,24 +451,18 @@ cudaError_t spread_tile_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsVi
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f);
         if (e != cudaSuccess) return e;
         kern<<<(unsigned)nchunks, 32 * B, smem_f, st>>>(f, g, pts, make_poly<float, MM>(w), chunks, nt2, nt3, H);
-    } else if constexpr (spread_df_smem<MM>() <= 227 * 1024) {
-        // FP64 family: the double-float kernel where its box and staged weights
-        // fit one SM's shared memory (m <= 7)
+    } else {
+        static_assert(spread_df_smem<MM>() <= 227 * 1024, "half box and staged weights fit one block");
+        // FP64 family: the double-float kernel where its half box and staged
+        // weights fit one SM's shared memory (every m up to 8)
         constexpr size_t smem_df = spread_df_smem<MM>();
         if (!wdf) return cudaErrorInvalidValue;
         auto kern = Hq ? spread_tile_df_kernel<MM, true> : spread_tile_df_kernel<MM, false>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
         if (e != cudaSuccess) return e;
-        kern<<<(unsigned)nchunks, 32 * B, smem_df, st>>>(f, g, pts, make_poly_df<MM>(*wdf), chunks, nt2, nt3, H, Hq);
-    } else {
-        if (Hq) return cudaErrorInvalidValue;   // deterministic mode: not at this m
-        // FP64 at m = 8: the box alone takes most of an SM's shared memory;
-        // FP64 shared-memory atomics, 512 threads
-        const size_t smem = 2 * sizeof(R) * (size_t)B * B * B;
-        auto kern = spread_tile_kernel<R, MM, 512>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kern<<<(unsigned)nchunks, 512, smem, st>>>(f, g, pts, make_poly<R, MM>(w), chunks, nt2, nt3, H);
+        // two blocks per chunk, one per half box
+        kern<<<2u * (unsigned)nchunks, SpreadDF<MM>::THREADS, smem_df, st>>>(f, g, pts, make_poly_df<MM>(*wdf),
+                                                                            chunks, nt2, nt3, H, Hq, 0ull);
     }
     return cudaGetLastError();
 }
