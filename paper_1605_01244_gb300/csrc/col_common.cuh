@@ -164,6 +164,56 @@ template <int MM> struct WeightsFP64 {
     }
 };
 
+// Half-interval tables (HalfTables in internal.cuh): the row and argument u
+// in [-1, 1] of tap `tap` at offset s.  4s - 3 is exact for s in [1/2, 1);
+// 1 - 4s is exact for s >= 1/8 and within 2^-53 below.
+template <int MM> __device__ __forceinline__ void half_arg(int tap, double s, int &row, double &u) {
+    const bool up = s >= 0.5;
+    row = up ? tap : 2 * MM - tap;
+    u = up ? fma(4.0, s, -3.0) : fma(-4.0, s, 1.0);
+}
+template <int MM> struct WeightsFP64H {
+    using Table = PolyN<double, MM, kPolyDegHalf>;
+    static constexpr int W = 2 * MM + 1, D = kPolyDegHalf;
+    double c[3][W][D + 1];
+    __device__ void load(const Table &P) {
+        for (int i = threadIdx.x; i < 3 * W * (D + 1); i += blockDim.x) (&c[0][0][0])[i] = (&P.c[0][0][0])[i];
+    }
+    __device__ __forceinline__ void eval(int d, int tap, double s, float &wh, float &wl) const {
+        int row;
+        double u;
+        half_arg<MM>(tap, s, row, u);
+        double v = c[d][row][D];
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) v = fma(v, u, c[d][row][k]);
+        split_df(v, wh, wl);
+    }
+};
+template <int MM> struct WeightsDFH {
+    using Table = PolyDFN<MM, kPolyDegHalf>;
+    static constexpr int W = 2 * MM + 1, D = kPolyDegHalf;
+    float ch[3][W][D + 1];
+    float cl[3][W][D + 1];
+    __device__ void load(const Table &P) {
+        for (int i = threadIdx.x; i < 3 * W * (D + 1); i += blockDim.x) {
+            (&ch[0][0][0])[i] = (&P.ch[0][0][0])[i];
+            (&cl[0][0][0])[i] = (&P.cl[0][0][0])[i];
+        }
+    }
+    __device__ __forceinline__ void eval(int d, int tap, double s, float &wh, float &wl) const {
+        int row;
+        double u;
+        half_arg<MM>(tap, s, row, u);
+        const float uh = __double2float_rn(u);
+        const float ul = __double2float_rn(u - (double)uh);
+        float vh = ch[d][row][D], vl = cl[d][row][D];
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) df_horner_step(vh, vl, uh, ul, ch[d][row][k], cl[d][row][k]);
+        wh = vh;
+        wl = vl;
+    }
+};
+
 // Value and derivative weights: P(t) and dP/dx = -2 n_d P'(t) (t = 2s - 1,
 // s decreases by n_d per unit of x), Horner for P and P' together.
 template <int MM> struct WeightsFP64D {

@@ -214,14 +214,14 @@ __global__ void __launch_bounds__(256) gather_col_f32_cube_kernel(const float2 *
 // weight w2[b] w3[c] is formed once per point; per plane a lane adds its
 // slots' products and the plane weight w1[a] multiplies the lane sum; the
 // group reduces the lane sums at the end.  Double-float throughout.
-template <int MM>
+template <int MM, class Wt>
 __global__ void __launch_bounds__(256, GBNFFT_SLOT_MINB) gather_slot_df_kernel(
     const float4 *__restrict__ G, Grid3 pg, PointsView<double> pts,
-    const __grid_constant__ typename WeightsFP64<MM>::Table P, double2 *__restrict__ f) {
+    const __grid_constant__ typename Wt::Table P, double2 *__restrict__ f) {
     constexpr int W = 2 * MM + 1;
     constexpr int GS = GroupSize<W>::value;
     constexpr int NSLOT = (W * W + GS - 1) / GS;
-    __shared__ WeightsFP64<MM> wt;
+    __shared__ Wt wt;
     wt.load(P);
     __syncthreads();
 
@@ -577,13 +577,22 @@ cudaError_t split_f32_dispatch(const float2 *G, Grid3 g, PointsView<float> pts, 
 template <int MM, int NG>
 cudaError_t col_df_dispatch(const float4 *G, Grid3 g, PointsView<double> pts, const WinTableDF &w,
                             const WinTable<double> &w64, bool fp64_weights, double2 *f, double2 *grad,
-                            cudaStream_t st) {
+                            cudaStream_t st, const HalfTables *half) {
     constexpr int GS = GroupSize<2 * MM + 1>::value;
     const int threads = 256;
     const int64_t blocks = (pts.M * GS + threads - 1) / threads;
-    if (NG == 1 && fp64_weights && !std::getenv("GBNFFT_DF_COLUMNS"))
-        gather_slot_df_kernel<MM><<<(unsigned)blocks, threads, 0, st>>>(G, g, pts, make_poly<double, MM>(w64), f);
-    else if (fp64_weights)
+    const int hmode = half ? half->mode : 0;
+    if (NG == 1 && fp64_weights && !std::getenv("GBNFFT_DF_COLUMNS")) {
+        if (hmode == 1)
+            gather_slot_df_kernel<MM, WeightsFP64H<MM>><<<(unsigned)blocks, threads, 0, st>>>(
+                G, g, pts, make_poly_n<double, MM, kPolyDegHalf>(half->w64), f);
+        else if (hmode == 2)
+            gather_slot_df_kernel<MM, WeightsDFH<MM>><<<(unsigned)blocks, threads, 0, st>>>(
+                G, g, pts, make_poly_dfn<MM, kPolyDegHalf>(half->wdf), f);
+        else
+            gather_slot_df_kernel<MM, WeightsFP64<MM>><<<(unsigned)blocks, threads, 0, st>>>(
+                G, g, pts, make_poly<double, MM>(w64), f);
+    } else if (fp64_weights)
         gather_col_df_kernel<MM, NG, WeightsFP64<MM>><<<(unsigned)blocks, threads, 0, st>>>(
             G, g, pts, make_poly<double, MM>(w64), f, grad);
     else
@@ -612,17 +621,17 @@ cudaError_t col_f32_select(const float2 *G, Grid3 g, int m, PointsView<float> pt
 template <int NG>
 cudaError_t col_df_select(const float4 *G, Grid3 g, int m, PointsView<double> pts,
                           const WinTableDF &w, const WinTable<double> &w64, bool fp64_weights, double2 *f,
-                          double2 *grad, cudaStream_t st) {
+                          double2 *grad, cudaStream_t st, const HalfTables *half) {
     if (pts.M == 0) return cudaSuccess;
     switch (m) {
-        case 1: return col_df_dispatch<1, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
-        case 2: return col_df_dispatch<2, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
-        case 3: return col_df_dispatch<3, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
-        case 4: return col_df_dispatch<4, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
-        case 5: return col_df_dispatch<5, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
-        case 6: return col_df_dispatch<6, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
-        case 7: return col_df_dispatch<7, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
-        case 8: return col_df_dispatch<8, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st);
+        case 1: return col_df_dispatch<1, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st, half);
+        case 2: return col_df_dispatch<2, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st, half);
+        case 3: return col_df_dispatch<3, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st, half);
+        case 4: return col_df_dispatch<4, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st, half);
+        case 5: return col_df_dispatch<5, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st, half);
+        case 6: return col_df_dispatch<6, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st, half);
+        case 7: return col_df_dispatch<7, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st, half);
+        case 8: return col_df_dispatch<8, NG>(G, g, pts, w, w64, fp64_weights, f, grad, st, half);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -669,9 +678,9 @@ cudaError_t launch_gather_split_f32(const float2 *G, Grid3 g, int m, PointsView<
 
 cudaError_t launch_gather_col_df(const float4 *G, Grid3 g, int m, PointsView<double> pts,
                                  const WinTableDF &w, const WinTable<double> &w64, bool fp64_weights,
-                                 double2 *f, double2 *grad, int ng, cudaStream_t st) {
-    return ng == 4 ? col_df_select<4>(G, g, m, pts, w, w64, fp64_weights, f, grad, st)
-                   : col_df_select<1>(G, g, m, pts, w, w64, fp64_weights, f, nullptr, st);
+                                 double2 *f, double2 *grad, int ng, cudaStream_t st, const HalfTables *half) {
+    return ng == 4 ? col_df_select<4>(G, g, m, pts, w, w64, fp64_weights, f, grad, st, nullptr)
+                   : col_df_select<1>(G, g, m, pts, w, w64, fp64_weights, f, nullptr, st, half);
 }
 
 }  // namespace gbnfft

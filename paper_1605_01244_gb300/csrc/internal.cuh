@@ -94,6 +94,48 @@ template <int MM> PolyDF<MM> make_poly_df(const WinTableDF &t) {
     return p;
 }
 
+// Half-interval window tables of the FP64 family's value gather.  The window
+// is even, so tap 2m - a at offset s weighs what tap a weighs at 1 - s:
+// w_{2m-a}(s) = w_a(1 - s).  A table of each tap on s in [1/2, 1] alone, as a
+// polynomial in u = 4s - 3, therefore serves every s: tap a at s >= 1/2 is row
+// a at u = 4s - 3, at s < 1/2 it is row 2m - a at u = 1 - 4s.  On the shorter
+// interval degree kPolyDegHalf reaches the accuracy that degree 16 gives on
+// the whole interval for m >= 4 (Chebyshev interpolation of the entire
+// window function; below m = 4 it falls short and the whole-interval table
+// serves).
+constexpr int kPolyDegHalf = 11;
+struct HalfTables {
+    WinTable<double> w64;   // FP64 coefficients, degree kPolyDegHalf in u
+    WinTableDF wdf;         // the same as float pairs (hi + lo)
+    int mode;               // 0: whole-interval FP64 table, 1: half table in FP64, 2: half table in double-float
+};
+template <typename R, int MM, int DD> struct PolyN {
+    static constexpr int W = 2 * MM + 1, D = DD;
+    R c[3][W][DD + 1];
+};
+template <typename R, int MM, int DD> PolyN<R, MM, DD> make_poly_n(const WinTable<R> &t) {
+    PolyN<R, MM, DD> p;
+    for (int d = 0; d < 3; ++d)
+        for (int a = 0; a < PolyN<R, MM, DD>::W; ++a)
+            for (int k = 0; k <= DD; ++k) p.c[d][a][k] = t.coef[d][a][k];
+    return p;
+}
+template <int MM, int DD> struct PolyDFN {
+    static constexpr int W = 2 * MM + 1, D = DD;
+    float ch[3][W][DD + 1];
+    float cl[3][W][DD + 1];
+};
+template <int MM, int DD> PolyDFN<MM, DD> make_poly_dfn(const WinTableDF &t) {
+    PolyDFN<MM, DD> p;
+    for (int d = 0; d < 3; ++d)
+        for (int a = 0; a < PolyDFN<MM, DD>::W; ++a)
+            for (int k = 0; k <= DD; ++k) {
+                p.ch[d][a][k] = t.ch[d][a][k];
+                p.cl[d][a][k] = t.cl[d][a][k];
+            }
+    return p;
+}
+
 // ---- range scaling of the FP64 family ---------------------------------------
 // The FP64 family computes its window sums, transform and adjoint spread in
 // double-float (float pairs), whose exponent range is FP32's.  So that any
@@ -221,9 +263,12 @@ cudaError_t launch_pad_grid_df(const double2 *G, Grid3 g, float4 *P, Grid3 pg, i
 cudaError_t launch_gather_col_f32(const float2 *G, Grid3 g, int m, PointsView<float> pts,
                                   const WinTable<float> &w, float2 *f, float2 *grad, int ng,
                                   cudaStream_t st);
+// half: the half-interval tables and their mode for the value gather (ng = 1;
+// nullptr or mode 0: the whole-interval FP64 table)
 cudaError_t launch_gather_col_df(const float4 *G, Grid3 g, int m, PointsView<double> pts,
                                  const WinTableDF &w, const WinTable<double> &w64, bool fp64_weights,
-                                 double2 *f, double2 *grad, int ng, cudaStream_t st);
+                                 double2 *f, double2 *grad, int ng, cudaStream_t st,
+                                 const HalfTables *half = nullptr);
 
 // ---- launchers implemented in kernels.cu (all enqueue on `st`) ------------
 

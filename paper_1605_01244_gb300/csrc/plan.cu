@@ -196,14 +196,17 @@ long double exact_weight(long double s, int a, int m, long double b) {
     return al / (1.0L - expl(-2.0L * b * al)) * expl(-b * tau * tau / (q + al)) * r;
 }
 
-// Degree-D interpolant of w_a(s) at the Chebyshev nodes of t = 2s - 1,
-// returned as monomial coefficients in t (mono[k] multiplies t^k).
-void fit_tap(int a, int m, long double b, int D, long double *mono) {
+// Degree-D interpolant of w_a(s) for s in [s0, s1] at the Chebyshev nodes of
+// t = (2s - s0 - s1) / (s1 - s0) in [-1, 1], returned as monomial
+// coefficients in t (mono[k] multiplies t^k).  The whole interval [0, 1]
+// gives t = 2s - 1; the upper half [1/2, 1] gives t = 4s - 3.
+void fit_tap(int a, int m, long double b, int D, long double *mono, long double s0 = 0.0L,
+             long double s1 = 1.0L) {
     const long double pi = acosl(-1.0L);
     long double f[kMaxCoef], cheb[kMaxCoef], Tm[kMaxCoef], T0[kMaxCoef], T1[kMaxCoef];
     for (int j = 0; j <= D; ++j) {
         const long double t = cosl(pi * ((long double)j + 0.5L) / (long double)(D + 1));
-        f[j] = exact_weight(0.5L * (t + 1.0L), a, m, b);
+        f[j] = exact_weight(s0 + 0.5L * (s1 - s0) * (t + 1.0L), a, m, b);
     }
     for (int k = 0; k <= D; ++k) {
         long double acc = 0;
@@ -241,9 +244,9 @@ template <typename R> R horner(const R *c, int D, R t) {
     return v;
 }
 
-// the double-float Horner of the FP64 family's FP32-pipe gather, step for step
-long double horner_df(const float *ch, const float *cl, int D, double s) {
-    const double t = 2.0 * s - 1.0;
+// the double-float Horner of the FP64 family's FP32-pipe gather, step for
+// step, at argument t (2s - 1 for the whole-interval table)
+long double horner_df(const float *ch, const float *cl, int D, double t) {
     const float th = (float)t, tl = (float)(t - (double)th);
     float vh = ch[D], vl = cl[D];
     for (int k = D - 1; k >= 0; --k) {
@@ -271,6 +274,8 @@ void build_window_tables(nfft3_plan p) {
     std::memset(&p->wt64, 0, sizeof(p->wt64));
     std::memset(&p->wt32, 0, sizeof(p->wt32));
     std::memset(&p->wtdf, 0, sizeof(p->wtdf));
+    std::memset(&p->half.w64, 0, sizeof(p->half.w64));
+    std::memset(&p->half.wdf, 0, sizeof(p->half.wdf));
     for (int d = 0; d < 3; ++d) {
         const long double b = (long double)p->b[d];
         for (int a = 0; a <= 2 * m; ++a) {
@@ -283,6 +288,12 @@ void build_window_tables(nfft3_plan p) {
                     p->wtdf.ch[d][a][k] = (float)mono[k];
                     p->wtdf.cl[d][a][k] = (float)(mono[k] - (long double)p->wtdf.ch[d][a][k]);
                 }
+                fit_tap(a, m, b, kPolyDegHalf, mono, 0.5L, 1.0L);
+                for (int k = 0; k <= kPolyDegHalf; ++k) {
+                    p->half.w64.coef[d][a][k] = (double)mono[k];
+                    p->half.wdf.ch[d][a][k] = (float)mono[k];
+                    p->half.wdf.cl[d][a][k] = (float)(mono[k] - (long double)p->half.wdf.ch[d][a][k]);
+                }
             } else {
                 fit_tap(a, m, b, PolyDeg<float>::value, mono);
                 for (int k = 0; k <= PolyDeg<float>::value; ++k) p->wt32.coef[d][a][k] = (float)mono[k];
@@ -293,7 +304,7 @@ void build_window_tables(nfft3_plan p) {
                 if (p->prec == 64) {
                     const double v = horner<double>(p->wt64.coef[d][a], PolyDeg<double>::value, 2.0 * s - 1.0);
                     const double e1 = (double)fabsl((long double)v - ex);
-                    const double e2 = (double)fabsl(horner_df(p->wtdf.ch[d][a], p->wtdf.cl[d][a], kPolyDegDF, s) - ex);
+                    const double e2 = (double)fabsl(horner_df(p->wtdf.ch[d][a], p->wtdf.cl[d][a], kPolyDegDF, 2.0 * s - 1.0) - ex);
                     if (e1 > p->window_err) p->window_err = e1;
                     if (e2 > p->window_err_df) p->window_err_df = e2;
                 } else {
@@ -303,6 +314,29 @@ void build_window_tables(nfft3_plan p) {
                 }
             }
         }
+    }
+    if (p->prec != 64 || p->half.mode == 0) return;
+    // the half-interval table in use, as the value gather evaluates it: tap a
+    // at s >= 1/2 from row a at u = 4s - 3, below from row 2m - a at u = 1 - 4s
+    for (int d = 0; d < 3; ++d) {
+        const long double b = (long double)p->b[d];
+        for (int a = 0; a <= 2 * m; ++a)
+            for (int i = 0; i <= kWindowSamples; ++i) {
+                const double s = (double)i / kWindowSamples;
+                const bool up = s >= 0.5;
+                const int row = up ? a : 2 * m - a;
+                const double u = up ? std::fma(4.0, s, -3.0) : std::fma(-4.0, s, 1.0);
+                const long double ex = exact_weight((long double)s, a, m, b);
+                if (p->half.mode == 1) {
+                    const double v = horner<double>(p->half.w64.coef[d][row], kPolyDegHalf, u);
+                    const double e1 = (double)fabsl((long double)v - ex);
+                    if (e1 > p->window_err) p->window_err = e1;
+                } else {
+                    const double e2 = (double)fabsl(
+                        horner_df(p->half.wdf.ch[d][row], p->half.wdf.cl[d][row], kPolyDegHalf, u) - ex);
+                    if (e2 > p->window_err_df) p->window_err_df = e2;
+                }
+            }
     }
 }
 
@@ -408,6 +442,17 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
         p->N[d] = Ns[d];
         p->n[d] = oversampled_size(Ns[d], sigma);
         p->b[d] = M_PI * (2.0 - (double)Ns[d] / (double)p->n[d]);
+    }
+    {
+        // FP64 value gather weights: half-interval table in double-float on
+        // the FP32 pipe (default), "fp64": the same table on the FP64 pipe,
+        // "full": the whole-interval FP64 table (read before the tables are
+        // built and checked); below m = 4 the half table of degree
+        // kPolyDegHalf is less accurate than the whole-interval one (2.9e-14
+        // at m = 1 against 1.9e-16), so the whole-interval table serves
+        const char *hw = std::getenv("GBNFFT_SLOT_WEIGHTS");
+        p->half.mode = hw && !std::strcmp(hw, "full") ? 0 : hw && !std::strcmp(hw, "fp64") ? 1 : 2;
+        if (p->m < 4) p->half.mode = 0;
     }
     build_window_tables(p);
     {
@@ -726,7 +771,8 @@ cudaError_t gather_padded(nfft3_plan p, int ng, typename Cplx<R>::T *f, typename
     p->launches += 1;
     if (prec == 64)
         return launch_gather_col_df((const float4 *)p->pgrid, pg, p->m, points_view<double>(p), p->wtdf,
-                                    p->wt64, p->df_weights_fp64, (double2 *)f, (double2 *)grad, ng, p->stream);
+                                    p->wt64, p->df_weights_fp64, (double2 *)f, (double2 *)grad, ng, p->stream,
+                                    &p->half);
     if (ng == 1 && p->pgrid_shift != 0 && p->tmap_ok && p->nchunks > 0)
         return launch_gather_tma_f32(p->tmap, p->pb.chunks, p->nchunks, p->pb.nt2, p->pb.nt3, g, p->m,
                                      points_view<float>(p), p->wt32, (float2 *)f, p->pb.status,

@@ -24,6 +24,7 @@ struct nfft3_plan_s {
     double window_err;
     double window_err_df;
     int df_weights_fp64;       // GBNFFT_DF_WEIGHTS: FP64-pipe weights (default) or df ("df")
+    gbnfft::HalfTables half;   // FP64 family: half-interval tables of the value gather (mode: GBNFFT_SLOT_WEIGHTS)
     int gather_mode;           // GBNFFT_GATHER: 0 col (default), 1 thread, 2 native (see plan.cu)
     int spread_direct;         // GBNFFT_SPREAD=direct: one thread per point, global atomics only
     int adj_cufft;             // GBNFFT_ADJ_FFT=cufft: adjoint transform by cuFFT + deconvolution kernel
