@@ -150,7 +150,7 @@ def gather_bytes(M: int, n: int, real_bytes: int) -> int:
 # (profiles/gather_col_128cubed_1.25e6pts_full.md, and
 # profiles/gather_split_f32_128cubed_1.25e6pts.md for the mixed family's two
 # split kernels together).
-GATHER_TRAFFIC_BYTES = {"gather_slot_df_kernel": 3.258e9,
+GATHER_TRAFFIC_BYTES = {"gather_slot_df_kernel": 3.255e9,
                         "gather_dense_f32_kernel + gather_col_f32_cube_kernel": 1.513e9}
 
 # FP32 instructions of one FP64-accurate (double-float) multiply-add: exact
