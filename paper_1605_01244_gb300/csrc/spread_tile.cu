@@ -81,22 +81,32 @@ __device__ __forceinline__ float2 df2_split(double v) {
 // of the tile's first kTile planes, so the planes near the middle of the box
 // receive every point and the outer ones few, and pairing an outer plane
 // with an inner one evens the warps' loads.
+//
+// Layout of a half box in shared memory: in each plane the rows of even
+// index come first, then the odd ones, each row padded to P nodes with
+// P = 5 (mod 8).  A warp's lane slots cover consecutive rows of one parity,
+// so the 8 lanes of a quarter warp (one 128-byte access of 16-byte nodes)
+// take the end of one row and the start of the next; with P = 5 (mod 8)
+// their nodes fall in 8 different bank groups.
 template <int MM> struct SpreadDF {
     static constexpr int W = 2 * MM + 1, B = kTile + 2 * MM, HB = B / 2;   // HB: planes per half
     static constexpr int NPAIR = (HB + 1) / 2, THREADS = 64 * NPAIR;
     // NR: stencil rows of one parity (at most); NS2: lane slots covering them
     static constexpr int NR = (W + 1) / 2, NS2 = (NR * W + 31) / 32;
+    static constexpr int P = B + ((13 - B % 8) % 8);   // row pitch: >= B, = 5 (mod 8)
+    static constexpr int PLANE = B * P, NODES = HB * PLANE;   // + 1 spare node
     static_assert(B % 2 == 0, "two halves of B / 2 planes");
+    static_assert(P % 8 == 5 && P >= B, "row pitch");
 };
 
 // shared memory of the double-float spread: the half box (float4 a node, and
 // a spare node for lane slots outside the stencil), the staged weights,
-// values and box offsets of up to kChunk points, the tap polynomials and the
+// values and packed box offsets of up to kChunk points, the tap polynomials and the
 // wrapped grid indices of the box
 template <int MM> constexpr size_t spread_df_smem() {
     using S = SpreadDF<MM>;
-    return sizeof(float4) * ((size_t)S::HB * S::B * S::B + 1) + sizeof(float2) * (size_t)kChunk * 3 * S::W +
-           sizeof(float4) * (size_t)kChunk + sizeof(int4) * (size_t)kChunk + sizeof(PolyDF<MM>) +
+    return sizeof(float4) * ((size_t)S::NODES + 1) + sizeof(float2) * (size_t)kChunk * 3 * S::W +
+           sizeof(float4) * (size_t)kChunk + sizeof(int) * (size_t)kChunk + sizeof(PolyDF<MM>) +
            sizeof(int) * 3 * S::B;
 }
 
@@ -179,27 +189,28 @@ __device__ __forceinline__ void fixed_add(unsigned long long *q, float h, float 
 // mode).  zero: a run-time zero for the packed arithmetic (x2_opaque).
 template <int MM, bool FIXED>
 __global__ void __launch_bounds__(SpreadDF<MM>::THREADS) spread_tile_df_kernel(
-    const double2 *__restrict__ f, Grid3 g, PointsView<double> pts, const __grid_constant__ PolyDF<MM> P,
+    const double2 *__restrict__ f, Grid3 g, PointsView<double> pts, const __grid_constant__ PolyDF<MM> Pt,
     const int4 *__restrict__ chunks, int nt2, int nt3, double2 *__restrict__ H, unsigned long long *__restrict__ Hq,
     f32x2 zero) {
     using S = SpreadDF<MM>;
-    constexpr int W = S::W, B = S::B, HB = S::HB, HB3 = HB * B * B, D = kPolyDegDF;
+    constexpr int W = S::W, B = S::B, HB = S::HB, D = kPolyDegDF, P = S::P, PLANE = S::PLANE;
+    constexpr int NODES = S::NODES;   // box[NODES]: the spare node
     constexpr int THREADS = S::THREADS, NR = S::NR, NS2 = S::NS2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *box = reinterpret_cast<float4 *>(smem_raw);                 // (re hi, im hi, re lo, im lo); + 1 spare
-    float2 *wts = reinterpret_cast<float2 *>(box + HB3 + 1);              // [point][d][tap]
+    float2 *wts = reinterpret_cast<float2 *>(box + NODES + 1);            // [point][d][tap]
     float4 *fsm = reinterpret_cast<float4 *>(wts + kChunk * 3 * W);      // f_j as (re hi, im hi, re lo, im lo)
-    int4 *osm = reinterpret_cast<int4 *>(fsm + kChunk);                  // box index of the first node
+    int *osm = reinterpret_cast<int *>(fsm + kChunk);                    // first node's box indices, packed
     PolyDF<MM> *tab = reinterpret_cast<PolyDF<MM> *>(osm + kChunk);       // double-float tap polynomials
     int *wrap = reinterpret_cast<int *>(tab + 1);                         // grid index of box index i, per dimension
     const int part = blockIdx.x & 1;                                      // planes [part HB, part HB + HB)
     const int4 ch = chunks[blockIdx.x >> 1];
     const int t = ch.x;
     const int tt3 = t % nt3, tt2 = (t / nt3) % nt2, tt1 = t / (nt3 * nt2);
-    for (int e = threadIdx.x; e < HB3; e += THREADS) box[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = threadIdx.x; e < NODES; e += THREADS) box[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     fill_wrap<B, MM>(wrap, tt1, tt2, tt3, g);
     {
-        const float *src = &P.ch[0][0][0];
+        const float *src = &Pt.ch[0][0][0];
         float *dst = &tab->ch[0][0][0];
         constexpr int NC = 2 * 3 * W * (D + 1);   // ch then cl
         for (int e = threadIdx.x; e < NC; e += THREADS) dst[e] = src[e];
@@ -223,21 +234,25 @@ __global__ void __launch_bounds__(SpreadDF<MM>::THREADS) spread_tile_df_kernel(
         const double2 fv = scale_value(f[key.w], value_shift(pts.vexp));
         const float2 re = df2_split(fv.x), im = df2_split(fv.y);
         fsm[i] = make_float4(re.x, im.x, re.y, im.y);
-        // box plane index of the stencil's first node, relative to this half
-        osm[i] = make_int4(tile_centre(key.x, MM, g.n1) - kTile * tt1 - part * HB,
-                           tile_centre(key.y, MM, g.n2) - kTile * tt2, tile_centre(key.z, MM, g.n3) - kTile * tt3, 0);
+        // box indices of the stencil's first node (plane relative to this
+        // half, in [-HB, kTile)), packed with a bias of 32 into 6-bit fields
+        const int ox = tile_centre(key.x, MM, g.n1) - kTile * tt1 - part * HB;
+        const int oy = tile_centre(key.y, MM, g.n2) - kTile * tt2, oz = tile_centre(key.z, MM, g.n3) - kTile * tt3;
+        osm[i] = (ox + 32) | (oy << 6) | (oz << 12);
     }
     __syncthreads();
     // phase 2: warp (q, h) owns local planes q and HB - 1 - q (one plane when
     // they coincide), rows of parity h.  Lane slot k covers stencil row
     // b = b0 + 2 r and column c (b0: the point's first row of parity h);
-    // slots past the stencil update the spare node box[HB3], so the loop has
+    // slots past the stencil update the spare node box[NODES], so the loop has
     // no branches.  Complex values are packed pairs: hi = (re hi, im hi),
     // lo = (re lo, im lo).
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, h = wid & 1, q0 = wid >> 1;
     const int plane_of[2] = {q0, HB - 1 - q0};
     const bool second = HB - 1 - q0 != q0;
     constexpr int kFar = 1 << 20;   // an offset that sends the slot to the spare node
+    // slot k of a lane: stencil row b = b0 + 2 r lies r storage rows after
+    // the point's first row of parity h
     int roff[2][NS2], w2o[2][NS2], w3o[NS2];
 #pragma unroll
     for (int k = 0; k < NS2; ++k) {
@@ -247,15 +262,18 @@ __global__ void __launch_bounds__(SpreadDF<MM>::THREADS) spread_tile_df_kernel(
         for (int b0 = 0; b0 < 2; ++b0) {
             const int b = b0 + 2 * r;
             const bool ok = sl < NR * W && b < W;
-            roff[b0][k] = ok ? b * B + c : kFar;
+            roff[b0][k] = ok ? r * P + c : kFar;
             w2o[b0][k] = ok ? W + b : W;
         }
         w3o[k] = 2 * W + c;
     }
     ulonglong2 *boxp = reinterpret_cast<ulonglong2 *>(box);
     for (int i = 0; i < ch.z; ++i) {
-        const int4 o = osm[i];
+        const int op = osm[i];
+        const int4 o = make_int4((op & 63) - 32, (op >> 6) & 63, op >> 12, 0);
         const int b0 = (h - o.y) & 1;   // first stencil row whose box row has parity h
+        // storage row of box row o.y + b0 (parity h): h B/2 + (o.y + b0) / 2
+        const int srow = h * (B / 2) + ((o.y + b0) >> 1);
         const float2 *wi = wts + i * 3 * W;
         const ulonglong2 fv = reinterpret_cast<const ulonglong2 *>(fsm)[i];
         // the point's nodes in this warp's set are distinct: all are loaded
@@ -266,10 +284,10 @@ __global__ void __launch_bounds__(SpreadDF<MM>::THREADS) spread_tile_df_kernel(
         for (int pp = 0; pp < 2; ++pp) {
             const int plane = plane_of[pp], a = plane - o.x;
             const bool on = (pp == 0 || second) && a >= 0 && a < W;
-            const int base = (plane * B + o.y) * B + o.z;
+            const int base = plane * PLANE + srow * P + o.z;
 #pragma unroll
             for (int k = 0; k < NS2; ++k) {
-                idx[pp][k] = min(base + (b0 ? roff[1][k] : roff[0][k]), HB3);
+                idx[pp][k] = min(base + (b0 ? roff[1][k] : roff[0][k]), NODES);
                 if (on) nv[pp][k] = boxp[idx[pp][k]];
             }
         }
@@ -302,10 +320,12 @@ __global__ void __launch_bounds__(SpreadDF<MM>::THREADS) spread_tile_df_kernel(
         }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < HB3; e += THREADS) {
-        const float4 v = box[e];   // (re hi, im hi, re lo, im lo)
+    for (int e = threadIdx.x; e < NODES; e += THREADS) {
+        const float4 v = box[e];   // (re hi, im hi, re lo, im lo); padding nodes stay zero
         if (v.x == 0.f && v.y == 0.f) continue;
-        const int i1 = e / (B * B) + part * HB, i2 = (e / B) % B, i3 = e % B;
+        const int pl = e / PLANE, rem = e - pl * PLANE, sr = rem / P, i3 = rem - sr * P;
+        if (i3 >= B) continue;
+        const int i1 = pl + part * HB, i2 = sr < B / 2 ? 2 * sr : 2 * (sr - B / 2) + 1;
         const int64_t node = ((int64_t)wrap[i1] * g.n2 + wrap[B + i2]) * g.n3 + wrap[2 * B + i3];
         if (FIXED) {
             fixed_add(Hq + 4 * node, v.x, v.z);
