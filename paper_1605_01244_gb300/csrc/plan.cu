@@ -1195,6 +1195,38 @@ template <typename R> int eval_host_impl(nfft3_plan p, const double *x_host, con
             return st;
         }
     }
+    if (p->fused && p->gather_mode == 3 && p->M > 0) {
+        // c first, then x, on the plan's stream (each copy gets the whole
+        // link); the transform of c runs on the auxiliary stream while x
+        // arrives and set_points sorts it; the gather waits for both
+        if (cudaMemcpyAsync(p->c_dev, c_host, 2 * sizeof(R) * NN, cudaMemcpyHostToDevice, p->stream) !=
+                cudaSuccess ||
+            cudaEventRecord(p->aux_ev[0], p->stream) != cudaSuccess ||
+            cudaMemcpyAsync(p->x_dev, x_host, sizeof(double) * 3 * p->M, cudaMemcpyHostToDevice, p->stream) !=
+                cudaSuccess ||
+            cudaStreamWaitEvent(p->aux_stream, p->aux_ev[0], 0) != cudaSuccess)
+            return NFFT3_ERR_CUDA;
+        cudaStream_t own = p->stream;
+        p->stream = p->aux_stream;   // the transform's launches go to the auxiliary stream
+        st = precompute_impl<R>(p, (const R *)p->c_dev, 0);
+        p->stream = own;
+        if (st != NFFT3_OK || cudaEventRecord(p->aux_ev[1], p->aux_stream) != cudaSuccess) {
+            cudaStreamSynchronize(p->aux_stream);
+            return st != NFFT3_OK ? st : NFFT3_ERR_CUDA;
+        }
+        st = set_points_impl(p, p->x_dev, prec);
+        if (st != NFFT3_OK) {
+            cudaStreamSynchronize(p->aux_stream);
+            return st;
+        }
+        if (cudaStreamWaitEvent(p->stream, p->aux_ev[1], 0) != cudaSuccess) return NFFT3_ERR_CUDA;
+        st = eval_stored_impl<R>(p, (R *)p->f_dev, nullptr, 1);
+        if (st < 0) return st;
+        if (cudaMemcpyAsync(f_host, p->f_dev, 2 * sizeof(R) * p->M, cudaMemcpyDeviceToHost, p->stream) !=
+            cudaSuccess)
+            return NFFT3_ERR_CUDA;
+        return cudaStreamSynchronize(p->stream) == cudaSuccess ? NFFT3_OK : NFFT3_ERR_CUDA;
+    }
     // c on the auxiliary stream (after all earlier work of the plan's stream),
     // x and set_points on the plan's stream; eval waits for c
     if (cudaEventRecord(p->aux_ev[0], p->stream) != cudaSuccess ||

@@ -216,6 +216,16 @@ def test_host_path_matches_device_path(prec):
     f_full = torch.empty(len(x), dtype=CD[prec])
     plan2.eval_host(xh, ch, f_full)
     assert torch.equal(f_full, fdev)
+    # back-to-back calls with new coefficients and points: the transform of
+    # the next call (on the plan's second stream) must not overtake the
+    # gather of the previous one
+    for seed in (7, 8):
+        c2, x2 = wl.small_random(M=3000, seed=seed)
+        x2h, c2h = torch.from_numpy(x2).contiguous(), torch.from_numpy(c2).to(CD[prec]).contiguous()
+        f2 = torch.empty(len(x2), dtype=CD[prec])
+        plan2.eval_host(x2h, c2h, f2)
+        plan.set_points(x2h.cuda())
+        assert torch.equal(f2, plan.eval(c2h.cuda()).cpu())
 
 
 @pytest.mark.parametrize("prec,m,tol", [("f64", 6, 1e-12), ("f32", 3, 1e-6)])
