@@ -220,7 +220,7 @@ int nfft3f_eval_grad_stored(nfft3_plan p, float *f, float *grad);
 int nfft3_set_num_points(nfft3_plan p, int64_t M);
 
 /*
- * Deterministic mode (on != 0; FP64 plans with m <= 7): set_points orders
+ * Deterministic mode (on != 0; FP64 plans): set_points orders
  * the points of each tile by original index (a stable radix sort instead of
  * the atomic counting sort), and the adjoint's spread adds its tile boxes to
  * the grid as exact fixed-point sums (two int64 limbs per component,
@@ -228,7 +228,7 @@ int nfft3_set_num_points(nfft3_plan p, int64_t M);
  * that adjoint results are bitwise reproducible from run to run.  Allocates
  * 32 bytes per oversampled grid node plus sort buffers; on == 0 releases
  * them.  Either way the points must be set again (NFFT3_ERR_NO_POINTS until
- * then).  NFFT3_ERR_ARG for mixed plans, m = 8, or the one-thread spread
+ * then).  NFFT3_ERR_ARG for mixed plans, or the one-thread spread
  * (GBNFFT_SPREAD=direct) at adjoint time.  Eval results are bitwise
  * reproducible in both modes.
  */

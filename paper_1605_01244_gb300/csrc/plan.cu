@@ -1120,7 +1120,7 @@ template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
     cudaError_t e;
     if (p->det) {
         // deterministic: the tile spread flushes exact fixed-point sums
-        if (prec != 64 || p->m > 7 || p->spread_direct) return NFFT3_ERR_ARG;
+        if (prec != 64 || p->spread_direct) return NFFT3_ERR_ARG;
         e = cudaMemsetAsync(p->Hq, 0, 4 * sizeof(unsigned long long) * nn, p->stream);
         if (e == cudaSuccess && p->nchunks > 0)
             e = launch_spread_tiles<R>((const C *)f, g, p->m, pv, win_table<R>(p), &p->wtdf, p->pb.chunks,
@@ -1400,7 +1400,7 @@ int nfft3_set_deterministic(nfft3_plan p, int on) {
         return NFFT3_OK;
     }
     if (p->det) return NFFT3_OK;
-    if (p->prec != 64 || p->m > 7) return NFFT3_ERR_ARG;
+    if (p->prec != 64) return NFFT3_ERR_ARG;
     const int64_t nn = (int64_t)p->n[0] * p->n[1] * p->n[2];
     const size_t cnt = stable_sort_count_ints(p->M_cap);
     void *v = nullptr;

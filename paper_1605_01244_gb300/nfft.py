@@ -192,7 +192,7 @@ class Plan:
         return f_host
 
     def set_deterministic(self, on: bool = True):
-        """Bitwise reproducible adjoints (FP64 plans, m <= 7): stable point
+        """Bitwise reproducible adjoints (FP64 plans): stable point
         order and exact fixed-point spread flushes.  set_points must follow."""
         _lib.call("nfft3_set_deterministic", self._h, int(bool(on)))
 

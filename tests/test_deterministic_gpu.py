@@ -64,7 +64,7 @@ def test_bitwise_reproducible_at_benchmark_size():
     assert torch.equal(fd_det, p0.eval(ct))
 
 
-@pytest.mark.parametrize("m", [3, 7])
+@pytest.mark.parametrize("m", [3, 7, 8])
 def test_small_size_against_direct_sum(m):
     from paper_1605_01244_gb300 import Plan
     N = (16, 20, 12)
@@ -76,17 +76,16 @@ def test_small_size_against_direct_sum(m):
     plan.set_points(to_dev(x))
     h = to_np(plan.adjoint(to_dev(f)))
     hd = oracle.adjoint(f, x, N)
-    assert rel_l2(h, hd) <= (5e-12 if m == 7 else 5e-6)
+    assert rel_l2(h, hd) <= (5e-12 if m >= 7 else 5e-6)
     assert torch.equal(plan.adjoint(to_dev(f)), plan.adjoint(to_dev(f)))
 
 
 def test_refused_where_not_supported():
     from paper_1605_01244_gb300 import Plan
-    for kw in ({"m": 3, "precision": "f32"}, {"m": 8, "precision": "f64"}):
-        plan = Plan((8, 8, 8), 10, **kw)
-        with pytest.raises(NFFTError) as e:
-            plan.set_deterministic(True)
-        assert e.value.code == NFFT3_ERR_ARG
+    plan = Plan((8, 8, 8), 10, m=3, precision="f32")
+    with pytest.raises(NFFTError) as e:
+        plan.set_deterministic(True)
+    assert e.value.code == NFFT3_ERR_ARG
     plan = Plan((8, 8, 8), 10, m=4)
     plan.set_deterministic(True)
     plan.set_deterministic(False)
