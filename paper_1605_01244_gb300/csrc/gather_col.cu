@@ -522,30 +522,46 @@ __global__ void __launch_bounds__(256) gather_dense_f32_kernel(const float2 *__r
                 w3[a] = v3;
             }
         }
-        const float2 *base = G + (int64_t)key.x * s1 + (int64_t)key.y * pg.n3 + key.z;
+        // rows are read as 16-byte pairs of values from the even node at or
+        // below the stencil's first one (rows start at even nodes: the padded
+        // row length is even); the third-dimension weights shift by one slot
+        // for an odd first node and the slot past the stencil weighs zero
+        constexpr int W2 = (W + 2) / 2;   // pairs covering W + 1 values
+        const int odd = key.z & 1;
+        float w3s[2 * W2];
+#pragma unroll
+        for (int c = 0; c < 2 * W2; ++c) {
+            const float lo = c < W ? w3[c] : 0.f, hi = c >= 1 && c - 1 < W ? w3[c - 1] : 0.f;
+            w3s[c] = odd ? hi : lo;
+        }
+        const float4 *base = reinterpret_cast<const float4 *>(G + (int64_t)key.x * s1 + (int64_t)key.y * pg.n3 +
+                                                                (key.z - odd));
+        const int64_t rstep = pg.n3 / 2;   // float4 per padded row
         float Tr = 0.f, Ti = 0.f;
 #pragma unroll 1
         for (int a = 0; a < W; ++a) {
             float Sr = 0.f, Si = 0.f;
-            const float2 *row = base;
+            const float4 *row = base;
 #pragma unroll
             for (int bb = 0; bb < W; ++bb) {
                 float Rr = 0.f, Ri = 0.f;
 #pragma unroll
-                for (int c = 0; c < W; ++c) {
-                    const float2 v = __ldg(row + c);
-                    Rr = fmaf(w3[c], v.x, Rr);
-                    Ri = fmaf(w3[c], v.y, Ri);
+                for (int c = 0; c < W2; ++c) {
+                    const float4 v = __ldg(row + c);
+                    Rr = fmaf(w3s[2 * c], v.x, Rr);
+                    Ri = fmaf(w3s[2 * c], v.y, Ri);
+                    Rr = fmaf(w3s[2 * c + 1], v.z, Rr);
+                    Ri = fmaf(w3s[2 * c + 1], v.w, Ri);
                 }
                 Sr = fmaf(w2[bb], Rr, Sr);
                 Si = fmaf(w2[bb], Ri, Si);
-                row += pg.n3;
+                row += rstep;
             }
             Tr = fmaf(w1[0], Sr, Tr);
             Ti = fmaf(w1[0], Si, Ti);
 #pragma unroll
             for (int k = 0; k < W - 1; ++k) w1[k] = w1[k + 1];
-            base += s1;
+            base += s1 / 2;
         }
         if (valid) f[key.w] = make_float2(Tr, Ti);
     }

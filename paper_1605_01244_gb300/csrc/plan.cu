@@ -736,9 +736,17 @@ int ensure_pgrid(nfft3_plan p, int ng) {
     if (p->pgrid && p->pgrid_count >= ng) return NFFT3_OK;
     const int64_t pn = (int64_t)(p->n[0] + 2 * p->m) * (p->n[1] + 2 * p->m) * (p->n[2] + 2 * p->m);
     const size_t elem = p->prec == 64 ? 16 : 8;   // double-float float4 or float2
+    // 64 zero bytes past the last grid: the mixed family's dense gather reads
+    // its rows as 16-byte pairs and may read one value past a row's end
+    // (with weight zero), past the last row into this slack
+    constexpr size_t kSlack = 64;
     void *v = nullptr;
-    const int st = dev_alloc(p, &v, elem * pn * ng);
+    const int st = dev_alloc(p, &v, elem * pn * ng + kSlack);
     if (st != NFFT3_OK) return st;
+    if (cudaMemsetAsync((char *)v + elem * pn * ng, 0, kSlack, p->stream) != cudaSuccess) {
+        dev_free(v);
+        return NFFT3_ERR_CUDA;
+    }
     dev_free(p->pgrid);
     p->pgrid = v;
     p->pgrid_count = ng;
