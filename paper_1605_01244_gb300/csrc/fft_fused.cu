@@ -19,14 +19,24 @@
 #include "internal.cuh"
 
 #ifndef GBNFFT_F32_LINE_ELEMS
-#define GBNFFT_F32_LINE_ELEMS 4096   // FP32 passes: 512-thread blocks (2048 and 8192 measured slower)
+#define GBNFFT_F32_LINE_ELEMS 4096   // FP32 passes: elements per block (2048 and 8192 measured slower at 8 a thread)
+#endif
+#ifndef GBNFFT_F32_EPT
+#define GBNFFT_F32_EPT 8             // FP32 adjoint passes: elements per thread (8: one radix-8 butterfly a pass)
+#endif
+#ifndef GBNFFT_F32_FWD_ELEMS
+#define GBNFFT_F32_FWD_ELEMS 4096    // FP32 forward passes: elements per block
+#endif
+#ifndef GBNFFT_F32_FWD_EPT
+#define GBNFFT_F32_FWD_EPT 16        // FP32 forward passes: elements per thread (16: 1.09 -> 0.96 ms at n = 512^3)
 #endif
 
 namespace gbnfft {
 namespace {
 
 // Line elements per block (lines x length) are A::kElems; a block has
-// kElems / 8 threads (one radix-8 butterfly each per pass).
+// A::kThreads = kElems / kEPT threads, each holding kEPT elements of a line
+// (kEPT / 8 radix-8 butterflies per pass).
 
 // ---- double-float arithmetic (FP64-accurate on the FP32 pipe) ---------------
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -59,6 +69,7 @@ struct ArithDF {
     using S = float4;
     static constexpr int kPadShift = 3;   // 16-byte elements: one pad per 8
     static constexpr int kElems = 4096;   // 512 threads
+    static constexpr int kEPT = 8, kThreads = kElems / kEPT;
     static __device__ __forceinline__ C ld(const S &s) { return C{s.x, s.y, s.z, s.w}; }
     static __device__ __forceinline__ S st(const C &c) { return make_float4(c.rh, c.rl, c.ih, c.il); }
     static __device__ __forceinline__ C zero() { return C{0.f, 0.f, 0.f, 0.f}; }
@@ -126,6 +137,7 @@ struct ArithF32 {
     using S = float2;
     static constexpr int kPadShift = 4;   // 8-byte elements: one pad per 16
     static constexpr int kElems = GBNFFT_F32_LINE_ELEMS;
+    static constexpr int kEPT = GBNFFT_F32_EPT, kThreads = kElems / kEPT;
     static __device__ __forceinline__ C ld(const S &s) { return C{s.x, s.y}; }
     static __device__ __forceinline__ S st(const C &c) { return make_float2(c.r, c.i); }
     static __device__ __forceinline__ C zero() { return C{0.f, 0.f}; }
@@ -147,6 +159,14 @@ struct ArithF32 {
     }
 };
 
+// The forward (series to padded grid) FP32 passes: the same arithmetic with
+// their own block shape (two radix-8 butterflies per thread and pass measured
+// faster there, slower in the adjoint passes)
+struct ArithF32Fwd : ArithF32 {
+    static constexpr int kElems = GBNFFT_F32_FWD_ELEMS;
+    static constexpr int kEPT = GBNFFT_F32_FWD_EPT, kThreads = kElems / kEPT;
+};
+
 // ---- radix-R DFTs with the inverse sign: X_k = sum_a x_a exp(+2 pi i a k / R) --
 template <class A> __device__ __forceinline__ void dft2(typename A::C &x0, typename A::C &x1) {
     const typename A::C s = A::add(x0, x1), d = A::sub(x0, x1);
@@ -164,7 +184,7 @@ __device__ __forceinline__ void dft4(typename A::C &y0, typename A::C &y1, typen
     y3 = A::sub(s1, s3);
 }
 // X_{2k} = DFT4(x_a + x_{a+4}), X_{2k+1} = DFT4((x_a - x_{a+4}) w8^a)
-template <class A> __device__ __forceinline__ void dft8(typename A::C (&x)[8]) {
+template <class A> __device__ __forceinline__ void dft8(typename A::C *x) {
     using C = typename A::C;
     C u[4], v[4];
 #pragma unroll
@@ -195,13 +215,13 @@ template <class A> __device__ __forceinline__ int pidx(int i) { return i + (i >>
 template <class A, int LOGL, int LOGNS, int LOGR>
 __device__ __forceinline__ void stockham_pass(typename A::S *x, const typename A::S *tw, int u, int bh) {
     using C = typename A::C;
-    constexpr int R = 1 << LOGR, PER = 8 / R;
-    constexpr int T = 1 << (LOGL - 3);
+    constexpr int R = 1 << LOGR, PER = A::kEPT / R;
+    constexpr int T = (1 << LOGL) / A::kEPT;
     constexpr int NB = 1 << (LOGL - LOGR);
     constexpr int NS = 1 << LOGNS;
     constexpr int TWS = LOGL - LOGNS - LOGR;   // twiddle index shift
     constexpr int PS = A::kPadShift;
-    C v[8];
+    C v[A::kEPT];
 #pragma unroll
     for (int b = 0; b < PER; ++b) {
         const int j = u + b * T;
@@ -226,14 +246,14 @@ __device__ __forceinline__ void stockham_pass(typename A::S *x, const typename A
             v[b * R + r] = t;
         }
     }
-    if constexpr (R == 8) {
-        dft8<A>(v);
-    } else if constexpr (R == 4) {
-        dft4<A>(v[0], v[1], v[2], v[3]);
-        dft4<A>(v[4], v[5], v[6], v[7]);
-    } else {
 #pragma unroll
-        for (int b = 0; b < 4; ++b) dft2<A>(v[2 * b], v[2 * b + 1]);
+    for (int b = 0; b < PER; ++b) {
+        if constexpr (R == 8)
+            dft8<A>(v + 8 * b);
+        else if constexpr (R == 4)
+            dft4<A>(v[4 * b], v[4 * b + 1], v[4 * b + 2], v[4 * b + 3]);
+        else
+            dft2<A>(v[2 * b], v[2 * b + 1]);
     }
     __syncthreads();
 #pragma unroll
@@ -266,12 +286,12 @@ __device__ __forceinline__ void stockham_from(typename A::S *x, const typename A
 }
 
 // In-place DFT of the block's lines in shared memory: line `line` of length
-// L = 2^LOGL starts at sm + line * LS, T = L/8 threads per line, radix-8
+// L = 2^LOGL starts at sm + line * LS, T = L/kEPT threads per line, radix-8
 // passes then one radix-4 or radix-2 pass for the remaining factor.
 template <class A, int LOGL>
 __device__ __forceinline__ void line_dft(typename A::S *sm, const typename A::S *__restrict__ tw, int LS,
                                          int bh) {
-    constexpr int T = 1 << (LOGL - 3);
+    constexpr int T = (1 << LOGL) / A::kEPT;
     const int line = threadIdx.x / T, u = threadIdx.x - line * T;
     stockham_from<A, LOGL, 0>(sm + line * LS, tw, u, bh);
 }
@@ -326,7 +346,7 @@ struct FusedArgs {
 // Pass 1: rows along l3 for the in-band (k1, k2); input c deconvolved.
 // A[q][i1 N2 + i2][l3].
 template <class A, typename R, int LOGL>
-__global__ void __launch_bounds__(A::kElems / 8) fused_rows_kernel(
+__global__ void __launch_bounds__(A::kThreads) fused_rows_kernel(
     const typename Cplx<R>::T *__restrict__ c, const R *__restrict__ D1, const R *__restrict__ D2,
     const R *__restrict__ D3, const typename A::S *__restrict__ tw3, typename A::S *__restrict__ out,
     FusedArgs a) {
@@ -367,7 +387,7 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_rows_kernel(
 // Pass 2: lines along l2 for each (k1, l3).  in A[q][i1 N2 + i2][l3],
 // out B[q][i1][l2][l3].  A block takes LPB consecutive l3 of one i1.
 template <class A, int LOGL>
-__global__ void __launch_bounds__(A::kElems / 8) fused_cols_kernel(const typename A::S *__restrict__ in,
+__global__ void __launch_bounds__(A::kThreads) fused_cols_kernel(const typename A::S *__restrict__ in,
                                                                   const typename A::S *__restrict__ tw2,
                                                                   typename A::S *__restrict__ out,
                                                                   FusedArgs a) {
@@ -384,7 +404,7 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_cols_kernel(const typenam
     const int nl = a.n3 - l30 < LPB ? a.n3 - l30 : LPB;
     load_twiddles<A>(tws, tw2, L);
     // each thread keeps one line (l3) and walks i2 / l2 with a constant stride
-    constexpr int STEP = (A::kElems / 8) / LPB;
+    constexpr int STEP = A::kThreads / LPB;
     const int line = threadIdx.x & (LPB - 1), r0 = threadIdx.x / LPB;
     S *sl = sm + line * LS;
     if (line < nl) {
@@ -405,7 +425,7 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_cols_kernel(const typenam
 // Pass 3: lines along l1 for each (l2, l3); in B[q][i1][l2][l3]; out the
 // padded grid P[q][p1][p2][p3], p = l + shift + t n in [0, n + 2m).
 template <class A, int LOGL>
-__global__ void __launch_bounds__(A::kElems / 8) fused_out_kernel(const typename A::S *__restrict__ in,
+__global__ void __launch_bounds__(A::kThreads) fused_out_kernel(const typename A::S *__restrict__ in,
                                                                  const typename A::S *__restrict__ tw1,
                                                                  typename A::S *__restrict__ P,
                                                                  FusedArgs a) {
@@ -422,7 +442,7 @@ __global__ void __launch_bounds__(A::kElems / 8) fused_out_kernel(const typename
     const int nl = a.n3 - l30 < LPB ? a.n3 - l30 : LPB;
     load_twiddles<A>(tws, tw1, L);
     // each thread keeps one line (l3) and walks i1 / l1 with a constant stride
-    constexpr int STEP = (A::kElems / 8) / LPB;
+    constexpr int STEP = A::kThreads / LPB;
     const int line = threadIdx.x & (LPB - 1), r0 = threadIdx.x / LPB;
     S *sl = sm + line * LS;
     if (line < nl) {
@@ -490,7 +510,7 @@ template <> struct AdjOut<float> {
 // Pass 1: along l1 for each (l2, l3); in H[l1][l2][l3] (family type),
 // out A[i1][l2][l3] (N1 n2 n3).  A block takes LPB consecutive l3 of one l2.
 template <class A, typename R, int LOGL>
-__global__ void __launch_bounds__(A::kElems / 8) adj_first_kernel(const typename Cplx<R>::T *__restrict__ H,
+__global__ void __launch_bounds__(A::kThreads) adj_first_kernel(const typename Cplx<R>::T *__restrict__ H,
                                                                  const typename A::S *__restrict__ tw1,
                                                                  typename A::S *__restrict__ out, FusedArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -504,7 +524,7 @@ __global__ void __launch_bounds__(A::kElems / 8) adj_first_kernel(const typename
     const int l30 = (blockIdx.x - l2 * nblk3) * LPB;
     const int nl = a.n3 - l30 < LPB ? a.n3 - l30 : LPB;
     load_twiddles<A>(tws, tw1, L);
-    constexpr int STEP = (A::kElems / 8) / LPB;
+    constexpr int STEP = A::kThreads / LPB;
     const int line = threadIdx.x & (LPB - 1), r0 = threadIdx.x / LPB;
     S *sl = sm + line * LS;
     const int64_t plane = (int64_t)a.n2 * a.n3;
@@ -523,7 +543,7 @@ __global__ void __launch_bounds__(A::kElems / 8) adj_first_kernel(const typename
 // Pass 2: along l2 for each (i1, l3); in A[i1][l2][l3], out B[i1][i2][l3]
 // (N1 N2 n3).  A block takes LPB consecutive l3 of one i1.
 template <class A, int LOGL>
-__global__ void __launch_bounds__(A::kElems / 8) adj_mid_kernel(const typename A::S *__restrict__ in,
+__global__ void __launch_bounds__(A::kThreads) adj_mid_kernel(const typename A::S *__restrict__ in,
                                                                const typename A::S *__restrict__ tw2,
                                                                typename A::S *__restrict__ out, FusedArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -537,7 +557,7 @@ __global__ void __launch_bounds__(A::kElems / 8) adj_mid_kernel(const typename A
     const int l30 = (blockIdx.x - i1 * nblk3) * LPB;
     const int nl = a.n3 - l30 < LPB ? a.n3 - l30 : LPB;
     load_twiddles<A>(tws, tw2, L);
-    constexpr int STEP = (A::kElems / 8) / LPB;
+    constexpr int STEP = A::kThreads / LPB;
     const int line = threadIdx.x & (LPB - 1), r0 = threadIdx.x / LPB;
     S *sl = sm + line * LS;
     if (line < nl) {
@@ -556,7 +576,7 @@ __global__ void __launch_bounds__(A::kElems / 8) adj_mid_kernel(const typename A
 // Pass 3: along l3 for each (i1, i2); in B[i1][i2][l3], out the deconvolved
 // band c[i1][i2][i3] (family type, conjugated back, range scaled back).
 template <class A, typename R, int LOGL>
-__global__ void __launch_bounds__(A::kElems / 8) adj_last_kernel(const typename A::S *__restrict__ in,
+__global__ void __launch_bounds__(A::kThreads) adj_last_kernel(const typename A::S *__restrict__ in,
                                                                 const R *__restrict__ D1, const R *__restrict__ D2,
                                                                 const R *__restrict__ D3,
                                                                 const typename A::S *__restrict__ tw3,
@@ -611,7 +631,7 @@ cudaError_t launch_rows(const typename Cplx<R>::T *c, const R *D1, const R *D2, 
     if (e != cudaSuccess) return e;
     const int64_t rows = (int64_t)a.N1 * a.N2, lpb = A::kElems >> LOGL;
     dim3 g((unsigned)((rows + lpb - 1) / lpb), (unsigned)a.ng);
-    fused_rows_kernel<A, R, LOGL><<<g, A::kElems / 8, sm, st>>>(c, D1, D2, D3, tw, out, a);
+    fused_rows_kernel<A, R, LOGL><<<g, A::kThreads, sm, st>>>(c, D1, D2, D3, tw, out, a);
     return cudaGetLastError();
 }
 
@@ -624,7 +644,7 @@ cudaError_t launch_cols(const typename A::S *in, const typename A::S *tw, typena
     if (e != cudaSuccess) return e;
     const int lpb = A::kElems >> LOGL;
     dim3 g((unsigned)(a.N1 * ((a.n3 + lpb - 1) / lpb)), (unsigned)a.ng);
-    fused_cols_kernel<A, LOGL><<<g, A::kElems / 8, sm, st>>>(in, tw, out, a);
+    fused_cols_kernel<A, LOGL><<<g, A::kThreads, sm, st>>>(in, tw, out, a);
     return cudaGetLastError();
 }
 
@@ -637,7 +657,7 @@ cudaError_t launch_out(const typename A::S *in, const typename A::S *tw, typenam
     if (e != cudaSuccess) return e;
     const int lpb = A::kElems >> LOGL;
     dim3 g((unsigned)(a.n2 * ((a.n3 + lpb - 1) / lpb)), (unsigned)a.ng);
-    fused_out_kernel<A, LOGL><<<g, A::kElems / 8, sm, st>>>(in, tw, P, a);
+    fused_out_kernel<A, LOGL><<<g, A::kThreads, sm, st>>>(in, tw, P, a);
     return cudaGetLastError();
 }
 
@@ -698,7 +718,7 @@ cudaError_t launch_adj_first(const typename Cplx<R>::T *H, const typename A::S *
                                          (int)sm);
     if (e != cudaSuccess) return e;
     const int lpb = A::kElems >> LOGL;
-    adj_first_kernel<A, R, LOGL><<<(unsigned)(a.n2 * ((a.n3 + lpb - 1) / lpb)), A::kElems / 8, sm, st>>>(H, tw, out,
+    adj_first_kernel<A, R, LOGL><<<(unsigned)(a.n2 * ((a.n3 + lpb - 1) / lpb)), A::kThreads, sm, st>>>(H, tw, out,
                                                                                                          a);
     return cudaGetLastError();
 }
@@ -711,7 +731,7 @@ cudaError_t launch_adj_mid(const typename A::S *in, const typename A::S *tw, typ
         cudaFuncSetAttribute(adj_mid_kernel<A, LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int lpb = A::kElems >> LOGL;
-    adj_mid_kernel<A, LOGL><<<(unsigned)(a.N1 * ((a.n3 + lpb - 1) / lpb)), A::kElems / 8, sm, st>>>(in, tw, out, a);
+    adj_mid_kernel<A, LOGL><<<(unsigned)(a.N1 * ((a.n3 + lpb - 1) / lpb)), A::kThreads, sm, st>>>(in, tw, out, a);
     return cudaGetLastError();
 }
 
@@ -723,7 +743,7 @@ cudaError_t launch_adj_last(const typename A::S *in, const R *D1, const R *D2, c
                                          (int)sm);
     if (e != cudaSuccess) return e;
     const int64_t rows = (int64_t)a.N1 * a.N2, lpb = A::kElems >> LOGL;
-    adj_last_kernel<A, R, LOGL><<<(unsigned)((rows + lpb - 1) / lpb), A::kElems / 8, sm, st>>>(in, D1, D2, D3, tw,
+    adj_last_kernel<A, R, LOGL><<<(unsigned)((rows + lpb - 1) / lpb), A::kThreads, sm, st>>>(in, D1, D2, D3, tw,
                                                                                               c, a);
     return cudaGetLastError();
 }
@@ -811,7 +831,7 @@ cudaError_t launch_fused_series(const typename Cplx<R>::T *c, const int N[3], co
     if constexpr (sizeof(R) == 8)
         return run_fused<ArithDF, R>(c, D1, D2, D3, tw, scratch, P, a, st);
     else
-        return run_fused<ArithF32, R>(c, D1, D2, D3, tw, scratch, P, a, st);
+        return run_fused<ArithF32Fwd, R>(c, D1, D2, D3, tw, scratch, P, a, st);
 }
 
 template cudaError_t launch_fused_series<double>(const double2 *, const int[3], const int[3],
