@@ -18,6 +18,13 @@
 #include "fastdiv.cuh"
 #include "internal.cuh"
 
+#ifndef GBNFFT_DF_LINE_ELEMS
+#define GBNFFT_DF_LINE_ELEMS 2048    // double-float passes: elements per block (4096: 3.27 / 3.87 ms
+                                     // forward / adjoint at n = 512^3, 2048: 3.09 / 3.37 ms)
+#endif
+#ifndef GBNFFT_DF_EPT
+#define GBNFFT_DF_EPT 8              // double-float passes: elements per thread
+#endif
 #ifndef GBNFFT_F32_LINE_ELEMS
 #define GBNFFT_F32_LINE_ELEMS 4096   // FP32 passes: elements per block (2048 and 8192 measured slower at 8 a thread)
 #endif
@@ -34,7 +41,8 @@
 namespace gbnfft {
 namespace {
 
-// Line elements per block (lines x length) are A::kElems; a block has
+// Line elements per block (lines x length) are A::kElems (at least the
+// longest line, 2^11); a block has
 // A::kThreads = kElems / kEPT threads, each holding kEPT elements of a line
 // (kEPT / 8 radix-8 butterflies per pass).
 
@@ -68,8 +76,8 @@ struct ArithDF {
     };
     using S = float4;
     static constexpr int kPadShift = 3;   // 16-byte elements: one pad per 8
-    static constexpr int kElems = 4096;   // 512 threads
-    static constexpr int kEPT = 8, kThreads = kElems / kEPT;
+    static constexpr int kElems = GBNFFT_DF_LINE_ELEMS;
+    static constexpr int kEPT = GBNFFT_DF_EPT, kThreads = kElems / kEPT;
     static __device__ __forceinline__ C ld(const S &s) { return C{s.x, s.y, s.z, s.w}; }
     static __device__ __forceinline__ S st(const C &c) { return make_float4(c.rh, c.rl, c.ih, c.il); }
     static __device__ __forceinline__ C zero() { return C{0.f, 0.f, 0.f, 0.f}; }
