@@ -15,7 +15,13 @@ __device__ __forceinline__ int centre_node(int l0, int m, int n) {
 
 // Points per thread per loop trip in the set_points passes: their loads are
 // issued together, so each thread keeps several HBM requests in flight.
-constexpr int kPtsILP = 4;
+#ifndef GBNFFT_PTS_ILP
+#define GBNFFT_PTS_ILP 4
+#endif
+#ifndef GBNFFT_PTS_BLOCKS_PER_SM
+#define GBNFFT_PTS_BLOCKS_PER_SM 8
+#endif
+constexpr int kPtsILP = GBNFFT_PTS_ILP;
 
 // Pass 1: reduce every point once (FP64 results, integer pipe for n = 2^L),
 // store the result unsorted as one aligned record per point (stencil origin,
@@ -355,7 +361,7 @@ int point_blocks(int64_t M) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int64_t want = ceil_div(M, 256);
-    int64_t cap = (int64_t)sms * 8;
+    int64_t cap = (int64_t)sms * GBNFFT_PTS_BLOCKS_PER_SM;
     return (int)(want < 1 ? 1 : (want < cap ? want : cap));
 }
 
