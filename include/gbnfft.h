@@ -242,7 +242,10 @@ int nfft3f_adjoint(nfft3_plan p, const float *f, float *c_out);
  * Host-buffer variants: copy x_host (M*3 doubles) and c_host (N^3 complex)
  * to plan-owned device buffers, set the points, evaluate, copy f back into
  * f_host (M complex) and synchronise.  Pinned host memory gives full copy
- * bandwidth; pageable memory works but is slower.
+ * bandwidth; pageable memory works but is slower.  With the default gather
+ * and the fused transform, c is copied first and transformed on a second
+ * stream owned by the plan while x is copied and sorted on the plan's
+ * stream; the gather waits for both.
  */
 int nfft3d_eval_host(nfft3_plan p, const double *x_host, const double *c_host, double *f_host);
 int nfft3f_eval_host(nfft3_plan p, const double *x_host, const float *c_host, float *f_host);
