@@ -73,6 +73,25 @@ def test_same_algorithm_as_cpu_nfft(N, M, m):
     assert rel_l2(f32, nfft_cpu.forward(c, x, plan32.n, m)) <= 2e-6
 
 
+@pytest.mark.parametrize("mode", ["df", "fp64", "full"])
+@pytest.mark.parametrize("m", [4, 6, 8])
+def test_value_gather_weight_tables(mode, m, monkeypatch):
+    """The FP64 value gather's tap weights: half-interval tables (degree 11 in
+    u = 4s - 3, tap 2m - a reflected for s < 1/2) in double-float (default)
+    or FP64, and the whole-interval FP64 table, each against the CPU NFFT
+    restatement; points at s = 0, 1/2 and just below 1 included."""
+    monkeypatch.setenv("GBNFFT_SLOT_WEIGHTS", mode)
+    N = (16, 24, 20)
+    n = (32, 48, 40)
+    c = wl.gaussian_coeffs(N, 1e9, seed=m)
+    edge = np.array([[0.0, 0.0, 0.0], [1 / 64, 1 / 96, 1 / 80], [-0.5, 0.5 - 1e-16, 1 / 64 - 1e-13],
+                     [0.5 / 32, 0.5 / 48, 0.5 / 40]])
+    x = np.concatenate([wl.uniform_points(600, seed=m + 1), edge])
+    f, plan = gpu_eval(c, x, m=m)
+    assert plan.n == n
+    assert max_rel(f, nfft_cpu.forward(c, x, n, m)) <= 1e-13
+
+
 def test_non_power_of_two_oversampling():
     N = (10, 14, 18)
     c = wl.gaussian_coeffs(N, 1e9, seed=3)
