@@ -243,9 +243,10 @@ int nfft3f_adjoint(nfft3_plan p, const float *f, float *c_out);
  * to plan-owned device buffers, set the points, evaluate, copy f back into
  * f_host (M complex) and synchronise.  Pinned host memory gives full copy
  * bandwidth; pageable memory works but is slower.  With the default gather
- * and the fused transform, c is copied first and transformed on a second
- * stream owned by the plan while x is copied and sorted on the plan's
- * stream; the gather waits for both.
+ * and the fused transform, c and then x (in two halves) are copied on a copy
+ * stream owned by the plan, c is transformed on a second plan-owned stream
+ * as soon as it has arrived, and set_points starts on the first half of x
+ * on the plan's stream; the gather waits for both.
  */
 int nfft3d_eval_host(nfft3_plan p, const double *x_host, const double *c_host, double *f_host);
 int nfft3f_eval_host(nfft3_plan p, const double *x_host, const float *c_host, float *f_host);

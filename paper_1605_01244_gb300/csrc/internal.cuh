@@ -394,10 +394,13 @@ int stable_sort_launches(const PointsBuild &pb);
 
 // stable: nullptr for the default order (by key; the order within a key
 // follows the count pass's atomics), else points within a key keep their
-// original order.
+// original order.  split, second: with 0 < split < M and an event, the
+// first pass takes points [0, split) at once and points [split, M) after
+// `second` (x's second part arriving by a copy that records it).
 template <typename R>
 cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R *s2, R *s3,
-                          cudaStream_t st, const StableSort *stable);
+                          cudaStream_t st, const StableSort *stable, int64_t split = 0,
+                          cudaEvent_t second = nullptr);
 
 // Chunk list from tile_start (after launch_points); the number of chunks is
 // left in chunk_start[ntile].

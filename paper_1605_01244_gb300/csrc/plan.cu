@@ -390,9 +390,9 @@ void release(nfft3_plan p) {
     dev_free(p->c_dev);
     dev_free(p->f_dev);
     if (p->aux_stream) {
-        cudaEventDestroy(p->aux_ev[0]);
-        cudaEventDestroy(p->aux_ev[1]);
+        for (int i = 0; i < 5; ++i) cudaEventDestroy(p->aux_ev[i]);
         cudaStreamDestroy(p->aux_stream);
+        cudaStreamDestroy(p->copy_stream);
     }
     if (p->fft1) cufftDestroy(p->fft1);
     if (p->have_fft4) cufftDestroy(p->fft4);
@@ -683,7 +683,7 @@ int exec_grid_fft(nfft3_plan p, void *data, int prec, int direction, int ng) {
     return NFFT3_OK;
 }
 
-int set_points_impl(nfft3_plan p, const double *x, int prec) {
+int set_points_impl(nfft3_plan p, const double *x, int prec, int64_t first_part = 0, cudaEvent_t second = nullptr) {
     if (!p || p->prec != prec) return NFFT3_ERR_ARG;
     if (!x && p->M > 0) return NFFT3_ERR_ARG;
     p->points_ok = 0;
@@ -693,12 +693,13 @@ int set_points_impl(nfft3_plan p, const double *x, int prec) {
     const StableSort *stable = p->det ? &p->ss : nullptr;
     if (prec == 64)
         e = launch_points<double>(x, p->pb, p->key, (double *)p->s[0], (double *)p->s[1],
-                                  (double *)p->s[2], p->stream, stable);
+                                  (double *)p->s[2], p->stream, stable, first_part, second);
     else
         e = launch_points<float>(x, p->pb, p->key, (float *)p->s[0], (float *)p->s[1],
-                                 (float *)p->s[2], p->stream, stable);
+                                 (float *)p->s[2], p->stream, stable, first_part, second);
     if (e != cudaSuccess) return NFFT3_ERR_CUDA;
     p->launches += (p->M > 0 ? 4 : 1) + scan_launches(p->pb.nkey + 1);
+    if (second && first_part > 0 && first_part < p->M) p->launches += 1;   // the first pass in two parts
     if (stable) p->launches += stable_sort_launches(p->pb);
     if (launch_chunks(p->pb, p->stream) != cudaSuccess) return NFFT3_ERR_CUDA;
     p->launches += 2 + scan_launches(p->pb.ntile + 1);
@@ -1184,13 +1185,19 @@ template <typename R> int eval_host_impl(nfft3_plan p, const double *x_host, con
         if (st == NFFT3_OK) st = dev_alloc(p, &p->c_dev, 2 * sizeof(R) * NN);
         if (st == NFFT3_OK) st = dev_alloc(p, &p->f_dev, 2 * sizeof(R) * (p->M_cap + 1));
         if (st == NFFT3_OK && !p->aux_stream) {
-            if (cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            bool ok = cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking) == cudaSuccess;
+            if (!ok) p->aux_stream = nullptr;
+            const bool cs = ok && cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+            int nev = 0;
+            if (cs)
+                while (nev < 5 && cudaEventCreateWithFlags(&p->aux_ev[nev], cudaEventDisableTiming) == cudaSuccess)
+                    ++nev;
+            if (!cs || nev < 5) {
+                for (int i = 0; i < nev; ++i) cudaEventDestroy(p->aux_ev[i]);
+                if (cs) cudaStreamDestroy(p->copy_stream);
+                if (ok) cudaStreamDestroy(p->aux_stream);
                 p->aux_stream = nullptr;
-                st = NFFT3_ERR_CUDA;
-            } else if (cudaEventCreateWithFlags(&p->aux_ev[0], cudaEventDisableTiming) != cudaSuccess ||
-                       cudaEventCreateWithFlags(&p->aux_ev[1], cudaEventDisableTiming) != cudaSuccess) {
-                cudaStreamDestroy(p->aux_stream);
-                p->aux_stream = nullptr;
+                p->copy_stream = nullptr;
                 st = NFFT3_ERR_CUDA;
             }
         }
@@ -1204,30 +1211,46 @@ template <typename R> int eval_host_impl(nfft3_plan p, const double *x_host, con
         }
     }
     if (p->fused && p->gather_mode == 3 && p->M > 0) {
-        // c first, then x, on the plan's stream (each copy gets the whole
-        // link); the transform of c runs on the auxiliary stream while x
-        // arrives and set_points sorts it; the gather waits for both
-        if (cudaMemcpyAsync(p->c_dev, c_host, 2 * sizeof(R) * NN, cudaMemcpyHostToDevice, p->stream) !=
+        // The copy stream brings c, then x in two parts (each copy gets the
+        // whole link); the transform of c runs on the auxiliary stream once
+        // c has arrived; set_points' first pass starts on the first part of x
+        // and takes the second part when it has arrived; the gather waits for
+        // the transform.  Every stream starts after the plan's earlier work.
+        const int64_t half = p->M / 2;
+        auto drain = [p]() {
+            cudaStreamSynchronize(p->copy_stream);
+            cudaStreamSynchronize(p->aux_stream);
+        };
+        if (cudaEventRecord(p->aux_ev[0], p->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(p->copy_stream, p->aux_ev[0], 0) != cudaSuccess ||
+            cudaMemcpyAsync(p->c_dev, c_host, 2 * sizeof(R) * NN, cudaMemcpyHostToDevice, p->copy_stream) !=
                 cudaSuccess ||
-            cudaEventRecord(p->aux_ev[0], p->stream) != cudaSuccess ||
-            cudaMemcpyAsync(p->x_dev, x_host, sizeof(double) * 3 * p->M, cudaMemcpyHostToDevice, p->stream) !=
-                cudaSuccess ||
-            cudaStreamWaitEvent(p->aux_stream, p->aux_ev[0], 0) != cudaSuccess)
+            cudaEventRecord(p->aux_ev[1], p->copy_stream) != cudaSuccess ||
+            cudaMemcpyAsync(p->x_dev, x_host, sizeof(double) * 3 * half, cudaMemcpyHostToDevice,
+                            p->copy_stream) != cudaSuccess ||
+            cudaEventRecord(p->aux_ev[2], p->copy_stream) != cudaSuccess ||
+            cudaMemcpyAsync(p->x_dev + 3 * half, x_host + 3 * half, sizeof(double) * 3 * (p->M - half),
+                            cudaMemcpyHostToDevice, p->copy_stream) != cudaSuccess ||
+            cudaEventRecord(p->aux_ev[3], p->copy_stream) != cudaSuccess ||
+            cudaStreamWaitEvent(p->aux_stream, p->aux_ev[1], 0) != cudaSuccess ||
+            cudaStreamWaitEvent(p->stream, p->aux_ev[2], 0) != cudaSuccess) {
+            drain();
             return NFFT3_ERR_CUDA;
+        }
         cudaStream_t own = p->stream;
         p->stream = p->aux_stream;   // the transform's launches go to the auxiliary stream
         st = precompute_impl<R>(p, (const R *)p->c_dev, 0);
         p->stream = own;
-        if (st != NFFT3_OK || cudaEventRecord(p->aux_ev[1], p->aux_stream) != cudaSuccess) {
-            cudaStreamSynchronize(p->aux_stream);
+        if (st != NFFT3_OK || cudaEventRecord(p->aux_ev[4], p->aux_stream) != cudaSuccess) {
+            drain();
             return st != NFFT3_OK ? st : NFFT3_ERR_CUDA;
         }
-        st = set_points_impl(p, p->x_dev, prec);
+        st = set_points_impl(p, p->x_dev, prec, half, p->aux_ev[3]);
         if (st != NFFT3_OK) {
-            cudaStreamSynchronize(p->aux_stream);
+            drain();
             return st;
         }
-        if (cudaStreamWaitEvent(p->stream, p->aux_ev[1], 0) != cudaSuccess) return NFFT3_ERR_CUDA;
+        if (cudaStreamWaitEvent(p->stream, p->aux_ev[4], 0) != cudaSuccess) return NFFT3_ERR_CUDA;
         st = eval_stored_impl<R>(p, (R *)p->f_dev, nullptr, 1);
         if (st < 0) return st;
         if (cudaMemcpyAsync(f_host, p->f_dev, 2 * sizeof(R) * p->M, cudaMemcpyDeviceToHost, p->stream) !=

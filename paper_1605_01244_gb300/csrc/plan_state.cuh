@@ -66,13 +66,15 @@ struct nfft3_plan_s {
     int4 *key;
     void *s[3];
     gbnfft::PointsBuild pb;
-    // host-buffer staging (allocated on first _host call); the coefficient
-    // copy runs on aux_stream, overlapping the copy of x and set_points
+    // host-buffer staging (allocated on first _host call): eval_host copies
+    // on copy_stream and, with the fused transform, transforms c on
+    // aux_stream while x arrives and set_points runs on the plan's stream
     double *x_dev;
     void *c_dev;
     void *f_dev;
     cudaStream_t aux_stream;
-    cudaEvent_t aux_ev[2];
+    cudaStream_t copy_stream;   // host-buffer copies of eval_host
+    cudaEvent_t aux_ev[5];
     // stage timing (CUDA events on the plan's stream), enabled by nfft3_timing_enable
     int timing;
     int nrec;

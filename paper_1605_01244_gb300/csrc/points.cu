@@ -29,17 +29,19 @@ constexpr int kPtsILP = GBNFFT_PTS_ILP;
 // points of the key before it.
 template <typename R>
 __global__ void __launch_bounds__(256) points_count_kernel(const double *__restrict__ x, PointsBuild pb,
-                                                           PointRec<R> *__restrict__ rec) {
+                                                           PointRec<R> *__restrict__ rec, int64_t j_begin,
+                                                           int64_t j_end) {
     const CoordParams cp1 = coord_params(pb.g.n1, pb.m), cp2 = coord_params(pb.g.n2, pb.m),
                       cp3 = coord_params(pb.g.n3, pb.m);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j0 < pb.M; j0 += kPtsILP * stride) {
+    for (int64_t j0 = j_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j0 < j_end;
+         j0 += kPtsILP * stride) {
         double xs[kPtsILP][3];
 #pragma unroll
         for (int q = 0; q < kPtsILP; ++q) {
             const int64_t j = j0 + q * stride;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) xs[q][d] = j < pb.M ? __ldcs(x + 3 * j + d) : 0.0;
+            for (int d = 0; d < 3; ++d) xs[q][d] = j < j_end ? __ldcs(x + 3 * j + d) : 0.0;
         }
         // phase 1: reduce, store the records, and issue one atomic per
         // distinct key in the warp (clustered points share keys) for all
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(256) points_count_kernel(const double *__restr
             peers[q] = 0;
             base[q] = 0;
             k[q] = 0;
-            if (j >= pb.M) continue;
+            if (j >= j_end) continue;
             const Reduced r1 = reduce_coord(xs[q][0], cp1, pb.status);
             const Reduced r2 = reduce_coord(xs[q][1], cp2, pb.status);
             const Reduced r3 = reduce_coord(xs[q][2], cp3, pb.status);
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(256) points_count_kernel(const double *__restr
 #pragma unroll
         for (int q = 0; q < kPtsILP; ++q) {
             const int64_t j = j0 + q * stride;
-            if (j >= pb.M) continue;
+            if (j >= j_end) continue;
             const int b = __shfl_sync(peers[q], base[q], __ffs(peers[q]) - 1);
             pb.key_rank[j] = make_int2(k[q], b + __popc(peers[q] & ((1u << lane) - 1u)));
         }
@@ -436,7 +438,7 @@ cudaError_t stable_perm(PointsBuild &pb, int *bufA, int *bufB, const StableSort 
 
 template <typename R>
 cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R *s2, R *s3,
-                          cudaStream_t st, const StableSort *stable) {
+                          cudaStream_t st, const StableSort *stable, int64_t split, cudaEvent_t second) {
     // key_count has nkey + 1 entries; the extra zero makes key_start[nkey] = M.
     cudaError_t e = cudaMemsetAsync(pb.key_count, 0, sizeof(int) * (pb.nkey + 1), st);
     if (e != cudaSuccess) return e;
@@ -445,8 +447,16 @@ cudaError_t launch_points(const double *x, PointsBuild &pb, int4 *key, R *s1, R 
     PointRec<R> *rec = (PointRec<R> *)pb.scratch;
     int *perm = (int *)((char *)pb.scratch + sizeof(PointRec<R>) * (pb.M_cap + 1));
     if (pb.M > 0) {
-        points_count_kernel<R><<<point_blocks(pb.M), 256, 0, st>>>(x, pb, rec);
+        // points [split, M) only after `second` (their coordinates may still
+        // be arriving); ranks come from the same atomic counts either way
+        const int64_t j1 = second && split > 0 && split < pb.M ? split : pb.M;
+        points_count_kernel<R><<<point_blocks(j1), 256, 0, st>>>(x, pb, rec, 0, j1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (j1 < pb.M) {
+            if ((e = cudaStreamWaitEvent(st, second, 0)) != cudaSuccess) return e;
+            points_count_kernel<R><<<point_blocks(pb.M - j1), 256, 0, st>>>(x, pb, rec, j1, pb.M);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
     }
     e = exclusive_scan(pb.key_count, pb.key_start, pb.nkey + 1, pb.scan_tmp, st);
     if (e != cudaSuccess) return e;
@@ -504,9 +514,10 @@ cudaError_t launch_split_lists(PointsBuild &pb, cudaStream_t st) {
 int split_list_launches(const PointsBuild &pb) { return 2 + 2 * scan_launches(pb.ntile + 1); }
 
 template cudaError_t launch_points<double>(const double *, PointsBuild &, int4 *, double *,
-                                           double *, double *, cudaStream_t, const StableSort *);
+                                           double *, double *, cudaStream_t, const StableSort *, int64_t,
+                                           cudaEvent_t);
 template cudaError_t launch_points<float>(const double *, PointsBuild &, int4 *, float *, float *,
-                                          float *, cudaStream_t, const StableSort *);
+                                          float *, cudaStream_t, const StableSort *, int64_t, cudaEvent_t);
 
 }  // namespace gbnfft
 
