@@ -239,6 +239,20 @@ int nfft3d_adjoint(nfft3_plan p, const double *f, double *c_out);
 int nfft3f_adjoint(nfft3_plan p, const float *f, float *c_out);
 
 /*
+ * nfft3*_set_points(x) followed by nfft3*_eval(c, f), in one call, with the
+ * same arguments, results and errors as those two calls (device pointers;
+ * x is read, c read, f written).  With the default gather and the fused
+ * transform (power-of-two oversampled sizes) the transform of c runs on a
+ * second stream owned by the plan while set_points sorts x on the plan's
+ * stream -- the two share no data -- and the gather waits for both; in
+ * other configurations the two calls run in sequence.  Returns after
+ * set_points' checks, like nfft3*_set_points; the evaluation completes
+ * asynchronously on the plan's stream.
+ */
+int nfft3d_eval_points(nfft3_plan p, const double *x, const double *c, double *f);
+int nfft3f_eval_points(nfft3_plan p, const double *x, const float *c, float *f);
+
+/*
  * Host-buffer variants: copy x_host (M*3 doubles) and c_host (N^3 complex)
  * to plan-owned device buffers, set the points, evaluate, copy f back into
  * f_host (M complex) and synchronise.  Pinned host memory gives full copy

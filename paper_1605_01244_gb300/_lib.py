@@ -52,6 +52,8 @@ SIGNATURES = {
     "nfft3f_eval_stored": (_I, [_P, _P]),
     "nfft3d_eval_grad_stored": (_I, [_P, _P, _P]),
     "nfft3f_eval_grad_stored": (_I, [_P, _P, _P]),
+    "nfft3d_eval_points": (_I, [_P, _P, _P, _P]),
+    "nfft3f_eval_points": (_I, [_P, _P, _P, _P]),
     "nfft3d_chain_x": (_I, [_P, _P, _P, _P]),
     "nfft3f_chain_x": (_I, [_P, _P, _P, _P]),
     "nfft3d_eval_grad_window": (_I, [_P, _P, _P, _P]),

@@ -1172,6 +1172,62 @@ template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
     return finish(p, cuda_status(e));
 }
 
+// The plan's second and copy streams and their events (created on first use).
+int ensure_aux(nfft3_plan p) {
+    if (p->aux_stream) return NFFT3_OK;
+    bool ok = cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) p->aux_stream = nullptr;
+    const bool cs = ok && cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+    int nev = 0;
+    if (cs)
+        while (nev < 5 && cudaEventCreateWithFlags(&p->aux_ev[nev], cudaEventDisableTiming) == cudaSuccess) ++nev;
+    if (!cs || nev < 5) {
+        for (int i = 0; i < nev; ++i) cudaEventDestroy(p->aux_ev[i]);
+        if (cs) cudaStreamDestroy(p->copy_stream);
+        if (ok) cudaStreamDestroy(p->aux_stream);
+        p->aux_stream = nullptr;
+        p->copy_stream = nullptr;
+        return NFFT3_ERR_CUDA;
+    }
+    return NFFT3_OK;
+}
+
+// set_points(x) and eval(c) in one call: with the default gather and the
+// fused transform, the transform of c runs on the plan's second stream while
+// set_points sorts x on the plan's stream (they share no data), and the
+// gather waits for both; otherwise the two calls in sequence.
+template <typename R> int eval_points_impl(nfft3_plan p, const double *x, const R *c, R *f) {
+    constexpr int prec = sizeof(R) == 8 ? 64 : 32;
+    if (!p || p->prec != prec) return NFFT3_ERR_ARG;
+    if (p->M > 0 && (!x || !c || !f)) return NFFT3_ERR_ARG;
+    if (!(p->fused && p->gather_mode == 3 && p->M > 0)) {
+        const int st = set_points_impl(p, x, prec);
+        return st != NFFT3_OK ? st : eval_impl<R>(p, c, f);
+    }
+    int st = ensure_aux(p);
+    if (st != NFFT3_OK) return st;
+    // the second stream starts after the plan's earlier work (a previous
+    // gather may still read the padded grid)
+    if (cudaEventRecord(p->aux_ev[0], p->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(p->aux_stream, p->aux_ev[0], 0) != cudaSuccess)
+        return NFFT3_ERR_CUDA;
+    cudaStream_t own = p->stream;
+    p->stream = p->aux_stream;   // the transform's launches go to the second stream
+    st = precompute_impl<R>(p, c, 0);
+    p->stream = own;
+    if (st != NFFT3_OK || cudaEventRecord(p->aux_ev[4], p->aux_stream) != cudaSuccess) {
+        cudaStreamSynchronize(p->aux_stream);
+        return st != NFFT3_OK ? st : NFFT3_ERR_CUDA;
+    }
+    st = set_points_impl(p, x, prec);
+    if (st != NFFT3_OK) {
+        cudaStreamSynchronize(p->aux_stream);
+        return st;
+    }
+    if (cudaStreamWaitEvent(p->stream, p->aux_ev[4], 0) != cudaSuccess) return NFFT3_ERR_CUDA;
+    return eval_stored_impl<R>(p, f, nullptr, 1);
+}
+
 template <typename R> int eval_host_impl(nfft3_plan p, const double *x_host, const R *c_host, R *f_host) {
     constexpr int prec = sizeof(R) == 8 ? 64 : 32;
     if (!p || p->prec != prec) return NFFT3_ERR_ARG;
@@ -1184,23 +1240,7 @@ template <typename R> int eval_host_impl(nfft3_plan p, const double *x_host, con
         p->x_dev = (double *)v;
         if (st == NFFT3_OK) st = dev_alloc(p, &p->c_dev, 2 * sizeof(R) * NN);
         if (st == NFFT3_OK) st = dev_alloc(p, &p->f_dev, 2 * sizeof(R) * (p->M_cap + 1));
-        if (st == NFFT3_OK && !p->aux_stream) {
-            bool ok = cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking) == cudaSuccess;
-            if (!ok) p->aux_stream = nullptr;
-            const bool cs = ok && cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
-            int nev = 0;
-            if (cs)
-                while (nev < 5 && cudaEventCreateWithFlags(&p->aux_ev[nev], cudaEventDisableTiming) == cudaSuccess)
-                    ++nev;
-            if (!cs || nev < 5) {
-                for (int i = 0; i < nev; ++i) cudaEventDestroy(p->aux_ev[i]);
-                if (cs) cudaStreamDestroy(p->copy_stream);
-                if (ok) cudaStreamDestroy(p->aux_stream);
-                p->aux_stream = nullptr;
-                p->copy_stream = nullptr;
-                st = NFFT3_ERR_CUDA;
-            }
-        }
+        if (st == NFFT3_OK) st = ensure_aux(p);
         if (st != NFFT3_OK) {
             void *x = p->x_dev;
             dev_free(x);
@@ -1368,6 +1408,13 @@ int nfft3d_adjoint(nfft3_plan p, const double *f, double *c_out) {
 }
 int nfft3f_adjoint(nfft3_plan p, const float *f, float *c_out) {
     return adjoint_impl<float>(p, f, c_out);
+}
+
+int nfft3d_eval_points(nfft3_plan p, const double *x, const double *c, double *f) {
+    return eval_points_impl<double>(p, x, c, f);
+}
+int nfft3f_eval_points(nfft3_plan p, const double *x, const float *c, float *f) {
+    return eval_points_impl<float>(p, x, c, f);
 }
 
 int nfft3d_eval_host(nfft3_plan p, const double *x_host, const double *c_host, double *f_host) {

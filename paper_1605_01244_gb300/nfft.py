@@ -117,6 +117,18 @@ class Plan:
                    self._fn("_eval_grad")(self._h, _ptr(c), _ptr(f), _ptr(g)))
         return f, g
 
+    def eval_points(self, x: torch.Tensor, c: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """set_points(x) then eval(c) in one call (the transform of c overlaps
+        the sort of x on a second stream where the plan allows)."""
+        self._cuda(x, torch.float64, (self.M, 3), "x")
+        self._cuda(c, self.cdtype, self.N, "c")
+        if out is None:
+            out = torch.empty(self.M, dtype=self.cdtype, device=self.device)
+        self._cuda(out, self.cdtype, (self.M,), "out")
+        _lib.check(self.prefix + "_eval_points", self._fn("_eval_points")(self._h, _ptr(x), _ptr(c), _ptr(out)))
+        self._x = x
+        return out
+
     def chain_x(self, G: torch.Tensor, grad: torch.Tensor) -> torch.Tensor:
         """(M, 3) float64 dL/dx with dL/dx_{j,d} = Re(conj(G_j) grad[j, d]):
         G the upstream gradient of f, grad from :meth:`eval_grad`."""

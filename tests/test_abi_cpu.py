@@ -88,6 +88,8 @@ def test_null_handles(lib):
     assert lib.nfft3d_set_points(None, None) == _lib.NFFT3_ERR_ARG
     assert lib.nfft3_sync(None) == _lib.NFFT3_ERR_ARG
     assert lib.nfft3d_chain_x(None, None, None, None) == _lib.NFFT3_ERR_ARG
+    assert lib.nfft3d_eval_points(None, None, None, None) == _lib.NFFT3_ERR_ARG
+    assert lib.nfft3f_eval_points(None, None, None, None) == _lib.NFFT3_ERR_ARG
     assert lib.nfft3f_chain_x(None, None, None, None) == _lib.NFFT3_ERR_ARG
 
 

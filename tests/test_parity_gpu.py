@@ -247,6 +247,33 @@ def test_host_path_matches_device_path(prec):
         assert torch.equal(f2, plan.eval(c2h.cuda()).cpu())
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_eval_points_matches_set_points_then_eval(prec):
+    """nfft3*_eval_points (the transform of c overlapping the sort of x)
+    against set_points followed by eval: the same bits, on back-to-back
+    calls with new points and coefficients, with a clustered population
+    (dense batches) included; non-finite points fail like set_points; an
+    empty plan returns at once."""
+    from paper_1605_01244_gb300 import Plan, _lib
+    N = (32, 32, 32)
+    M = 20001
+    plan = Plan(N, M, m=5, precision=prec)
+    ref = Plan(N, M, m=5, precision=prec)
+    for seed in (1, 2, 3):
+        c = to_dev(wl.gaussian_coeffs(N, 6.0, seed=seed), CD[prec])
+        x = to_dev(wl.mixed_points(M, 0.01, seed=seed + 10))
+        f = plan.eval_points(x, c)
+        ref.set_points(x)
+        assert torch.equal(f, ref.eval(c))
+    bad = x.clone()
+    bad[7, 1] = float("nan")
+    with pytest.raises(NFFTError) as e:
+        plan.eval_points(bad, c)
+    assert e.value.code == NFFT3_ERR_POINTS
+    empty = Plan(N, 0, m=5, precision=prec)
+    assert empty.eval_points(torch.empty((0, 3), dtype=torch.float64, device="cuda"), c).shape == (0,)
+
+
 @pytest.mark.parametrize("prec,m,tol", [("f64", 6, 1e-12), ("f32", 3, 1e-6)])
 def test_precision_sweep_full_size_sampled(prec, m, tol):
     """N = 256^3, M = 10^7 (half uniform, half clustered, std 0.02), the
