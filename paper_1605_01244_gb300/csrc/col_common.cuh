@@ -75,6 +75,37 @@ __device__ __forceinline__ void x2_df_mac(f32x2 &sh, f32x2 &sl, f32x2 xh, f32x2 
     sl = x2_add(sl, x2_add(err, e));
     sh = s;
 }
+// (ph, pl) = (xh, xl) (yh, yl), normalised, on both halves of the pairs: the
+// exact product of the high parts, its error and the cross terms, then one
+// fast two-sum; z: a run-time zero (x2_opaque)
+__device__ __forceinline__ void x2_df_mul(f32x2 &ph, f32x2 &pl, f32x2 xh, f32x2 xl, f32x2 yh, f32x2 yl,
+                                          f32x2 z) {
+    const f32x2 p = x2_opaque(x2_mul(xh, yh), z);
+    f32x2 e = x2_fma(xh, yh, x2_sub(0ull, p));
+    e = x2_fma(xh, yl, e);
+    e = x2_fma(xl, yh, e);
+    ph = x2_add(p, e);
+    pl = x2_sub(e, x2_sub(ph, p));
+}
+// (sh, sl) += (xh, xl) (yh, yl) on both halves, for a multiplier x that is
+// reused: nxh = -xh and nxl = -xl are passed in (made once, through
+// x2_opaque), so the product's error is carried negated, ne = -e, by
+// multiply-adds alone.  The product of the high parts is fma(xh, yh, z) with
+// the run-time zero z: the same value as the product, but not a product the
+// code generator could fuse into the two-sum's addition.  The same results as
+// x2_df_mac, up to the sign of zero.
+__device__ __forceinline__ void x2_df_mac_neg(f32x2 &sh, f32x2 &sl, f32x2 xh, f32x2 nxh, f32x2 nxl, f32x2 yh,
+                                              f32x2 yl, f32x2 z) {
+    const f32x2 p = x2_fma(xh, yh, z);
+    f32x2 ne = x2_fma(nxh, yh, p);
+    ne = x2_fma(nxh, yl, ne);
+    ne = x2_fma(nxl, yh, ne);
+    const f32x2 s = x2_add(sh, p);
+    const f32x2 bb = x2_sub(s, sh);
+    const f32x2 err = x2_add(x2_sub(sh, x2_sub(s, bb)), x2_sub(p, bb));
+    sl = x2_add(sl, x2_sub(err, ne));
+    sh = s;
+}
 // df_norm on both halves
 __device__ __forceinline__ void x2_df_norm(f32x2 &sh, f32x2 &sl) {
     const f32x2 s = x2_add(sh, sl);

@@ -301,10 +301,12 @@ cudaError_t launch_spread(const typename Cplx<R>::T *f, Grid3 g, int m, PointsVi
 // Hq non-null (FP64 family, m <= 7): the boxes are flushed as exact
 // fixed-point sums into Hq (four int64 limbs per node, zeroed by the caller)
 // instead of FP64 atomics into H; launch_fixed_to_grid then writes H.
+// wdf_dev: the FP64 family's table wdf in device memory (16-byte aligned H).
 template <typename R>
 cudaError_t launch_spread_tiles(const typename Cplx<R>::T *f, Grid3 g, int m, PointsView<R> pts,
-                                const WinTable<R> &w, const WinTableDF *wdf, const int4 *chunks, int nchunks,
-                                int nt2, int nt3, typename Cplx<R>::T *H, unsigned long long *Hq, cudaStream_t st);
+                                const WinTable<R> &w, const WinTableDF *wdf, const WinTableDF *wdf_dev,
+                                const int4 *chunks, int nchunks, int nt2, int nt3, typename Cplx<R>::T *H,
+                                unsigned long long *Hq, cudaStream_t st);
 cudaError_t launch_fixed_to_grid(const unsigned long long *Hq, double2 *H, int64_t total, cudaStream_t st);
 
 template <typename R>

@@ -360,6 +360,7 @@ void release(nfft3_plan p) {
     }
     dev_free(p->grid);
     dev_free(p->pgrid);
+    dev_free(p->wtdf_dev);
     {
         void *v = p->vexp;
         dev_free(v);
@@ -514,6 +515,11 @@ int make_plan(nfft3_plan *out, int prec, int N1, int N2, int N3, int64_t M, int 
                                         cudaMemcpyHostToDevice));
         std::free(h);
         std::free(hf);
+    }
+    if (st == NFFT3_OK && prec == 64) {
+        st = dev_alloc(p, &p->wtdf_dev, sizeof(WinTableDF));
+        if (st == NFFT3_OK)
+            st = cuda_status(cudaMemcpy(p->wtdf_dev, &p->wtdf, sizeof(WinTableDF), cudaMemcpyHostToDevice));
     }
     const int64_t nn = (int64_t)p->n[0] * p->n[1] * p->n[2];
     if (st == NFFT3_OK) {
@@ -1132,8 +1138,9 @@ template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
         if (prec != 64 || p->spread_direct) return NFFT3_ERR_ARG;
         e = cudaMemsetAsync(p->Hq, 0, 4 * sizeof(unsigned long long) * nn, p->stream);
         if (e == cudaSuccess && p->nchunks > 0)
-            e = launch_spread_tiles<R>((const C *)f, g, p->m, pv, win_table<R>(p), &p->wtdf, p->pb.chunks,
-                                       p->nchunks, p->pb.nt2, p->pb.nt3, H, p->Hq, p->stream);
+            e = launch_spread_tiles<R>((const C *)f, g, p->m, pv, win_table<R>(p), &p->wtdf,
+                                       (const WinTableDF *)p->wtdf_dev, p->pb.chunks, p->nchunks, p->pb.nt2,
+                                       p->pb.nt3, H, p->Hq, p->stream);
         if (e == cudaSuccess) e = launch_fixed_to_grid(p->Hq, (double2 *)H, nn, p->stream);
         p->launches += 1;
     } else {
@@ -1141,7 +1148,8 @@ template <typename R> int adjoint_impl(nfft3_plan p, const R *f, R *c_out) {
         if (e != cudaSuccess) return NFFT3_ERR_CUDA;
         if (!p->spread_direct && p->nchunks > 0)
             e = launch_spread_tiles<R>((const C *)f, g, p->m, pv, win_table<R>(p), prec == 64 ? &p->wtdf : nullptr,
-                                       p->pb.chunks, p->nchunks, p->pb.nt2, p->pb.nt3, H, nullptr, p->stream);
+                                       (const WinTableDF *)p->wtdf_dev, p->pb.chunks, p->nchunks, p->pb.nt2,
+                                       p->pb.nt3, H, nullptr, p->stream);
         else
             e = launch_spread<R>((const C *)f, g, p->m, pv, win_table<R>(p), H, p->stream);
     }

@@ -21,6 +21,7 @@ struct nfft3_plan_s {
     gbnfft::WinTable<double> wt64;
     gbnfft::WinTable<float> wt32;
     gbnfft::WinTableDF wtdf;   // FP64 family: double-float copy for the FP32-pipe gather
+    void *wtdf_dev;            // FP64 family: wtdf in device memory (read by the adjoint spread)
     double window_err;
     double window_err_df;
     int df_weights_fp64;       // GBNFFT_DF_WEIGHTS: FP64-pipe weights (default) or df ("df")

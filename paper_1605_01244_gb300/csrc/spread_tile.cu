@@ -8,6 +8,8 @@
 // spread_tile_df_kernel (FP64, double-float; rows of one parity in two
 // planes per warp) and spread_tile_f32_kernel (mixed; one plane per warp)
 // give each warp its own set of box nodes, so no node update needs an atomic.
+#include <cstdint>
+
 #include "col_common.cuh"
 
 namespace gbnfft {
@@ -338,6 +340,230 @@ __global__ void __launch_bounds__(SpreadDF<MM>::THREADS) spread_tile_df_kernel(
     }
 }
 
+// ---- FP64 family, line-owned: the box in registers ----------------------------
+// Thread (i1, i2) owns the box line of nodes (i1, i2, 0 .. B-1) and keeps
+// them in registers as double-float pairs for the whole chunk.  For each
+// point whose stencil crosses the line (i1 - ox and i2 - oy both within the
+// 2m+1 taps), the thread forms F = f w1(i1 - ox) w2(i2 - oy) once and adds
+// F w3(c) to its node oz + c for the 2m+1 taps c.  The chunk's points are
+// the same for every thread, so the tap range along the line (oz) is the
+// same across a warp and its test costs no divergence; no node is read or
+// written in shared memory during the sums.  Lines are numbered i1-major, so
+// a warp covers about 1.6 planes: for an average point 9 of the 13 warps
+// have a line in its stencil, with 59 % of their lanes active.  After the
+// last point the lines go to shared memory (a box with an odd line pitch,
+// which keeps a quarter warp's 16-byte stores in distinct banks), and the
+// box is added to the grid in node order, as in the half-box kernel.
+template <int MM> struct SpreadLine {
+    static constexpr int W = 2 * MM + 1, B = kTile + 2 * MM, NL = B * B;
+    static constexpr int THREADS = (NL + 31) / 32 * 32;
+    static constexpr int LP = B + 1;   // line pitch of the flush box (nodes)
+    // staging: f w1, w2 and w3 as 16-byte pairs per point and tap, f, the
+    // packed offsets and the tap polynomials; the flush box reuses the bytes
+    static constexpr size_t STAGE = sizeof(float4) * ((size_t)3 * kChunk * W + kChunk) +
+                                    sizeof(int) * (size_t)kChunk + sizeof(PolyDF<MM>);
+    static constexpr size_t BOX = sizeof(float4) * (size_t)NL * LP;
+    static constexpr size_t UNION = ((STAGE > BOX ? STAGE : BOX) + 15) / 16 * 16;
+    static constexpr size_t SMEM = UNION + sizeof(int) * 3 * B;
+};
+
+// node O + c += F w3(c) for the 2m+1 taps c, renormalised after each
+// addition, for the point's first stencil node O = oz along the line: one
+// straight run of independent updates per value of oz, so that the code
+// generator can interleave their dependent chains (the node index must be a
+// constant for the nodes to stay in registers)
+template <int O, int B, int W>
+__device__ __forceinline__ void line_taps(int oz, f32x2 (&acch)[B], f32x2 (&accl)[B], f32x2 Fh, f32x2 nFh,
+                                          f32x2 nFl, const ulonglong2 *__restrict__ w3, f32x2 zero) {
+    if constexpr (O + W <= B) {
+        if (oz == O) {
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+                const ulonglong2 wv = w3[c];
+                x2_df_mac_neg(acch[O + c], accl[O + c], Fh, nFh, nFl, wv.x, wv.y, zero);
+                x2_df_norm(acch[O + c], accl[O + c]);
+            }
+        } else {
+            line_taps<O + 1, B, W>(oz, acch, accl, Fh, nFh, nFl, w3, zero);
+        }
+    }
+}
+
+// dst[0 .. bytes) += src[0 .. bytes) element by element in FP64, by the
+// tensor memory accelerator (each element's addition is atomic); both
+// addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_add_f64(double *dst, const void *src, unsigned bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(src);
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;"
+                 :: "l"(dst), "r"(sa), "r"(bytes) : "memory");
+}
+
+template <int MM, bool FIXED>
+__global__ void __launch_bounds__(SpreadLine<MM>::THREADS, 1) spread_line_df_kernel(
+    const double2 *__restrict__ f, Grid3 g, PointsView<double> pts, const WinTableDF *__restrict__ wt,
+    const int4 *__restrict__ chunks, int nt2, int nt3, double2 *__restrict__ H, unsigned long long *__restrict__ Hq,
+    f32x2 zero) {
+    using S = SpreadLine<MM>;
+    constexpr int W = S::W, B = S::B, NL = S::NL, THREADS = S::THREADS, LP = S::LP, D = kPolyDegDF;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ulonglong2 *Gs = reinterpret_cast<ulonglong2 *>(smem_raw);     // [point][a] f w1: (re, im hi), (re, im lo)
+    ulonglong2 *w2s = Gs + kChunk * W;                              // [point][b] w2: (hi, hi), (lo, lo)
+    ulonglong2 *w3s = w2s + kChunk * W;                             // [point][c] w3: (hi, hi), (lo, lo)
+    float4 *fsm = reinterpret_cast<float4 *>(w3s + kChunk * W);    // f: (re hi, im hi, re lo, im lo)
+    int *osm = reinterpret_cast<int *>(fsm + kChunk);              // first stencil node's box indices, packed
+    PolyDF<MM> *tab = reinterpret_cast<PolyDF<MM> *>(osm + kChunk);
+    float4 *box = reinterpret_cast<float4 *>(smem_raw);            // flush: [line][i3], pitch LP
+    int *wrap = reinterpret_cast<int *>(smem_raw + S::UNION);
+    const int4 ch = chunks[blockIdx.x];
+    const int t = ch.x;
+    const int tt3 = t % nt3, tt2 = (t / nt3) % nt2, tt1 = t / (nt3 * nt2);
+    fill_wrap<B, MM>(wrap, tt1, tt2, tt3, g);
+    {
+        // the plan's table in device memory (read by every block, so it stays
+        // in L2): rows of D + 1 coefficients, consecutive threads on
+        // consecutive addresses
+        // (all of a thread's loads first, so that they wait on L2 once)
+        constexpr int NR = 3 * W * (D + 1), PER = (2 * NR + THREADS - 1) / THREADS;
+        float *dst = &tab->ch[0][0][0];   // ch then cl
+        float v[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = threadIdx.x + q * THREADS, ee = e < 2 * NR ? e : 0;
+            const int which = ee / NR, r = ee - which * NR, row = r / (D + 1), k = r - row * (D + 1);
+            const int d = row / W, tap = row - d * W;
+            v[q] = which ? wt->cl[d][tap][k] : wt->ch[d][tap][k];
+        }
+#pragma unroll
+        for (int q = 0; q < PER; ++q)
+            if (threadIdx.x + q * THREADS < 2 * NR) dst[threadIdx.x + q * THREADS] = v[q];
+    }
+    for (int i = threadIdx.x; i < ch.z; i += THREADS) {
+        const int4 key = pts.key[(int64_t)ch.y + i];
+        // f enters scaled by 2^s, so the float pairs keep its range
+        const double2 fv = scale_value(f[key.w], value_shift(pts.vexp));
+        const float2 re = df2_split(fv.x), im = df2_split(fv.y);
+        fsm[i] = make_float4(re.x, im.x, re.y, im.y);
+        // box indices of the stencil's first node, each in [0, kTile)
+        const int ox = tile_centre(key.x, MM, g.n1) - kTile * tt1;
+        const int oy = tile_centre(key.y, MM, g.n2) - kTile * tt2, oz = tile_centre(key.z, MM, g.n3) - kTile * tt3;
+        osm[i] = ox | (oy << 6) | (oz << 12);
+    }
+    __syncthreads();
+    // tap weights by double-float Horner in t = 2s - 1.  Item (i, d, g)
+    // evaluates the taps g, g + TG, g + 2 TG, ... of dimension d of point i,
+    // their Horner chains side by side (the steps of one chain depend on one
+    // another, those of different taps do not).  The first dimension's
+    // weights are multiplied by f here, once per point and tap.
+    constexpr int TG = (W + 3) / 4, NT = (W + TG - 1) / TG;
+    for (int e = threadIdx.x; e < ch.z * 3 * TG; e += THREADS) {
+        const int i = e / (3 * TG), r = e - i * (3 * TG), d = r / TG, g0 = r - d * TG;
+        const int64_t j = (int64_t)ch.y + i;
+        const double s = d == 0 ? pts.s1[j] : d == 1 ? pts.s2[j] : pts.s3[j];
+        const float2 tv = df2_split(2.0 * s - 1.0);
+        float vh[NT], vl[NT];
+#pragma unroll
+        for (int q = 0; q < NT; ++q) {
+            const int tap = min(g0 + TG * q, W - 1);   // a tap past W: computed, not stored
+            vh[q] = tab->ch[d][tap][D];
+            vl[q] = tab->cl[d][tap][D];
+        }
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k)
+#pragma unroll
+            for (int q = 0; q < NT; ++q) {
+                const int tap = min(g0 + TG * q, W - 1);
+                df_horner_step(vh[q], vl[q], tv.x, tv.y, tab->ch[d][tap][k], tab->cl[d][tap][k]);
+            }
+#pragma unroll
+        for (int q = 0; q < NT; ++q) {
+            const int tap = g0 + TG * q;
+            if (tap >= W) break;
+            if (d == 0) {
+                const float4 fv = fsm[i];
+                const float2 v = make_float2(vh[q], vl[q]);
+                const float2 re = df2_mul(make_float2(fv.x, fv.z), v), im = df2_mul(make_float2(fv.y, fv.w), v);
+                Gs[i * W + tap] = make_ulonglong2(x2_pack(re.x, im.x), x2_pack(re.y, im.y));
+            } else {
+                (d == 1 ? w2s : w3s)[i * W + tap] =
+                    make_ulonglong2(x2_pack(vh[q], vh[q]), x2_pack(vl[q], vl[q]));
+            }
+        }
+    }
+    __syncthreads();
+    const int line = threadIdx.x;
+    const int i1 = line < NL ? line / B : B, i2 = line - (line / B) * B;   // i1 = B: a lane with no line
+    f32x2 acch[B], accl[B];   // node (i1, i2, j): (re, im) hi and lo
+#pragma unroll
+    for (int j = 0; j < B; ++j) acch[j] = accl[j] = 0ull;
+    for (int i = 0; i < ch.z; ++i) {
+        const int op = osm[i];
+        const int a = i1 - (op & 63), b = i2 - ((op >> 6) & 63);
+        if ((unsigned)a >= (unsigned)W || (unsigned)b >= (unsigned)W) continue;
+        const int oz = op >> 12;
+        // F = f w1 w2 as packed double-float pairs
+        const ulonglong2 G = Gs[i * W + a], w2 = w2s[i * W + b];
+        f32x2 Fh, Fl;
+        x2_df_mul(Fh, Fl, G.x, G.y, w2.x, w2.y, zero);
+        // -F, made opaque so that no product of F is folded against it
+        const f32x2 nFh = x2_opaque(x2_sub(0ull, Fh), zero), nFl = x2_opaque(x2_sub(0ull, Fl), zero);
+        line_taps<0, B, W>(oz, acch, accl, Fh, nFh, nFl, w3s + i * W, zero);
+    }
+    __syncthreads();   // the staging bytes become the flush box
+    if constexpr (!FIXED) {
+        // each thread turns its line into FP64 and adds it to the grid row by
+        // row with bulk reductions (split where the row wraps around the grid)
+        if (line < NL) {
+            double2 *row = reinterpret_cast<double2 *>(box) + line * LP;
+            f32x2 any = 0ull;
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                float rh, ih, rl, il;
+                x2_unpack(acch[j], rh, ih);
+                x2_unpack(accl[j], rl, il);
+                row[j] = make_double2(df_pair_to_double(rh, rl), df_pair_to_double(ih, il));
+                any |= acch[j];
+            }
+            if (any != 0ull) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the row, to the copy engine
+                double *grow = reinterpret_cast<double *>(H + ((int64_t)wrap[i1] * g.n2 + wrap[B + i2]) * g.n3);
+                for (int j = 0; j < B;) {
+                    const int c3 = wrap[2 * B + j], run = min(B - j, g.n3 - c3);
+                    bulk_add_f64(grow + 2 * (int64_t)c3, row + j, 16u * (unsigned)run);
+                    j += run;
+                }
+            }
+        }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // the rows have been read
+    } else {
+        if (line < NL) {
+            ulonglong2 *row = reinterpret_cast<ulonglong2 *>(box + line * LP);
+#pragma unroll
+            for (int j = 0; j < B; ++j) row[j] = make_ulonglong2(acch[j], accl[j]);
+        }
+        __syncthreads();
+        // exact fixed-point sums, U nodes a thread at a time
+        constexpr int NN = NL * B, U = 4;
+        for (int e0 = threadIdx.x; e0 < NN; e0 += U * THREADS) {
+            float4 v[U];
+            int64_t node[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * THREADS, ee = e < NN ? e : NN - 1;
+                const int ln = ee / B, i3 = ee - ln * B, l1 = ln / B, l2 = ln - l1 * B;
+                v[u] = e < NN ? box[ln * LP + i3] : make_float4(0.f, 0.f, 0.f, 0.f);   // (re hi, im hi, re lo, im lo)
+                node[u] = ((int64_t)wrap[l1] * g.n2 + wrap[B + l2]) * g.n3 + wrap[2 * B + i3];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (v[u].x == 0.f && v[u].y == 0.f) continue;
+                fixed_add(Hq + 4 * node[u], v[u].x, v[u].z);
+                fixed_add(Hq + 4 * node[u] + 2, v[u].y, v[u].w);
+            }
+        }
+    }
+}
+
 // H[node] = the fixed-point limbs as FP64 (deterministic mode)
 __global__ void fixed_to_grid_kernel(const unsigned long long *__restrict__ Hq, double2 *__restrict__ H,
                                      int64_t total) {
@@ -445,10 +671,13 @@ __global__ void __launch_bounds__(32 * (kTile + 2 * MM)) spread_tile_f32_kernel(
     }
 }
 
+// the line-owned FP64 kernel serves m <= 7
+template <int MM> constexpr bool kLineSpread = MM <= 7;
+
 template <typename R, int MM>
 cudaError_t spread_tile_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsView<R> pts, const WinTable<R> &w,
-                                 const WinTableDF *wdf, const int4 *chunks, int nchunks, int nt2, int nt3,
-                                 typename Cplx<R>::T *H, unsigned long long *Hq, cudaStream_t st) {
+                                 const WinTableDF *wdf, const WinTableDF *wdf_dev, const int4 *chunks, int nchunks,
+                                 int nt2, int nt3, typename Cplx<R>::T *H, unsigned long long *Hq, cudaStream_t st) {
     constexpr int B = kTile + 2 * MM;
     if constexpr (sizeof(R) == 4) {
         if (Hq) return cudaErrorInvalidValue;   // deterministic mode: FP64 family only
@@ -459,10 +688,22 @@ cudaError_t spread_tile_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsVi
         kern<<<(unsigned)nchunks, 32 * B, smem_f, st>>>(f, g, pts, make_poly<float, MM>(w), chunks, nt2, nt3, H);
     } else {
         static_assert(spread_df_smem<MM>() <= 227 * 1024, "half box and staged weights fit one block");
-        // FP64 family: the double-float kernel where its half box and staged
-        // weights fit one SM's shared memory (every m up to 8)
-        constexpr size_t smem_df = spread_df_smem<MM>();
         if (!wdf) return cudaErrorInvalidValue;
+        if constexpr (kLineSpread<MM>) {
+            // FP64 family, m <= 7: one thread per box line, nodes in registers
+            constexpr size_t smem_l = SpreadLine<MM>::SMEM;
+            static_assert(smem_l <= 227 * 1024, "flush box fits one block");
+            if (!wdf_dev || (reinterpret_cast<uintptr_t>(H) & 15u)) return cudaErrorInvalidValue;
+            auto kern = Hq ? spread_line_df_kernel<MM, true> : spread_line_df_kernel<MM, false>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l);
+            if (e != cudaSuccess) return e;
+            kern<<<(unsigned)nchunks, SpreadLine<MM>::THREADS, smem_l, st>>>(f, g, pts, wdf_dev, chunks, nt2, nt3, H,
+                                                                              Hq, 0ull);
+            return cudaGetLastError();
+        }
+        // m = 8: the half-box kernel (a line of 24 nodes does not fit the
+        // registers of 576 threads)
+        constexpr size_t smem_df = spread_df_smem<MM>();
         auto kern = Hq ? spread_tile_df_kernel<MM, true> : spread_tile_df_kernel<MM, false>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
         if (e != cudaSuccess) return e;
@@ -477,27 +718,30 @@ cudaError_t spread_tile_dispatch(const typename Cplx<R>::T *f, Grid3 g, PointsVi
 
 template <typename R>
 cudaError_t launch_spread_tiles(const typename Cplx<R>::T *f, Grid3 g, int m, PointsView<R> pts,
-                                const WinTable<R> &w, const WinTableDF *wdf, const int4 *chunks, int nchunks,
-                                int nt2, int nt3, typename Cplx<R>::T *H, unsigned long long *Hq, cudaStream_t st) {
+                                const WinTable<R> &w, const WinTableDF *wdf, const WinTableDF *wdf_dev,
+                                const int4 *chunks, int nchunks, int nt2, int nt3, typename Cplx<R>::T *H,
+                                unsigned long long *Hq, cudaStream_t st) {
     if (nchunks <= 0) return cudaSuccess;
     switch (m) {
-        case 1: return spread_tile_dispatch<R, 1>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
-        case 2: return spread_tile_dispatch<R, 2>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
-        case 3: return spread_tile_dispatch<R, 3>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
-        case 4: return spread_tile_dispatch<R, 4>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
-        case 5: return spread_tile_dispatch<R, 5>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
-        case 6: return spread_tile_dispatch<R, 6>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
-        case 7: return spread_tile_dispatch<R, 7>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
-        case 8: return spread_tile_dispatch<R, 8>(f, g, pts, w, wdf, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 1: return spread_tile_dispatch<R, 1>(f, g, pts, w, wdf, wdf_dev, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 2: return spread_tile_dispatch<R, 2>(f, g, pts, w, wdf, wdf_dev, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 3: return spread_tile_dispatch<R, 3>(f, g, pts, w, wdf, wdf_dev, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 4: return spread_tile_dispatch<R, 4>(f, g, pts, w, wdf, wdf_dev, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 5: return spread_tile_dispatch<R, 5>(f, g, pts, w, wdf, wdf_dev, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 6: return spread_tile_dispatch<R, 6>(f, g, pts, w, wdf, wdf_dev, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 7: return spread_tile_dispatch<R, 7>(f, g, pts, w, wdf, wdf_dev, chunks, nchunks, nt2, nt3, H, Hq, st);
+        case 8: return spread_tile_dispatch<R, 8>(f, g, pts, w, wdf, wdf_dev, chunks, nchunks, nt2, nt3, H, Hq, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template cudaError_t launch_spread_tiles<double>(const double2 *, Grid3, int, PointsView<double>,
-                                                 const WinTable<double> &, const WinTableDF *, const int4 *, int,
+                                                 const WinTable<double> &, const WinTableDF *, const WinTableDF *,
+                                                 const int4 *, int,
                                                  int, int, double2 *, unsigned long long *, cudaStream_t);
 template cudaError_t launch_spread_tiles<float>(const float2 *, Grid3, int, PointsView<float>,
-                                                const WinTable<float> &, const WinTableDF *, const int4 *, int,
+                                                const WinTable<float> &, const WinTableDF *, const WinTableDF *,
+                                                const int4 *, int,
                                                 int, int, float2 *, unsigned long long *, cudaStream_t);
 
 cudaError_t launch_fixed_to_grid(const unsigned long long *Hq, double2 *H, int64_t total, cudaStream_t st) {

@@ -562,14 +562,16 @@ def test_pruned_and_full_fft_agree(sigma, monkeypatch):
 
 @pytest.mark.parametrize("prec,m,N", [("f64", 6, (24, 20, 32)), ("f64", 8, (8, 8, 8)), ("f64", 1, (16, 10, 12)),
                                       ("f64", 7, (20, 24, 16)), ("f64", 4, (32, 32, 32)), ("f64", 8, (24, 16, 20)),
-                                      ("f32", 3, (24, 20, 32)), ("f32", 8, (10, 12, 8))])
+                                      ("f64", 6, (8, 8, 8)), ("f32", 3, (24, 20, 32)), ("f32", 8, (10, 12, 8))])
 def test_tiled_spread_matches_direct_and_cpu(prec, m, N, monkeypatch):
-    """The adjoint's shared-memory tile spread (default) against the one-thread-
-    per-point spread (GBNFFT_SPREAD=direct) and the CPU NFFT restatement.  A
-    dense cluster puts hundreds of points in one tile (several chunks of one
-    tile); N = 8^3 at m = 8 gives n = 16 < the 24-node box, whose nodes wrap
-    onto each other.  The FP64 half boxes hold an odd number of planes at
-    m = 1 and m = 7 (one warp then owns a single plane)."""
+    """The adjoint's tile spread (default) against the one-thread-per-point
+    spread (GBNFFT_SPREAD=direct) and the CPU NFFT restatement.  A dense
+    cluster puts hundreds of points in one tile (several chunks of one tile).
+    N = 8^3 gives n = 16, below the box of 20 nodes (m = 6, the line-owned
+    kernel: a box row reaches the grid's row in two pieces, and box lines land
+    on the same grid row twice) and of 24 nodes (m = 8, the half-box kernel,
+    whose nodes wrap onto each other).  The FP64 half boxes hold an odd number
+    of planes at m = 1 and m = 7 (one warp then owns a single plane)."""
     from paper_1605_01244_gb300 import Plan
     x = np.concatenate([wl.uniform_points(900, seed=60), wl.cluster_points(1100, 0.002, seed=61)])
     g = wl.rng(62)
