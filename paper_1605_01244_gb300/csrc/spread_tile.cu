@@ -1,13 +1,16 @@
-// Adjoint spread through shared memory (the first step of the transposed
-// NFFT: H[l] += f_j phi(x_j - l / n) over the 2m+1 stencil nodes per
-// dimension), one block per chunk of at most kChunk sorted points of one
+// Adjoint spread by tile boxes (the first step of the transposed NFFT:
+// H[l] += f_j phi(x_j - l / n) over the 2m+1 stencil nodes per dimension),
+// one block (or two) per chunk of at most kChunk sorted points of one
 // kTile^3 tile.  The stencils of a tile's points lie in the box of
 // (kTile + 2m)^3 nodes starting m nodes before the tile, so the block
 // accumulates them there and then adds the box to the oversampled grid once
-// (global atomics, node indices wrapped mod n).
-// spread_tile_df_kernel (FP64, double-float; rows of one parity in two
-// planes per warp) and spread_tile_f32_kernel (mixed; one plane per warp)
-// give each warp its own set of box nodes, so no node update needs an atomic.
+// (node indices wrapped mod n).
+// spread_line_df_kernel (FP64, m <= 7): one thread per box line, the nodes
+// in registers, rows added by bulk FP64 reductions.  spread_tile_df_kernel
+// (FP64, m = 8; double-float half boxes in shared memory, rows of one parity
+// in two planes per warp) and spread_tile_f32_kernel (mixed; one plane per
+// warp) give each warp its own set of box nodes, so no node update needs an
+// atomic, and add the box with global atomics.
 #include <cstdint>
 
 #include "col_common.cuh"
@@ -351,9 +354,13 @@ __global__ void __launch_bounds__(SpreadDF<MM>::THREADS) spread_tile_df_kernel(
 // written in shared memory during the sums.  Lines are numbered i1-major, so
 // a warp covers about 1.6 planes: for an average point 9 of the 13 warps
 // have a line in its stencil, with 59 % of their lanes active.  After the
-// last point the lines go to shared memory (a box with an odd line pitch,
-// which keeps a quarter warp's 16-byte stores in distinct banks), and the
-// box is added to the grid in node order, as in the half-box kernel.
+// last point each thread converts its line to FP64 in shared memory (lines
+// at an odd pitch, which keeps a quarter warp's 16-byte stores in distinct
+// banks) and adds it to the grid's row with bulk FP64 reductions by the
+// tensor memory accelerator, one per contiguous piece of the row (two where
+// the box wraps around the grid).  In deterministic mode the lines stay
+// double-float pairs and the box is added in node order as exact fixed-point
+// sums, as in the half-box kernel.
 template <int MM> struct SpreadLine {
     static constexpr int W = 2 * MM + 1, B = kTile + 2 * MM, NL = B * B;
     static constexpr int THREADS = (NL + 31) / 32 * 32;
