@@ -224,8 +224,9 @@ int nfft3_set_num_points(nfft3_plan p, int64_t M);
  * the points of each tile by original index (a stable radix sort instead of
  * the atomic counting sort), and the adjoint's spread adds its tile boxes to
  * the grid as exact fixed-point sums (two int64 limbs per component,
- * resolution 2^-60 of the range-scaled values) instead of FP64 atomics, so
- * that adjoint results are bitwise reproducible from run to run.  Allocates
+ * resolution 2^-60 of the range-scaled values) instead of FP64 additions in
+ * whatever order the blocks run (atomics, or bulk row reductions), so that
+ * adjoint results are bitwise reproducible from run to run.  Allocates
  * 32 bytes per oversampled grid node plus sort buffers; on == 0 releases
  * them.  Either way the points must be set again (NFFT3_ERR_NO_POINTS until
  * then).  NFFT3_ERR_ARG for mixed plans, or the one-thread spread
